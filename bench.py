@@ -1,0 +1,403 @@
+"""Benchmark of the similarity self-join on the 2M-point 4-D uniform workload.
+
+One step = the whole hot path on one batch: build the grid index of the
+points already resident on the GPU (extent, cell keys, radix sort, cell table,
+packing, neighbour runs, work items) and run the join (distance tiles, eps
+threshold, compaction into result pages) until the result count is known.
+
+Prints ONE JSON line (rank 0).  ``value`` is candidate pairs per second for the
+headline kernel: the candidate pairs of the full 3^4 grid neighbourhoods
+(ordered, self pairs included) divided by the step time, summed over ranks.
+The plain FP64 kernels are timed in the same run under ``variants``.
+
+--impl reference runs the CPU oracle instead (brute force, all host cores, a
+bounded sample of queries per step, scaled to the whole workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "self-join candidate pairs/s and join time, n=2M d=4: FP64 plain vs low-prec filter"
+UNIT = "candidate pairs/s"
+HEADLINE = "filter_f32"
+VARIANTS = ["filter_f32", "fp64_fma", "fp64_dmma"]
+L2_FLUSH_BYTES = 256 << 20
+FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+FP64_PEAK_TFLOPS = 1.25                                   # GB300 nominal FP64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=2_000_000)
+    ap.add_argument("--variants", default=",".join(VARIANTS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0 = sized for ~15 s)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(w, extra=None):
+    cfg = {"workload": f"uniform4d: n={w.n} points i.i.d. uniform in [0,1]^4 (seed {w.seed}), "
+                       f"eps={w.eps:.7g} (4-ball volume for a mean of 64 neighbours)",
+           "n": w.n, "d": w.d, "eps": w.eps}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---- clocks sampled during the timed region -----------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- native arm -------------------------------------------------------------------
+
+def run_native(args):
+    import torch
+
+    from paper_2209_11287_gb300 import binding, build, workloads
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    binding.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    w = workloads.uniform4d(n=args.n)
+    pts = torch.from_numpy(w.points).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def one_step(opt, host=None, host_out=None):
+        h = binding.sj_build_index(pts if host is None else host, w.eps, opt, stream)
+        r = binding.sj_self_join(h)
+        if host_out is not None:
+            binding.sj_result_copy(r, host_out)
+        info = (int(r.count), int(r.n_candidates), int(r.n_evaluated), int(r.n_rechecked), int(r.reruns))
+        binding.sj_result_free(r)
+        binding.sj_destroy(h)
+        return info
+
+    results = {}
+    sampler = ClockSampler(local)
+    variants = [v for v in args.variants.split(",") if v]
+    for vi, kname in enumerate(variants):
+        opt = binding.sj_default_options(kernel=kname)
+        for _ in range(args.warmup):
+            one_step(opt)
+        barrier()
+        if vi == 0:
+            sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        launches0 = binding.sj_kernel_launches()
+        info = None
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict the inputs from L2 between steps
+            ev[k][0].record(stream)
+            info = one_step(opt)
+            ev[k][1].record(stream)
+        barrier()
+        launches = binding.sj_kernel_launches() - launches0
+        clocks = sampler.stop() if vi == 0 else None
+        times = [a.elapsed_time(b) for a, b in ev]
+        ms = max_over_ranks(sum(times) / len(times))
+        count, cand, evald, rech, reruns = info
+        results[kname] = {"ms_per_step": ms, "count": count, "n_candidates": cand, "n_evaluated": evald,
+                          "n_rechecked": rech, "reruns": reruns, "launches": launches, "clocks": clocks,
+                          "ms_min": min(times), "ms_max": max(times)}
+
+    # kernel-only time of the headline's distance kernel, CUDA events on its stream
+    head = results[variants[0]]
+    kern_ms = kernel_time(binding, torch, w, pts, stream, variants[0], flush, args)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    host_pts = torch.from_numpy(w.points).pin_memory()
+    host_out = torch.empty((head["count"] + 16, 2), dtype=torch.int32).pin_memory()
+    opt = binding.sj_default_options(kernel=variants[0])
+    one_step(opt, host_pts, host_out)
+    barrier()
+    t_e2e = []
+    for k in range(max(3, min(args.steps, 10))):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        one_step(opt, host_pts, host_out)
+        torch.cuda.synchronize(dev)
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(statistics.mean(t_e2e))
+
+    if rank == 0:
+        line = make_line(args, w, results, variants, world, kern_ms, e2e_s, head)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, head["n_candidates"], args.cpu_queries)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def kernel_time(binding, torch, w, pts, stream, kname, flush, args):
+    """Average duration of the distance-tile kernel alone: the join is run on a
+    built index with CUDA events around sj_self_join's kernel (the count read
+    back is outside the events only by the host synchronisation)."""
+    opt = binding.sj_default_options(kernel=kname)
+    h = binding.sj_build_index(pts, w.eps, opt, stream)
+    for _ in range(2):
+        binding.sj_result_free(binding.sj_self_join(h))
+    ts = []
+    for k in range(max(3, args.steps)):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = binding.sj_self_join(h)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+        binding.sj_result_free(r)
+    binding.sj_destroy(h)
+    return statistics.mean(ts)
+
+
+def read_traffic(kname):
+    """DRAM bytes per launch of the distance kernel from the committed ncu
+    summary (a line 'dram_bytes_per_launch: <int>' and 'kernel_source_sha:
+    <sha>'), or None when absent or taken on different kernel sources."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"join_{kname}_uniform4d.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2209_11287_gb300", "csrc", "sj_join_cc.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha") != sha:
+        return None
+    try:
+        return int(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def make_line(args, w, results, variants, world, kern_ms, e2e_s, head):
+    kname = variants[0]
+    cand = head["n_candidates"]
+    value = world * cand / (head["ms_per_step"] * 1e-3)
+    # roofline of the distance kernel: FP32 FMA work of the evaluated pairs
+    # (d fma = 2d flop per pair) against the FP32 FMA peak, and its bytes
+    # (points read once + 8 bytes per emitted pair) against HBM
+    flops = 2.0 * w.d * head["n_evaluated"]
+    tfl = flops / (kern_ms * 1e-3) / 1e12
+    bytes_alg = w.n * (4 * 4 + 4 * 3) + 8 * head["count"]
+    gbs = bytes_alg / (kern_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp_peak = FP32_FMA_PEAK_TFLOPS if kname != "fp64_fma" else FP64_PEAK_TFLOPS
+    frac_alu, frac_hbm = tfl / fp_peak, gbs / hbm_peak
+    traffic = read_traffic(kname)
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(fp_peak, 2), "unit": "TFLOP/s",
+                "frac": round(frac_alu, 4), "traffic": traffic, "kernel": f"k_join_cc ({kname})",
+                "kernel_ms": round(kern_ms, 4), "hbm_frac": round(frac_hbm, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(frac_hbm, 4), "traffic": traffic, "kernel": f"k_join_cc ({kname})",
+                "kernel_ms": round(kern_ms, 4), "alu_frac": round(frac_alu, 4)}
+    var = {}
+    for k in variants:
+        r = results[k]
+        var[k] = {"ms_per_step": round(r["ms_per_step"], 4), "candidate_pairs_per_s": world * r["n_candidates"] / (r["ms_per_step"] * 1e-3),
+                  "result_pairs_per_s": world * r["count"] / (r["ms_per_step"] * 1e-3), "result_pairs": r["count"],
+                  "evaluated_pairs": r["n_evaluated"], "rechecked_pairs": r["n_rechecked"], "reruns": r["reruns"]}
+    e2e_val = world * cand / e2e_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(head["ms_per_step"], 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if kname.startswith("filter") else "f64", "data": "synthetic",
+        "config": workload_config(w, {"kernel": kname, "symmetric": 1, "parallelism": f"replicas x{world}",
+                                      "l2": "flushed between steps (256 MB write)",
+                                      "candidate_pairs": cand, "result_pairs": head["count"]}),
+        "variants": var,
+        "roofline": roof,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": w.n * w.d * 8,
+                "d2h_bytes_per_step": head["count"] * 8, "ms_per_step": round(e2e_s * 1e3, 3)},
+        "gpu_launches": int(head["launches"]),
+        "clocks": head["clocks"],
+    }
+    return line
+
+
+# ---- CPU oracle ----------------------------------------------------------------------
+
+def cpu_baseline(w, n_candidates, n_queries=0):
+    """The oracle (brute force, every query against all n points) on the host
+    cores for a sample of queries, scaled to the whole workload."""
+    import oracle
+    oracle.build()
+    cores = oracle.threads(0)
+    rng = np.random.Generator(np.random.PCG64(4242))
+    if n_queries <= 0:
+        # size the sample for ~15 s: probe with a small one first
+        probe = np.sort(rng.choice(w.n, size=max(64, 4 * cores), replace=False))
+        t0 = time.perf_counter()
+        oracle.rows(w.points, w.eps, probe)
+        dt = time.perf_counter() - t0
+        n_queries = int(min(w.n, max(probe.size, probe.size * 15.0 / max(dt, 1e-3))))
+    sample = np.sort(rng.choice(w.n, size=n_queries, replace=False))
+    t0 = time.perf_counter()
+    oracle.rows(w.points, w.eps, sample)
+    dt = time.perf_counter() - t0
+    full_s = dt * w.n / n_queries
+    return {"value": n_candidates / full_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_queries} of {w.n} queries, each against all {w.n} points, scaled by n / sample",
+            "sample_seconds": round(dt, 2), "full_join_seconds_est": round(full_s, 1)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2209_11287_gb300 import workloads
+    import oracle
+    oracle.build()
+    w = workloads.uniform4d(n=args.n)
+    cand = canonical_candidates_host(w)
+    cores = oracle.threads(0)
+    rng = np.random.Generator(np.random.PCG64(99))
+    # per step: a bounded sample of queries sized so all steps end in a few minutes
+    per_step = max(64, int(args.cpu_queries) if args.cpu_queries else 2000)
+    times = []
+    for k in range(args.warmup + args.steps):
+        sample = np.sort(rng.choice(w.n, size=per_step, replace=False))
+        t0 = time.perf_counter()
+        oracle.rows(w.points, w.eps, sample)
+        dt = (time.perf_counter() - t0) * w.n / per_step
+        if k >= args.warmup:
+            times.append(dt)
+    s = statistics.mean(times)
+    value = cand / s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(w, {"kernel": "oracle brute force (CPU)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} of {w.n} queries per step against all points, scaled by n / sample"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def canonical_candidates_host(w):
+    """Candidate pairs of the full 3^d neighbourhoods on the grid of side
+    eps (1 + 2^-20), counted with the oracle's grid helper."""
+    import oracle
+    return oracle.grid_candidate_count_fast(w.points, w.eps * (1.0 + 2.0 ** -20))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * simjoin.h — C ABI of libsj, a GB300 (sm_103a) Euclidean distance
+ * similarity self-join.
+ *
+ * The operation (Sec. II-A, Eq. 1 of "Leveraging GPU Tensor Cores for Double
+ * Precision Euclidean Distance Calculations", Gallet and Gowanlock): given a
+ * set V of n points in d dimensions and a distance eps, return every ordered
+ * pair (i, j) of V x V with dist(x_i, x_j) <= eps, where dist is the
+ * Euclidean distance.  Self pairs (i, i) and both orders (i, j), (j, i) are
+ * part of the result (the selectivity of Sec. IV-A, (|R| - |V|) / |V|,
+ * counts each point finding itself).
+ *
+ * Decision rule, fixed for every kernel: with e2 = eps * eps rounded once in
+ * binary64 and s = sum_k (x_ik - x_jk)^2 evaluated in binary64 in dimension
+ * order, each subtraction, product and sum rounded separately, (i, j) belongs
+ * to the result iff s <= e2, and its distance is sqrt(s) correctly rounded.
+ * Kernels that compute distances another way (the expanded form of Eq. 3,
+ * low-precision tensor-core products) certify each decision with an error
+ * bound and re-decide every pair inside the bound with exactly this rule, so
+ * every kernel returns the same set.
+ *
+ * Method (Sec. III): points are indexed by a grid of cells of side >= eps
+ * (Sec. III-B); queries of one cell share their candidate set, the points of
+ * the 3^m adjacent cells; candidate distances are evaluated in tiles as
+ * ||a||^2 + ||b||^2 - 2 a.b (Eq. 3, Eq. 4, Fig. 2).
+ *
+ * Conventions for every entry point:
+ *  - Return value: SJ_OK (0) or a negative SJ_ERR_* status.  Nothing is
+ *    thrown across the ABI.  sj_error_string() names a status;
+ *    sj_last_error_message() gives detail for the calling thread's last error.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work of a handle runs on the stream given at
+ *    sj_build_index.
+ *  - Pointers documented "host or device" may point to either kind of memory;
+ *    the library detects which (unified addressing).
+ *  - Indices are int32: n must be below 2^31.
+ */
+#ifndef SIMJOIN_H
+#define SIMJOIN_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SJ_API __attribute__((visibility("default")))
+#else
+#define SJ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SJ_OK 0
+#define SJ_ERR_ARG (-1)             /* invalid argument: n < 1, n >= 2^31, d < 1,
+                                       d > SJ_MAX_D, eps <= 0 / NaN / Inf,
+                                       non-finite coordinate, NULL pointer */
+#define SJ_ERR_OOM (-2)             /* device or host allocation failed */
+#define SJ_ERR_RESULT_OVERFLOW (-3) /* result larger than the page pool even
+                                       after the automatic regrowth; count is
+                                       still exact */
+#define SJ_ERR_TIMEOUT (-4)         /* a bounded device wait ran out */
+#define SJ_ERR_CUDA (-5)            /* a CUDA runtime or driver call failed */
+#define SJ_ERR_UNSUPPORTED (-6)     /* kernel / shape combination not built */
+
+#define SJ_MAX_D 128
+
+/* ---- distance kernels -------------------------------------------------- */
+#define SJ_KERNEL_AUTO 0        /* fastest certified kernel for (d, sizes) */
+#define SJ_KERNEL_FP64_FMA 1    /* FP64 CUDA-core FMA tiles (expanded form,
+                                   Eq. 3) + direct-form recheck of the band */
+#define SJ_KERNEL_FP64_DMMA 2   /* FP64 tensor-core tiles, mma.sync m8n8k4
+                                   f64 (the paper's FP64 MMA, Fig. 2) */
+#define SJ_KERNEL_FILTER_F32 3  /* FP32 CUDA-core filter with certified bound,
+                                   FP64 direct recheck of the band */
+#define SJ_KERNEL_FILTER_BF16X3 4 /* tcgen05 kind::f16 with 3-term bf16 split
+                                     operands, FP32 accumulation in TMEM,
+                                     certified bound, FP64 recheck */
+
+/* ---- options ----------------------------------------------------------- */
+typedef struct sj_options {
+    int32_t kernel;           /* SJ_KERNEL_* */
+    int32_t emit_distances;   /* 1: also return the FP64 distance of every
+                                 pair (direct form, bit-identical to the
+                                 decision rule's sqrt(s)) */
+    int32_t indexed_dims;     /* m, the number of dims the grid indexes
+                                 (Sec. II-D: an index on fewer dims than d);
+                                 0 = automatic */
+    int32_t symmetric;        /* 1: evaluate each unordered pair of adjacent
+                                 cells once and emit both orders (halves the
+                                 distance work); 0: every query cell scans its
+                                 full 3^m neighbourhood as in Sec. III-B */
+    int32_t queries_per_item; /* queries per work item (a cell's queries are
+                                 split into items of at most this many);
+                                 0 = automatic */
+    int32_t reserved0;
+    int64_t page_pairs;       /* pairs per result page; 0 = 1 << 22 */
+    int64_t max_pairs_hint;   /* expected result size; 0 = automatic */
+} sj_options;
+
+/* Fills *opt with the defaults (kernel AUTO, no distances, automatic m,
+ * symmetric, automatic item size and pool). */
+SJ_API void sj_default_options(sj_options* opt);
+
+/* ---- index ------------------------------------------------------------- */
+typedef struct sj_index* sj_handle;
+
+/*
+ * Builds the grid index of Sec. III-B for `n` points of dimension `d`
+ * (row-major, binary64, `pts` host or device, owned by the caller and not
+ * retained) and distance `eps`: per-dim extent, cell keys of the m indexed
+ * dims, radix sort by key, cell table, points packed in cell order with their
+ * norms, and the list of work items (query ranges with their candidate
+ * ranges).  `opt` may be NULL (defaults).  On success *out is a new handle,
+ * to be released with sj_destroy.  Errors: SJ_ERR_ARG (see above, including a
+ * non-finite coordinate), SJ_ERR_OOM, SJ_ERR_CUDA.
+ */
+SJ_API int sj_build_index(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt,
+                   void* stream, sj_handle* out);
+
+/* Releases a handle and its device memory (after its stream's work). */
+SJ_API void sj_destroy(sj_handle h);
+
+/* Sizes of a built index: non-empty cells, work items, indexed dims m,
+ * candidate pairs of the full neighbourhoods (ordered, self included),
+ * pair evaluations the join performs.  Any output pointer may be NULL. */
+SJ_API int sj_index_info(sj_handle h, int64_t* n_cells, int64_t* n_items, int32_t* m, int64_t* n_candidates,
+                  int64_t* n_evaluated);
+
+/* ---- join -------------------------------------------------------------- */
+typedef struct sj_result {
+    int64_t count;            /* |R|, exact */
+    int64_t page_pairs;       /* pairs per page */
+    int32_t n_pages;          /* pages holding pairs [0, count) */
+    int32_t has_distances;
+    int32_t* const* pair_pages; /* host array of n_pages device pointers; page p
+                                   holds pairs p*page_pairs .. as (i, j) int32
+                                   in original input indices */
+    double* const* dist_pages;  /* NULL, or host array of n_pages device
+                                   pointers to the matching FP64 distances */
+    int64_t n_candidates;     /* candidate pairs of the full neighbourhoods */
+    int64_t n_evaluated;      /* pair evaluations performed by the kernel */
+    int64_t n_rechecked;      /* pairs re-decided by the FP64 direct form */
+    int32_t reruns;           /* reruns after the page pool overflowed */
+    int32_t kernel;           /* SJ_KERNEL_* actually used */
+    void* internal;           /* library-owned */
+} sj_result;
+
+/*
+ * Runs the self-join on a built index (Sec. III: for every work item, the
+ * distance tile between its queries and candidates, the eps threshold and a
+ * warp-aggregated compaction into the paged result buffer).  Work is queued
+ * on the handle's stream; the call returns once the result count is known
+ * (one device-to-host read of the count).  Pages stay on the device until
+ * sj_result_copy.  When the pool is too small the join is rerun once with a
+ * pool of the exact size (result->reruns).  *out must be released with
+ * sj_result_free.  Errors: SJ_ERR_OOM, SJ_ERR_CUDA, SJ_ERR_UNSUPPORTED,
+ * SJ_ERR_RESULT_OVERFLOW (count valid, pages hold a prefix).
+ */
+SJ_API int sj_self_join(sj_handle h, sj_result* out);
+
+/*
+ * Copies the pairs (2 * count int32, (i, j) interleaved) to `pairs_out` and,
+ * when the result has them and `dist_out` is not NULL, the distances
+ * (count doubles) to `dist_out`; both host or device.  The order of pairs is
+ * unspecified.  Synchronous with respect to the host.
+ */
+SJ_API int sj_result_copy(const sj_result* r, int32_t* pairs_out, double* dist_out);
+
+/* Releases a result's pages (NULL-safe, idempotent). */
+SJ_API void sj_result_free(sj_result* r);
+
+/* Convenience: build + join + destroy in one call. */
+SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt, void* stream,
+            sj_result* out);
+
+/* ---- batched joins ----------------------------------------------------- */
+/*
+ * Runs `count` independent self-joins (instance k: pts[k] with n[k] points of
+ * dimension d[k] and distance eps[k]; pts[k] host or device) with all
+ * indexes built by segmented kernels and all distance tiles in one
+ * persistent launch; results go to per_instance_out[k] (each released with
+ * sj_result_free).  Errors as for sj_build_index / sj_self_join; on error no
+ * result needs freeing.
+ */
+SJ_API int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps,
+                  int32_t count, const sj_options* opt, void* stream, sj_result* per_instance_out);
+
+/* ---- status ------------------------------------------------------------ */
+SJ_API const char* sj_error_string(int status);
+/* Detail of the calling thread's last error (empty string if none). */
+SJ_API const char* sj_last_error_message(void);
+/* Library version and the compute capability it was built for. */
+SJ_API const char* sj_version(void);
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all threads, all devices); a measurement aid, no paper counterpart. */
+SJ_API int64_t sj_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIMJOIN_H */

@@ -217,6 +217,31 @@ def grid_candidate_count(x, w: float, dims=None) -> int:
     return int(total)
 
 
+def grid_candidate_count_fast(x, w: float, dims=None) -> int:
+    """The same count as grid_candidate_count, vectorised over cells with
+    numpy: each cell's coordinates are shifted by each of the 3^m offsets,
+    encoded as integers and looked up in the sorted list of occupied cells."""
+    cells = grid_cells(x, w, dims)
+    n, m = cells.shape
+    uniq, cnt = np.unique(cells, axis=0, return_counts=True)
+    ext = uniq.max(axis=0) + 3
+    strides = np.ones(m, dtype=np.int64)
+    for k in range(m - 2, -1, -1):
+        strides[k] = strides[k + 1] * ext[k + 1]
+    codes = (uniq + 1) @ strides
+    order = np.argsort(codes)
+    codes_s, cnt_s = codes[order], cnt[order]
+    offs = np.array(np.meshgrid(*([[-1, 0, 1]] * m), indexing="ij")).reshape(m, -1).T
+    neigh = np.zeros(uniq.shape[0], dtype=np.int64)
+    for o in offs:
+        c = (uniq + 1 + o) @ strides
+        pos = np.searchsorted(codes_s, c)
+        pos_c = np.minimum(pos, codes_s.size - 1)
+        hit = codes_s[pos_c] == c
+        neigh += np.where(hit, cnt_s[pos_c], 0)
+    return int((cnt.astype(np.int64) * neigh).sum())
+
+
 def calibrate_eps(x, target: float, n_queries: int = 2000, seed: int = 12345) -> float:
     """eps whose mean neighbour count, self excluded (the selectivity s of
     Sec. IV-A), over ``n_queries`` seeded sample queries equals ``target``:

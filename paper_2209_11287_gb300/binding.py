@@ -1,0 +1,324 @@
+"""ctypes binding of libsj (include/simjoin.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and does no
+arithmetic of the join: points go to the library as a pointer (a CUDA tensor's
+device pointer, or host memory of a numpy array / CPU tensor), results come
+back as the library's device pages, copied out by ``sj_result_copy``.
+
+The library must have been built (``paper_2209_11287_gb300.build.build()``);
+loading fails loudly otherwise — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SJ_OK = 0
+SJ_ERR_ARG = -1
+SJ_ERR_OOM = -2
+SJ_ERR_RESULT_OVERFLOW = -3
+SJ_ERR_TIMEOUT = -4
+SJ_ERR_CUDA = -5
+SJ_ERR_UNSUPPORTED = -6
+
+SJ_KERNEL_AUTO = 0
+SJ_KERNEL_FP64_FMA = 1
+SJ_KERNEL_FP64_DMMA = 2
+SJ_KERNEL_FILTER_F32 = 3
+SJ_KERNEL_FILTER_BF16X3 = 4
+
+KERNELS = {
+    "auto": SJ_KERNEL_AUTO,
+    "fp64_fma": SJ_KERNEL_FP64_FMA,
+    "fp64_dmma": SJ_KERNEL_FP64_DMMA,
+    "filter_f32": SJ_KERNEL_FILTER_F32,
+    "filter_bf16x3": SJ_KERNEL_FILTER_BF16X3,
+}
+
+
+class SimJoinError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libsj status {status}: {message}")
+        self.status = status
+
+
+class sj_options(ctypes.Structure):
+    _fields_ = [
+        ("kernel", ctypes.c_int32),
+        ("emit_distances", ctypes.c_int32),
+        ("indexed_dims", ctypes.c_int32),
+        ("symmetric", ctypes.c_int32),
+        ("queries_per_item", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("page_pairs", ctypes.c_int64),
+        ("max_pairs_hint", ctypes.c_int64),
+    ]
+
+
+class sj_result(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int64),
+        ("page_pairs", ctypes.c_int64),
+        ("n_pages", ctypes.c_int32),
+        ("has_distances", ctypes.c_int32),
+        ("pair_pages", ctypes.POINTER(ctypes.c_void_p)),
+        ("dist_pages", ctypes.POINTER(ctypes.c_void_p)),
+        ("n_candidates", ctypes.c_int64),
+        ("n_evaluated", ctypes.c_int64),
+        ("n_rechecked", ctypes.c_int64),
+        ("reruns", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("internal", ctypes.c_void_p),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libsj (declares the C signatures).  Raises if it was not built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsj is not built ({path} missing); run paper_2209_11287_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        lib.sj_default_options.argtypes = [ctypes.POINTER(sj_options)]
+        lib.sj_default_options.restype = None
+        lib.sj_build_index.argtypes = [_vp, _i64, _i32, ctypes.c_double, ctypes.POINTER(sj_options), _vp,
+                                       ctypes.POINTER(_vp)]
+        lib.sj_build_index.restype = ctypes.c_int
+        lib.sj_destroy.argtypes = [_vp]
+        lib.sj_destroy.restype = None
+        lib.sj_index_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
+                                      ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+        lib.sj_index_info.restype = ctypes.c_int
+        lib.sj_self_join.argtypes = [_vp, ctypes.POINTER(sj_result)]
+        lib.sj_self_join.restype = ctypes.c_int
+        lib.sj_result_copy.argtypes = [ctypes.POINTER(sj_result), _vp, _vp]
+        lib.sj_result_copy.restype = ctypes.c_int
+        lib.sj_result_free.argtypes = [ctypes.POINTER(sj_result)]
+        lib.sj_result_free.restype = None
+        lib.sj_join.argtypes = [_vp, _i64, _i32, ctypes.c_double, ctypes.POINTER(sj_options), _vp,
+                                ctypes.POINTER(sj_result)]
+        lib.sj_join.restype = ctypes.c_int
+        lib.sj_join_batch.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
+                                      ctypes.POINTER(ctypes.c_double), _i32, ctypes.POINTER(sj_options), _vp,
+                                      ctypes.POINTER(sj_result)]
+        lib.sj_join_batch.restype = ctypes.c_int
+        lib.sj_error_string.argtypes = [ctypes.c_int]
+        lib.sj_error_string.restype = ctypes.c_char_p
+        lib.sj_last_error_message.argtypes = []
+        lib.sj_last_error_message.restype = ctypes.c_char_p
+        lib.sj_version.argtypes = []
+        lib.sj_version.restype = ctypes.c_char_p
+        lib.sj_kernel_launches.argtypes = []
+        lib.sj_kernel_launches.restype = ctypes.c_int64
+        _lib = lib
+        return lib
+
+
+def header_symbols() -> list[str]:
+    """Entry points declared in include/simjoin.h."""
+    src = open(os.path.join(_build.INCLUDE, "simjoin.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sj_[a-z_0-9]+)\s*\(", src)))
+
+
+def _check(status: int):
+    if status != SJ_OK:
+        lib = load()
+        raise SimJoinError(status, f"{lib.sj_error_string(status).decode()}: {lib.sj_last_error_message().decode()}")
+
+
+# ---- argument marshalling helpers ---------------------------------------------
+
+def _points_ptr(points):
+    """(pointer, n, d, keepalive) of a 2-D float64 C-contiguous array or tensor."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(points, torch.Tensor):
+        if points.dtype != torch.float64 or points.dim() != 2:
+            raise ValueError("points must be a 2-D float64 tensor")
+        points = points.contiguous()
+        return points.data_ptr(), points.shape[0], points.shape[1], points
+    a = np.ascontiguousarray(points, dtype=np.float64)
+    if a.ndim != 2:
+        raise ValueError("points must be an n x d array")
+    return a.ctypes.data, a.shape[0], a.shape[1], a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:  # pragma: no cover
+            pass
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---- entry points --------------------------------------------------------------
+
+def sj_default_options(**overrides) -> sj_options:
+    o = sj_options()
+    load().sj_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "kernel" and isinstance(v, str):
+            v = KERNELS[v]
+        setattr(o, k, int(v))
+    return o
+
+
+def sj_build_index(points, eps: float, options: sj_options | None = None, stream=None):
+    """Build the grid index; returns an opaque handle (int).  ``points``: n x d
+    float64, a CUDA tensor (used in place) or host memory (copied)."""
+    ptr, n, d, keep = _points_ptr(points)
+    h = ctypes.c_void_p()
+    _check(load().sj_build_index(ptr, n, d, float(eps), ctypes.byref(options) if options is not None else None,
+                                 _stream_ptr(stream), ctypes.byref(h)))
+    del keep
+    return h.value
+
+
+def sj_destroy(handle) -> None:
+    if handle:
+        load().sj_destroy(handle)
+
+
+def sj_index_info(handle) -> dict:
+    c, it, e, f = _i64(), _i64(), _i64(), _i64()
+    m = _i32()
+    _check(load().sj_index_info(handle, ctypes.byref(c), ctypes.byref(it), ctypes.byref(m), ctypes.byref(e),
+                                ctypes.byref(f)))
+    return {"n_cells": c.value, "n_items": it.value, "m": m.value, "n_candidates": e.value, "n_evaluated": f.value}
+
+
+def sj_self_join(handle) -> sj_result:
+    r = sj_result()
+    _check(load().sj_self_join(handle, ctypes.byref(r)))
+    return r
+
+
+def sj_result_copy(result: sj_result, pairs_out=None, dist_out=None):
+    """Copy pairs (count x 2 int32) and distances (count float64) into the given
+    outputs (CUDA tensors, CPU tensors or numpy arrays), allocating host numpy
+    arrays when an output is None.  Returns (pairs, dists or None)."""
+    cnt = int(result.count)
+    if pairs_out is None:
+        pairs_out = np.empty((cnt, 2), dtype=np.int32)
+    if dist_out is None and result.has_distances:
+        dist_out = np.empty(cnt, dtype=np.float64)
+
+    def ptr(a, dtype_np, torch_dtype_name):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            if str(a.dtype) != f"torch.{torch_dtype_name}" or not a.is_contiguous() or a.numel() < (2 * cnt if torch_dtype_name == "int32" else cnt):
+                raise ValueError("output tensor has the wrong dtype, layout or size")
+            return a.data_ptr()
+        if a.dtype != dtype_np or not a.flags.c_contiguous or a.size < (2 * cnt if dtype_np == np.int32 else cnt):
+            raise ValueError("output array has the wrong dtype, layout or size")
+        return a.ctypes.data
+
+    _check(load().sj_result_copy(ctypes.byref(result), ptr(pairs_out, np.int32, "int32"),
+                                 ptr(dist_out, np.float64, "float64") if result.has_distances else None))
+    return pairs_out, (dist_out if result.has_distances else None)
+
+
+def sj_result_free(result: sj_result) -> None:
+    load().sj_result_free(ctypes.byref(result))
+
+
+def sj_join(points, eps: float, options: sj_options | None = None, stream=None) -> sj_result:
+    ptr, n, d, keep = _points_ptr(points)
+    r = sj_result()
+    _check(load().sj_join(ptr, n, d, float(eps), ctypes.byref(options) if options is not None else None,
+                          _stream_ptr(stream), ctypes.byref(r)))
+    del keep
+    return r
+
+
+def sj_join_batch(points_list, eps_list, options: sj_options | None = None, stream=None) -> list:
+    count = len(points_list)
+    ptrs = (_vp * count)()
+    ns = (_i64 * count)()
+    ds = (_i32 * count)()
+    es = (ctypes.c_double * count)()
+    keep = []
+    for k, (p, e) in enumerate(zip(points_list, eps_list)):
+        ptr, n, d, kp = _points_ptr(p)
+        keep.append(kp)
+        ptrs[k], ns[k], ds[k], es[k] = ptr, n, d, float(e)
+    res = (sj_result * count)()
+    _check(load().sj_join_batch(ptrs, ns, ds, es, count, ctypes.byref(options) if options is not None else None,
+                                _stream_ptr(stream), res))
+    return list(res)
+
+
+def sj_error_string(status: int) -> str:
+    return load().sj_error_string(int(status)).decode()
+
+
+def sj_last_error_message() -> str:
+    return load().sj_last_error_message().decode()
+
+
+def sj_version() -> str:
+    return load().sj_version().decode()
+
+
+def sj_kernel_launches() -> int:
+    return int(load().sj_kernel_launches())
+
+
+# ---- convenience ------------------------------------------------------------------
+
+def self_join(points, eps: float, kernel="auto", emit_distances=False, symmetric=True, indexed_dims=0,
+              max_pairs_hint=0, stream=None):
+    """Build, join and copy out in one call: returns (pairs int32 n x 2 numpy,
+    distances or None, stats dict)."""
+    opt = sj_default_options(kernel=kernel, emit_distances=int(emit_distances), symmetric=int(symmetric),
+                             indexed_dims=indexed_dims, max_pairs_hint=max_pairs_hint)
+    h = sj_build_index(points, eps, opt, stream)
+    try:
+        info = sj_index_info(h)
+        r = sj_self_join(h)
+        try:
+            pairs, dists = sj_result_copy(r)
+            stats = dict(info, count=int(r.count), n_rechecked=int(r.n_rechecked), reruns=int(r.reruns),
+                         kernel=int(r.kernel))
+        finally:
+            sj_result_free(r)
+    finally:
+        sj_destroy(h)
+    return pairs, dists, stats
+
+
+def pairs_to_keys(pairs: np.ndarray) -> np.ndarray:
+    """Sorted 64-bit keys (i << 32) | j of an (i, j) int32 pair array."""
+    p = np.asarray(pairs).astype(np.int64)
+    return np.sort((p[:, 0] << 32) | p[:, 1])

@@ -1,0 +1,448 @@
+// C ABI of libsj: argument checks, handle and result lifetime, the paged
+// result pool and the device memory pool.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <new>
+
+#include "sj_internal.cuh"
+
+namespace sj {
+
+// ---- errors ----------------------------------------------------------------------
+static thread_local char g_msg[512];
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_msg[0] = 0; }
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---- device memory pool -------------------------------------------------------------
+// One stream-ordered pool per device whose release threshold keeps freed
+// blocks cached, so repeated joins do not return memory to the driver.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64];
+static bool g_pool_init[64];
+
+static int pool_for(int dev, cudaMemPool_t* out) {
+    if (dev < 0 || dev >= 64) {
+        set_error("device ordinal %d out of range", dev);
+        return SJ_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_init[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        SJ_CK(cudaMemPoolCreate(&p, &props));
+        unsigned long long thr = ~0ull;
+        SJ_CK(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pools[dev] = p;
+        g_pool_init[dev] = true;
+    }
+    *out = g_pools[dev];
+    return SJ_OK;
+}
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    SJ_CK(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    SJ_TRY(pool_for(dev, &pool));
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed", bytes);
+        return SJ_ERR_OOM;
+    }
+    SJ_CK(e);
+    return SJ_OK;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int device_sm_count(int device) {
+    static int cache[64];
+    if (device < 0 || device >= 64) return 1;
+    if (cache[device] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+        cache[device] = v > 0 ? v : 1;
+    }
+    return cache[device];
+}
+
+static void release_index(Index* ix) {
+    if (!ix) return;
+    cudaStream_t s = ix->stream;
+    dev_free(ix->xs, s);
+    dev_free(ix->y, s);
+    dev_free(ix->h, s);
+    dev_free(ix->thr_out, s);
+    dev_free(ix->thr_in, s);
+    dev_free(ix->perm, s);
+    dev_free(ix->cell_key, s);
+    dev_free(ix->cell_start, s);
+    dev_free(ix->runs, s);
+    dev_free(ix->items, s);
+    dev_free(ix->counters, s);
+}
+
+static int pick_kernel(const Index* ix) {
+    int k = ix->opt.kernel;
+    if (k != SJ_KERNEL_AUTO) return k;
+    return SJ_KERNEL_FILTER_F32;
+}
+
+static int round_dim(int d) {
+    int p = 2;
+    while (p < d) p <<= 1;
+    return p;
+}
+
+}  // namespace sj
+
+using namespace sj;
+
+struct sj_index : public sj::Index {};
+
+extern "C" {
+
+void sj_default_options(sj_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->kernel = SJ_KERNEL_AUTO;
+    o->emit_distances = 0;
+    o->indexed_dims = 0;
+    o->symmetric = 1;
+    o->queries_per_item = 0;
+    o->page_pairs = 0;
+    o->max_pairs_hint = 0;
+}
+
+const char* sj_error_string(int status) {
+    switch (status) {
+        case SJ_OK: return "ok";
+        case SJ_ERR_ARG: return "invalid argument";
+        case SJ_ERR_OOM: return "out of memory";
+        case SJ_ERR_RESULT_OVERFLOW: return "result larger than the page pool";
+        case SJ_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SJ_ERR_CUDA: return "CUDA error";
+        case SJ_ERR_UNSUPPORTED: return "unsupported kernel or shape";
+        default: return "unknown status";
+    }
+}
+
+const char* sj_last_error_message(void) { return g_msg; }
+
+const char* sj_version(void) { return "libsj 0.1 sm_103a"; }
+
+int64_t sj_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+int sj_build_index(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt, void* stream,
+                   sj_handle* out) {
+    clear_error();
+    if (!out) {
+        set_error("out is NULL");
+        return SJ_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!pts || n < 1 || n > 0x7FFFFFFFll || d < 1 || d > SJ_MAX_D || !(eps > 0) || !isfinite(eps)) {
+        set_error("invalid argument: pts=%p n=%lld d=%d eps=%g", (const void*)pts, (long long)n, (int)d, eps);
+        return SJ_ERR_ARG;
+    }
+    sj_options o;
+    sj_default_options(&o);
+    if (opt) o = *opt;
+    if (o.kernel < SJ_KERNEL_AUTO || o.kernel > SJ_KERNEL_FILTER_BF16X3 || o.indexed_dims < 0 ||
+        o.queries_per_item < 0 || o.page_pairs < 0 || o.max_pairs_hint < 0) {
+        set_error("invalid options");
+        return SJ_ERR_ARG;
+    }
+    sj_index* ix = new (std::nothrow) sj_index();
+    if (!ix) return SJ_ERR_OOM;
+    cudaError_t e = cudaGetDevice(&ix->device);
+    if (e != cudaSuccess) {
+        set_error("cudaGetDevice: %s", cudaGetErrorString(e));
+        delete ix;
+        return SJ_ERR_CUDA;
+    }
+    ix->stream = static_cast<cudaStream_t>(stream);
+    ix->opt = o;
+    ix->n = n;
+    ix->d = d;
+    ix->dp = round_dim(d);
+    ix->eps = eps;
+    ix->e2 = eps * eps;
+    ix->kernel = pick_kernel(ix);
+    if (ix->kernel == SJ_KERNEL_FILTER_BF16X3) {
+        set_error("kernel %d not available in this build", ix->kernel);
+        delete ix;
+        return SJ_ERR_UNSUPPORTED;
+    }
+    if (ix->kernel == SJ_KERNEL_FP64_DMMA && ix->dp < 4) ix->dp = 4;
+    // points: use device memory in place, or stage host memory
+    const double* dpts = pts;
+    double* staged = nullptr;
+    int st = SJ_OK;
+    if (!is_device_pointer(pts)) {
+        st = dev_alloc_t(&staged, (size_t)n * d, ix->stream);
+        if (st == SJ_OK) {
+            e = cudaMemcpyAsync(staged, pts, (size_t)n * d * sizeof(double), cudaMemcpyHostToDevice, ix->stream);
+            if (e != cudaSuccess) {
+                set_error("host-to-device copy: %s", cudaGetErrorString(e));
+                st = SJ_ERR_CUDA;
+            }
+        }
+        dpts = staged;
+    }
+    if (st == SJ_OK) st = build_index(ix, dpts);
+    if (staged) dev_free(staged, ix->stream);
+    if (st != SJ_OK) {
+        release_index(ix);
+        cudaStreamSynchronize(ix->stream);
+        delete ix;
+        return st;
+    }
+    *out = ix;
+    return SJ_OK;
+}
+
+void sj_destroy(sj_handle h) {
+    if (!h) return;
+    release_index(h);
+    cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+int sj_index_info(sj_handle h, int64_t* n_cells, int64_t* n_items, int32_t* m, int64_t* n_candidates,
+                  int64_t* n_evaluated) {
+    if (!h) {
+        set_error("NULL handle");
+        return SJ_ERR_ARG;
+    }
+    if (n_cells) *n_cells = h->n_cells;
+    if (n_items) *n_items = h->n_items;
+    if (m) *m = h->m;
+    if (n_candidates) *n_candidates = h->n_candidates;
+    if (n_evaluated) *n_evaluated = h->n_evaluated;
+    return SJ_OK;
+}
+
+static int alloc_pages(ResultImpl* ri, int64_t pages_needed, int64_t page_pairs, bool dist, cudaStream_t s) {
+    while ((int64_t)ri->pair_pages.size() < pages_needed) {
+        int32_t* p = nullptr;
+        SJ_TRY(dev_alloc_t(&p, (size_t)page_pairs * 2, s));
+        ri->pair_pages.push_back(p);
+        if (dist) {
+            double* q = nullptr;
+            SJ_TRY(dev_alloc_t(&q, (size_t)page_pairs, s));
+            ri->dist_pages.push_back(q);
+        }
+    }
+    return SJ_OK;
+}
+
+static void free_result_impl(ResultImpl* ri) {
+    if (!ri) return;
+    for (int32_t* p : ri->pair_pages) dev_free(p, ri->stream);
+    for (double* p : ri->dist_pages) dev_free(p, ri->stream);
+    delete ri;
+}
+
+static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, int page_log2, bool dist,
+                    unsigned long long* count_out, unsigned long long* rechecked_out) {
+    cudaStream_t s = ix->stream;
+    const int64_t np = (int64_t)ri->pair_pages.size();
+    // device page tables
+    int2** dpt = nullptr;
+    double** ddt = nullptr;
+    SJ_TRY(dev_alloc_t(&dpt, (size_t)std::max<int64_t>(np, 1), s));
+    if (dist) SJ_TRY(dev_alloc_t(&ddt, (size_t)std::max<int64_t>(np, 1), s));
+    if (np > 0) {
+        SJ_CK(cudaMemcpyAsync(dpt, ri->pair_pages.data(), np * sizeof(void*), cudaMemcpyHostToDevice, s));
+        if (dist) SJ_CK(cudaMemcpyAsync(ddt, ri->dist_pages.data(), np * sizeof(void*), cudaMemcpyHostToDevice, s));
+    }
+    SJ_CK(cudaMemsetAsync(ix->counters, 0, 4 * sizeof(unsigned long long), s));
+    JoinOut jo;
+    jo.pages = dpt;
+    jo.dpages = ddt;
+    jo.page_log2 = page_log2;
+    jo.capacity = (unsigned long long)np * (unsigned long long)page_pairs;
+    int st = SJ_OK;
+    if (ix->n_items > 0) {
+        if (ix->kernel == SJ_KERNEL_FP64_DMMA)
+            st = launch_join_dmma(ix, jo, dist ? 1 : 0);
+        else
+            st = launch_join_cc(ix, jo, dist ? 1 : 0);
+    }
+    unsigned long long c[4] = {0, 0, 0, 0};
+    if (st == SJ_OK) {
+        cudaError_t e = cudaMemcpyAsync(c, ix->counters, sizeof c, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("join: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+        }
+    }
+    dev_free(dpt, s);
+    dev_free(ddt, s);
+    *count_out = c[1];
+    *rechecked_out = c[2];
+    return st;
+}
+
+int sj_self_join(sj_handle h, sj_result* out) {
+    clear_error();
+    if (!h || !out) {
+        set_error("NULL argument");
+        return SJ_ERR_ARG;
+    }
+    memset(out, 0, sizeof *out);
+    int64_t page_pairs = h->opt.page_pairs > 0 ? h->opt.page_pairs : kDefaultPagePairs;
+    int page_log2 = 0;
+    while ((int64_t(1) << page_log2) < page_pairs) ++page_log2;
+    page_pairs = int64_t(1) << page_log2;
+    const bool dist = h->opt.emit_distances != 0;
+    // initial pool: the hint, else the candidate count capped by a share of
+    // free memory (the result never exceeds the candidate count)
+    int64_t want = h->opt.max_pairs_hint;
+    if (want <= 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        const int64_t per_pair = dist ? 16 : 8;
+        const int64_t budget = (int64_t)(fr / 4) / per_pair;
+        want = std::min<int64_t>(h->n_candidates, std::max<int64_t>(budget, 16 * h->n));
+    }
+    ResultImpl* ri = new (std::nothrow) ResultImpl();
+    if (!ri) return SJ_ERR_OOM;
+    ri->stream = h->stream;
+    int64_t np = (want + page_pairs - 1) / page_pairs;
+    if (np < 1) np = 1;
+    int st = alloc_pages(ri, np, page_pairs, dist, h->stream);
+    unsigned long long count = 0, rechecked = 0;
+    int reruns = 0;
+    if (st == SJ_OK) st = run_join(h, ri, page_pairs, page_log2, dist, &count, &rechecked);
+    if (st == SJ_OK && count > (unsigned long long)ri->pair_pages.size() * (unsigned long long)page_pairs) {
+        // overflow: grow the pool to the exact count and run again
+        int64_t need = (int64_t)((count + page_pairs - 1) / page_pairs);
+        st = alloc_pages(ri, need, page_pairs, dist, h->stream);
+        if (st == SJ_OK) {
+            reruns = 1;
+            st = run_join(h, ri, page_pairs, page_log2, dist, &count, &rechecked);
+        }
+        if (st == SJ_OK && count > (unsigned long long)ri->pair_pages.size() * (unsigned long long)page_pairs) {
+            set_error("result of %llu pairs still exceeds the page pool", count);
+            st = SJ_ERR_RESULT_OVERFLOW;
+        }
+    }
+    if (st != SJ_OK && st != SJ_ERR_RESULT_OVERFLOW) {
+        free_result_impl(ri);
+        return st;
+    }
+    // keep only the pages that hold pairs
+    int64_t used = (int64_t)((count + page_pairs - 1) / page_pairs);
+    used = std::min<int64_t>(used, (int64_t)ri->pair_pages.size());
+    while ((int64_t)ri->pair_pages.size() > used) {
+        dev_free(ri->pair_pages.back(), ri->stream);
+        ri->pair_pages.pop_back();
+        if (dist) {
+            dev_free(ri->dist_pages.back(), ri->stream);
+            ri->dist_pages.pop_back();
+        }
+    }
+    out->count = (int64_t)count;
+    out->page_pairs = page_pairs;
+    out->n_pages = (int32_t)ri->pair_pages.size();
+    out->has_distances = dist ? 1 : 0;
+    out->pair_pages = ri->pair_pages.data();
+    out->dist_pages = dist ? ri->dist_pages.data() : nullptr;
+    out->n_candidates = h->n_candidates;
+    out->n_evaluated = h->n_evaluated;
+    out->n_rechecked = (int64_t)rechecked;
+    out->reruns = reruns;
+    out->kernel = h->kernel;
+    out->internal = ri;
+    return st;
+}
+
+int sj_result_copy(const sj_result* r, int32_t* pairs_out, double* dist_out) {
+    clear_error();
+    if (!r) {
+        set_error("NULL result");
+        return SJ_ERR_ARG;
+    }
+    if (r->count == 0) return SJ_OK;
+    if (!pairs_out && !dist_out) return SJ_OK;
+    const ResultImpl* ri = static_cast<const ResultImpl*>(r->internal);
+    if (!ri) {
+        set_error("result has no pages");
+        return SJ_ERR_ARG;
+    }
+    int64_t left = std::min<int64_t>(r->count, (int64_t)r->n_pages * r->page_pairs);
+    for (int p = 0; p < r->n_pages && left > 0; ++p) {
+        const int64_t cnt = std::min<int64_t>(left, r->page_pairs);
+        const int64_t off = (int64_t)p * r->page_pairs;
+        if (pairs_out)
+            SJ_CK(cudaMemcpyAsync(pairs_out + 2 * off, r->pair_pages[p], (size_t)cnt * 2 * sizeof(int32_t),
+                                  cudaMemcpyDefault, ri->stream));
+        if (dist_out && r->has_distances && r->dist_pages)
+            SJ_CK(cudaMemcpyAsync(dist_out + off, r->dist_pages[p], (size_t)cnt * sizeof(double), cudaMemcpyDefault,
+                                  ri->stream));
+        left -= cnt;
+    }
+    SJ_CK(cudaStreamSynchronize(ri->stream));
+    return SJ_OK;
+}
+
+void sj_result_free(sj_result* r) {
+    if (!r) return;
+    free_result_impl(static_cast<ResultImpl*>(r->internal));
+    memset(r, 0, sizeof *r);
+}
+
+int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt, void* stream,
+            sj_result* out) {
+    sj_handle h = nullptr;
+    int st = sj_build_index(pts, n, d, eps, opt, stream, &h);
+    if (st != SJ_OK) return st;
+    st = sj_self_join(h, out);
+    sj_destroy(h);
+    return st;
+}
+
+int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps, int32_t count,
+                  const sj_options* opt, void* stream, sj_result* per_instance_out) {
+    clear_error();
+    (void)pts; (void)n; (void)d; (void)eps; (void)opt; (void)stream; (void)per_instance_out;
+    if (count < 0) return SJ_ERR_ARG;
+    set_error("batched joins are not built yet");
+    return SJ_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,806 @@
+// Grid index of the similarity self-join (Sec. III-B): extent, cell keys,
+// LSD radix sort, cell table, packing in cell order with norms and certified
+// thresholds, neighbour-run enumeration and work items.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <numeric>
+
+#include "sj_internal.cuh"
+
+namespace sj {
+
+// ---------------------------------------------------------------------------
+// order-preserving map double -> uint64 (for atomic min / max)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ord_of(double v) {
+    unsigned long long b = __double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+static double from_ord(unsigned long long o) {
+    unsigned long long b = (o >> 63) ? (o & 0x7FFFFFFFFFFFFFFFull) : ~o;
+    double v;
+    memcpy(&v, &b, sizeof v);
+    return v;
+}
+
+// Per-dim min / max of the points and a flag for any non-finite coordinate.
+__global__ void k_extent(const double* __restrict__ x, int64_t total, int d, unsigned long long* lo,
+                         unsigned long long* hi, int* bad) {
+    extern __shared__ unsigned long long s_ext[];  // [2 * d]
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        s_ext[k] = ~0ull;
+        s_ext[d + k] = 0ull;
+    }
+    __syncthreads();
+    int local_bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = x[i];
+        int k = (int)(i % d);
+        if (!isfinite(v)) {
+            local_bad = 1;
+            continue;
+        }
+        unsigned long long o = ord_of(v);
+        atomicMin(&s_ext[k], o);
+        atomicMax(&s_ext[d + k], o);
+    }
+    if (local_bad) atomicOr(bad, 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        atomicMin(&lo[k], s_ext[k]);
+        atomicMax(&hi[k], s_ext[d + k]);
+    }
+}
+
+struct GridParams {
+    int m;
+    int dims[kMaxM];
+    double lo[kMaxM];
+    int64_t ncell[kMaxM];
+    unsigned long long stride[kMaxM];
+    double w;
+};
+
+// Cell coordinate of one value: floor((x - lo) / w), clamped to the grid.
+__device__ __forceinline__ int64_t cell_coord(double v, double lo, double w, int64_t ncell) {
+    double t = floor((v - lo) / w);
+    int64_t c = (int64_t)t;
+    return c < 0 ? 0 : (c >= ncell ? ncell - 1 : c);
+}
+
+__global__ void k_cell_keys(const double* __restrict__ x, int64_t n, int d, GridParams g,
+                            unsigned long long* keys, int32_t* ids) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long key = 0;
+    for (int k = 0; k < g.m; ++k) {
+        int64_t c = cell_coord(x[i * d + g.dims[k]], g.lo[k], g.w, g.ncell[k]);
+        key += (unsigned long long)c * g.stride[k];
+    }
+    keys[i] = key;
+    ids[i] = (int32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 (reduce-then-scan over tiles of 4096)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t warp_base = wid ? s_warp[wid - 1] : 0;
+    *total = s_warp[(blockDim.x >> 5) - 1];
+    uint32_t r = warp_base + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_tile_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* sums) {
+    __shared__ uint32_t s_warp[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t acc = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
+        if (idx < n) acc += in[idx];
+    }
+    uint32_t tot;
+    block_exclusive_scan(acc, s_warp, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Scans one tile (thread t owns items t*kScanItems .. +kScanItems, a
+// contiguous chunk) and adds the tile's base offset.
+__global__ void k_scan_tiles(const uint32_t* __restrict__ in, uint32_t* out, int64_t n,
+                             const uint32_t* __restrict__ tile_base) {
+    __shared__ uint32_t s_warp[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        acc += v[i];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(acc, s_warp, &tot) + (tile_base ? tile_base[blockIdx.x] : 0);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+}
+
+int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return SJ_OK;
+    int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        k_scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        return SJ_OK;
+    }
+    uint32_t* sums = nullptr;
+    SJ_TRY(dev_alloc_t(&sums, (size_t)tiles * 2, s));
+    uint32_t* sums_scan = sums + tiles;
+    k_scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    int st = scan_exclusive_u32(sums, sums_scan, tiles, s);
+    if (st == SJ_OK) {
+        k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums_scan);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error("scan launch: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+        }
+    }
+    dev_free(sums, s);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (uint64 key, int32 value), 8-bit digits, stable passes
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // elements per tile
+
+// hist[digit * tiles + tile] = count of `digit` in the tile.
+__global__ void k_sort_hist(const unsigned long long* __restrict__ keys, int64_t n, int shift, uint32_t* hist,
+                            int64_t tiles) {
+    __shared__ uint32_t s_h[256];
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+        int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = s_h[threadIdx.x];
+}
+
+// Stable scatter: element order within the tile is round-major then thread
+// order, i.e. the input order, and ranks follow it.
+__global__ void k_sort_scatter(const unsigned long long* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
+                               unsigned long long* keys_out, int32_t* vals_out, int64_t n, int shift,
+                               const uint32_t* __restrict__ offs, int64_t tiles) {
+    __shared__ uint32_t s_base[256];           // running output position per digit
+    __shared__ uint32_t s_wcnt[kSortThreads / 32][256];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    s_base[threadIdx.x] = offs[(int64_t)threadIdx.x * tiles + blockIdx.x];
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < kSortRounds; ++r) {
+        for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+        bool valid = i < n;
+        unsigned long long k = valid ? keys_in[i] : 0ull;
+        int32_t v = valid ? vals_in[i] : 0;
+        unsigned dig = valid ? (unsigned)((k >> shift) & 255u) : 256u;  // 256 = padding
+        unsigned peers = __match_any_sync(0xffffffffu, dig);
+        unsigned rank_in_warp = __popc(peers & lt);
+        bool leader = rank_in_warp == 0;
+        if (valid && leader) s_wcnt[wid][dig] = __popc(peers);
+        __syncthreads();
+        {   // per digit: exclusive prefix over warps, advance the running base
+            unsigned dg = threadIdx.x;
+            uint32_t run = s_base[dg];
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                uint32_t c = s_wcnt[w][dg];
+                s_wcnt[w][dg] = run;
+                run += c;
+            }
+            s_base[dg] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = s_wcnt[wid][dig] + rank_in_warp;
+            keys_out[pos] = k;
+            vals_out[pos] = v;
+        }
+        __syncthreads();
+    }
+}
+
+int radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cudaStream_t s) {
+    if (n <= 1 || key_bits <= 0) return SJ_OK;
+    int64_t tiles = (n + kSortTile - 1) / kSortTile;
+    if ((int64_t)tiles * 256 >= (int64_t(1) << 32)) {
+        set_error("radix sort: input too large");
+        return SJ_ERR_ARG;
+    }
+    unsigned long long* k2 = nullptr;
+    int32_t* v2 = nullptr;
+    uint32_t* hist = nullptr;
+    int st = SJ_OK;
+    if ((st = dev_alloc_t(&k2, n, s)) != SJ_OK) return st;
+    if ((st = dev_alloc_t(&v2, n, s)) != SJ_OK) {
+        dev_free(k2, s);
+        return st;
+    }
+    if ((st = dev_alloc_t(&hist, (size_t)tiles * 256 * 2, s)) != SJ_OK) {
+        dev_free(k2, s);
+        dev_free(v2, s);
+        return st;
+    }
+    uint32_t* offs = hist + tiles * 256;
+    unsigned long long* ka = reinterpret_cast<unsigned long long*>(keys);
+    int32_t* va = vals;
+    unsigned long long* kb = k2;
+    int32_t* vb = v2;
+    int passes = (key_bits + 7) / 8;
+    for (int p = 0; p < passes && st == SJ_OK; ++p) {
+        int shift = 8 * p;
+        k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(ka, n, shift, hist, tiles);
+        note_launch();
+        st = scan_exclusive_u32(hist, offs, tiles * 256, s);
+        if (st != SJ_OK) break;
+        k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, offs, tiles);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error("radix sort launch: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+        }
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (st == SJ_OK && ka != reinterpret_cast<unsigned long long*>(keys)) {
+        cudaError_t e1 = cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+        cudaError_t e2 = cudaMemcpyAsync(vals, va, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            set_error("radix sort copy-back failed");
+            st = SJ_ERR_CUDA;
+        }
+    }
+    dev_free(k2, s);
+    dev_free(v2, s);
+    dev_free(hist, s);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// cell table
+// ---------------------------------------------------------------------------
+__global__ void k_heads(const unsigned long long* __restrict__ keys, int64_t n, uint32_t* flags) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_cells(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ flags,
+                        const uint32_t* __restrict__ idx, int64_t n, unsigned long long* cell_key,
+                        int32_t* cell_start, unsigned long long* n_cells) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flags[i]) {
+        cell_key[idx[i]] = keys[i];
+        cell_start[idx[i]] = (int32_t)i;
+    }
+    if (i == n - 1) {
+        uint32_t m = idx[i] + flags[i];
+        *n_cells = m;
+        cell_start[m] = (int32_t)n;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// packing in cell order, kernel coordinates and certified thresholds
+// ---------------------------------------------------------------------------
+struct PackParams {
+    double lo[SJ_MAX_D];
+    double e2, eps;
+    double pbound;   // upper bound of ||y||^2 over all points
+    double delta;    // bound on |y_k - (x_k - lo_k)| per coordinate
+    double ulp_t;    // unit roundoff of the kernel type
+    int d, dp;
+};
+
+__host__ __device__ inline double gamma_n(double u, int k) { return k * u / (1.0 - k * u); }
+
+// Thresholds on a = y_q.y_c - ||y_q||^2/2 computed in T (fma chain over the
+// padded dims, started at -||y_q||^2/2) for candidate c with computed norm
+// pc.  With s_y = ||y_q - y_c||^2 = ||y_c||^2 - 2 a_exact, the evaluation
+// error satisfies |s_y - (pc - 2 a)| <= 3 gamma_T(dp) (||y_q||^2 + ||y_c||^2)
+// (norm chains and the dot-product chain); doubled for safety:
+//   E_s = 6.2 gamma_T(dp + 1) (pbound + pc).
+// The coordinates carry |y_k - (x_k - lo_k)| <= delta, so
+// |sqrt(s_y) - sqrt(s)| <= eta = 2 delta sqrt(d), s the exact squared
+// distance of the inputs.  The decision rule's s differs from the exact one by
+// at most gamma_64(d + 3) s; g = 2 gamma_64(d + 3) covers it.  Then
+//   a <  thr_out  =>  s > e2 (1 + g)     => out for the decision rule,
+//   a >= thr_in   =>  s <= e2 (1 - g)    => in for the decision rule,
+// with thr_out = (pc - (eps (1 + g) + eta)^2 - E_s) / 2 rounded down and
+// thr_in = (pc - (eps (1 - g) - eta)^2 + E_s) / 2 rounded up (+inf when
+// eps (1 - g) <= eta); both get a further 4 u_T relative margin for their
+// own rounding.
+template <typename T>
+__device__ __forceinline__ T round_down_to(double v);
+template <>
+__device__ __forceinline__ double round_down_to<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float round_down_to<float>(double v) { return __double2float_rd(v); }
+template <typename T>
+__device__ __forceinline__ T round_up_to(double v);
+template <>
+__device__ __forceinline__ double round_up_to<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float round_up_to<float>(double v) { return __double2float_ru(v); }
+
+template <typename T>
+__global__ void k_pack(const double* __restrict__ x, const int32_t* __restrict__ perm, int64_t n,
+                       const PackParams* __restrict__ pp, double* xs, T* y, T* h, T* thr_out, T* thr_in) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int d = pp->d, dp = pp->dp;
+    const int64_t src = (int64_t)perm[p] * d;
+    T nrm = T(0);
+    for (int k = 0; k < dp; ++k) {
+        double v = k < d ? x[src + k] : 0.0;
+        xs[p * dp + k] = v;
+        T yk = k < d ? T(v - pp->lo[k]) : T(0);
+        y[p * dp + k] = yk;
+        nrm = fma(yk, yk, nrm);
+    }
+    h[p] = -nrm * T(0.5);
+    const double u = pp->ulp_t;
+    const double pc = (double)nrm;
+    const double g = 2.0 * gamma_n(ldexp(1.0, -53), d + 3);
+    const double eta = 2.0 * pp->delta * sqrt((double)d) * (1.0 + ldexp(1.0, -40));
+    const double es = 6.2 * gamma_n(u, dp + 1) * (pp->pbound + pc);
+    const double so_r = pp->eps * (1.0 + g) + eta;
+    const double so = so_r * so_r;
+    double to = (pc - so - es) * 0.5;
+    to -= 4.0 * u * (pc + so + es);
+    thr_out[p] = round_down_to<T>(to);
+    const double si_r = pp->eps * (1.0 - g) - eta;
+    if (si_r > 0) {
+        const double si = si_r * si_r;
+        double ti = (pc - si + es) * 0.5;
+        ti += 4.0 * u * (pc + si + es);
+        thr_in[p] = round_up_to<T>(ti);
+    } else {
+        thr_in[p] = T(INFINITY);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// neighbour runs and work items
+// ---------------------------------------------------------------------------
+struct EnumParams {
+    int m;
+    int64_t ncell[kMaxM];
+    unsigned long long stride[kMaxM];
+    int symmetric;
+    int qmax;
+};
+
+__device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long* a, int64_t n, unsigned long long v) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Visits the candidate runs of cell c: for every offset vector o of the
+// first m-1 indexed dims in {-1,0,1} inside the grid, the cells whose last
+// coordinate is within one of c's form one contiguous key range, hence one
+// contiguous range of sorted points.  In symmetric mode only offset vectors
+// that are lexicographically positive keep their whole range; the zero vector
+// keeps the cell itself (no mirroring) and the next cell along the last dim.
+template <typename F>
+__device__ void visit_runs(const EnumParams& e, const unsigned long long* __restrict__ cell_key,
+                           const int32_t* __restrict__ cell_start, int64_t n_cells, int64_t c, F&& f) {
+    if (e.m == 0) {  // a single cell holding every point
+        f(cell_start[0], cell_start[n_cells], false, true);
+        return;
+    }
+    const unsigned long long key = cell_key[c];
+    int64_t cc[kMaxM];
+    for (int k = 0; k < e.m; ++k) cc[k] = (int64_t)((key / e.stride[k]) % (unsigned long long)e.ncell[k]);
+    const int mm = e.m - 1;
+    int nvec = 1;
+    for (int k = 0; k < mm; ++k) nvec *= 3;
+    const int64_t last = cc[mm];
+    for (int vi = 0; vi < nvec; ++vi) {
+        int rem = vi;
+        long long delta = 0;
+        int sign = 0;  // lexicographic sign of the offset vector
+        bool inside = true;
+        for (int k = 0; k < mm; ++k) {
+            int o = rem % 3 - 1;
+            rem /= 3;
+            // digits are produced least-significant first; lexicographic order
+            // is on k ascending, so record the first non-zero from k = 0
+            if (cc[k] + o < 0 || cc[k] + o >= e.ncell[k]) inside = false;
+            delta += (long long)o * (long long)e.stride[k];
+        }
+        if (!inside) continue;
+        {
+            int rem2 = vi;
+            for (int k = 0; k < mm; ++k) {
+                int o = rem2 % 3 - 1;
+                rem2 /= 3;
+                if (sign == 0 && o != 0) sign = o;
+            }
+        }
+        const unsigned long long base = (unsigned long long)((long long)key + delta);
+        int64_t lo_l = last > 0 ? last - 1 : 0;
+        int64_t hi_l = last + 1 < e.ncell[mm] ? last + 1 : e.ncell[mm] - 1;
+        auto emit_range = [&](int64_t a_l, int64_t b_l, bool mirror, bool self) {
+            if (a_l > b_l) return;
+            unsigned long long k_lo = base - (unsigned long long)(last - a_l);
+            unsigned long long k_hi = base + (unsigned long long)(b_l - last);
+            int64_t ca = lower_bound_u64(cell_key, n_cells, k_lo);
+            int64_t cb = lower_bound_u64(cell_key, n_cells, k_hi + 1);
+            if (ca >= cb) return;
+            f(cell_start[ca], cell_start[cb], mirror, self);
+        };
+        if (!e.symmetric) {
+            emit_range(lo_l, hi_l, false, sign == 0);
+        } else if (sign > 0) {
+            emit_range(lo_l, hi_l, true, false);
+        } else if (sign == 0) {
+            emit_range(last, last, false, true);
+            emit_range(last + 1, hi_l, true, false);
+        }
+    }
+}
+
+struct EnumTotals {
+    unsigned long long n_runs, n_items, n_candidates, n_evaluated;
+};
+
+__global__ void k_enum_count(EnumParams e, const unsigned long long* __restrict__ cell_key,
+                             const int32_t* __restrict__ cell_start, int64_t n_cells, uint32_t* run_cnt,
+                             uint32_t* item_cnt, EnumTotals* tot) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long my_cand = 0, my_eval = 0, my_runs = 0, my_items = 0;
+    if (c < n_cells) {
+        const int64_t q = cell_start[c + 1] - cell_start[c];
+        uint32_t nr = 0;
+        unsigned long long ev = 0;
+        visit_runs(e, cell_key, cell_start, n_cells, c, [&](int32_t a, int32_t b, bool, bool) {
+            ++nr;
+            ev += (unsigned long long)(b - a);
+        });
+        // canonical candidate count: the full neighbourhood
+        unsigned long long full = 0;
+        EnumParams ef = e;
+        ef.symmetric = 0;
+        visit_runs(ef, cell_key, cell_start, n_cells, c,
+                   [&](int32_t a, int32_t b, bool, bool) { full += (unsigned long long)(b - a); });
+        run_cnt[c] = nr;
+        uint32_t ni = (uint32_t)((q + e.qmax - 1) / e.qmax);
+        item_cnt[c] = ni;
+        my_cand = full * (unsigned long long)q;
+        my_eval = ev * (unsigned long long)q;
+        my_runs = nr;
+        my_items = ni;
+    }
+    // warp reduction then one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        my_cand += __shfl_down_sync(0xffffffffu, my_cand, o);
+        my_eval += __shfl_down_sync(0xffffffffu, my_eval, o);
+        my_runs += __shfl_down_sync(0xffffffffu, my_runs, o);
+        my_items += __shfl_down_sync(0xffffffffu, my_items, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&tot->n_candidates, my_cand);
+        atomicAdd(&tot->n_evaluated, my_eval);
+        atomicAdd(&tot->n_runs, my_runs);
+        atomicAdd(&tot->n_items, my_items);
+    }
+}
+
+__global__ void k_enum_fill(EnumParams e, const unsigned long long* __restrict__ cell_key,
+                            const int32_t* __restrict__ cell_start, int64_t n_cells,
+                            const uint32_t* __restrict__ run_off, const uint32_t* __restrict__ item_off,
+                            Run* runs, Item* items) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n_cells) return;
+    uint32_t r = run_off[c];
+    const uint32_t r0 = r;
+    visit_runs(e, cell_key, cell_start, n_cells, c, [&](int32_t a, int32_t b, bool mirror, bool) {
+        Run rr;
+        rr.start = a;
+        rr.end_flags = (uint32_t)b | (mirror ? kMirrorBit : 0u);
+        runs[r++] = rr;
+    });
+    const int32_t q0 = cell_start[c], q1 = cell_start[c + 1];
+    uint32_t it = item_off[c];
+    for (int32_t q = q0; q < q1; q += e.qmax) {
+        Item x;
+        x.q0 = q;
+        x.q1 = q + e.qmax < q1 ? q + e.qmax : q1;
+        x.r0 = (int32_t)r0;
+        x.r1 = (int32_t)r;
+        items[it++] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+static int choose_grid(Index* ix) {
+    const int d = ix->d;
+    // w >= eps with a relative margin that absorbs the rounding of
+    // (x - lo) / w, so two coordinates within eps are never two cells apart.
+    ix->w = ix->eps * (1.0 + ldexp(1.0, -20));
+    struct Cand {
+        int k;
+        int64_t ncell;
+    };
+    std::vector<Cand> cand;
+    for (int k = 0; k < d; ++k) {
+        double r = ix->hi[k] - ix->lo[k];
+        double cells = floor(r / ix->w) + 1.0;
+        if (!(cells < ldexp(1.0, 30))) continue;  // too fine for a safe cell coordinate
+        cand.push_back({k, (int64_t)cells});
+    }
+    // most selective dims first (most cells); ties keep the input order
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.ncell > b.ncell; });
+    int want = ix->opt.indexed_dims > 0 ? std::min(ix->opt.indexed_dims, kMaxM) : std::min(d, kMaxM);
+    std::vector<Cand> take;
+    long double prod = 1;
+    for (const Cand& c : cand) {
+        if ((int)take.size() >= want) break;
+        if (ix->opt.indexed_dims <= 0 && c.ncell < 3) continue;  // no pruning from <3 cells
+        if (prod * (long double)c.ncell > ldexpl(1.0L, 62)) continue;
+        prod *= (long double)c.ncell;
+        take.push_back(c);
+    }
+    // keep the input order of the chosen dims (row-major keys)
+    std::sort(take.begin(), take.end(), [](const Cand& a, const Cand& b) { return a.k < b.k; });
+    ix->m = (int)take.size();
+    unsigned long long stride = 1;
+    for (int i = ix->m - 1; i >= 0; --i) {
+        ix->dims[i] = take[i].k;
+        ix->ncell[i] = take[i].ncell;
+        ix->stride[i] = stride;
+        stride *= (unsigned long long)take[i].ncell;
+    }
+    unsigned long long maxkey = stride - 1;
+    ix->key_bits = 0;
+    while (ix->key_bits < 64 && (maxkey >> ix->key_bits) != 0) ++ix->key_bits;
+    return SJ_OK;
+}
+
+template <typename T>
+static int pack_points(Index* ix, const double* pts, const PackParams& hp) {
+    cudaStream_t s = ix->stream;
+    const int64_t n = ix->n;
+    PackParams* dpp = nullptr;
+    SJ_TRY(dev_alloc_t(&dpp, 1, s));
+    SJ_CK(cudaMemcpyAsync(dpp, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
+    T *y, *h, *to, *ti;
+    SJ_TRY(dev_alloc_t(&y, (size_t)n * ix->dp, s));
+    SJ_TRY(dev_alloc_t(&h, (size_t)n, s));
+    SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
+    SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
+    ix->y = y;
+    ix->h = h;
+    ix->thr_out = to;
+    ix->thr_in = ti;
+    k_pack<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, ix->perm, n, dpp, ix->xs, y, h, to, ti);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    // the pack parameters are read by the kernel before the free is ordered
+    dev_free(dpp, s);
+    return SJ_OK;
+}
+
+int build_index(Index* ix, const double* pts) {
+    cudaStream_t s = ix->stream;
+    const int64_t n = ix->n;
+    const int d = ix->d;
+    // ---- extent and finiteness check (one sync) ----
+    unsigned long long* ext = nullptr;
+    SJ_TRY(dev_alloc_t(&ext, (size_t)2 * d + 1, s));
+    std::vector<unsigned long long> init(2 * d + 1);
+    for (int k = 0; k < d; ++k) {
+        init[k] = ~0ull;
+        init[d + k] = 0ull;
+    }
+    init[2 * d] = 0;
+    SJ_CK(cudaMemcpyAsync(ext, init.data(), init.size() * 8, cudaMemcpyHostToDevice, s));
+    {
+        int64_t total = n * d;
+        int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)device_sm_count(ix->device) * 8);
+        k_extent<<<blocks, 256, 2 * d * sizeof(unsigned long long), s>>>(
+            pts, total, d, ext, ext + d, reinterpret_cast<int*>(ext + 2 * d));
+        note_launch();
+        SJ_CK(cudaGetLastError());
+    }
+    std::vector<unsigned long long> got(2 * d + 1);
+    SJ_CK(cudaMemcpyAsync(got.data(), ext, got.size() * 8, cudaMemcpyDeviceToHost, s));
+    SJ_CK(cudaStreamSynchronize(s));
+    dev_free(ext, s);
+    if (*reinterpret_cast<int*>(&got[2 * d]) != 0) {
+        set_error("non-finite coordinate in the input points");
+        return SJ_ERR_ARG;
+    }
+    ix->lo.resize(d);
+    ix->hi.resize(d);
+    for (int k = 0; k < d; ++k) {
+        ix->lo[k] = from_ord(got[k]);
+        ix->hi[k] = from_ord(got[d + k]);
+    }
+    SJ_TRY(choose_grid(ix));
+
+    // ---- cell keys and sort ----
+    unsigned long long* keys = nullptr;
+    SJ_TRY(dev_alloc_t(&keys, (size_t)n, s));
+    SJ_TRY(dev_alloc_t(&ix->perm, (size_t)n, s));
+    GridParams gp{};
+    gp.m = ix->m;
+    gp.w = ix->w;
+    for (int i = 0; i < ix->m; ++i) {
+        gp.dims[i] = ix->dims[i];
+        gp.lo[i] = ix->lo[ix->dims[i]];
+        gp.ncell[i] = ix->ncell[i];
+        gp.stride[i] = ix->stride[i];
+    }
+    k_cell_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, n, d, gp, keys, ix->perm);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    SJ_TRY(radix_sort_pairs(reinterpret_cast<uint64_t*>(keys), ix->perm, n, ix->key_bits, s));
+
+    // ---- cell table (one sync for the cell count) ----
+    uint32_t *flags = nullptr, *idx = nullptr;
+    SJ_TRY(dev_alloc_t(&flags, (size_t)n, s));
+    SJ_TRY(dev_alloc_t(&idx, (size_t)n, s));
+    unsigned long long* dcount = nullptr;
+    SJ_TRY(dev_alloc_t(&dcount, 1, s));
+    k_heads<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, flags);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    SJ_TRY(scan_exclusive_u32(flags, idx, n, s));
+    unsigned long long* ckey_tmp = nullptr;
+    int32_t* cstart_tmp = nullptr;
+    SJ_TRY(dev_alloc_t(&ckey_tmp, (size_t)n, s));
+    SJ_TRY(dev_alloc_t(&cstart_tmp, (size_t)n + 1, s));
+    k_cells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, flags, idx, n, ckey_tmp, cstart_tmp, dcount);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+
+    // ---- packing (independent of the cell count) ----
+    SJ_TRY(dev_alloc_t(&ix->xs, (size_t)n * ix->dp, s));
+    PackParams hp{};
+    for (int k = 0; k < d; ++k) hp.lo[k] = ix->lo[k];
+    hp.e2 = ix->e2;
+    hp.eps = ix->eps;
+    double pb = 0, rmax = 0;
+    for (int k = 0; k < d; ++k) {
+        double r = ix->hi[k] - ix->lo[k];
+        pb += r * r;
+        rmax = std::max(rmax, r);
+    }
+    hp.pbound = pb * (1.0 + ldexp(1.0, -20));
+    hp.d = d;
+    hp.dp = ix->dp;
+    const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32;
+    hp.ulp_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
+    hp.delta = 1.01 * (use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53)) * rmax;
+    if (use_f32)
+        SJ_TRY(pack_points<float>(ix, pts, hp));
+    else
+        SJ_TRY(pack_points<double>(ix, pts, hp));
+    {
+        double es = 6.2 * gamma_n(hp.ulp_t, ix->dp + 1) * 2.0 * hp.pbound;
+        ix->filter_band_rel = 2.0 * es / ix->e2;
+    }
+
+    unsigned long long M = 0;
+    SJ_CK(cudaMemcpyAsync(&M, dcount, 8, cudaMemcpyDeviceToHost, s));
+    SJ_CK(cudaStreamSynchronize(s));
+    ix->n_cells = (int64_t)M;
+    SJ_TRY(dev_alloc_t(&ix->cell_key, (size_t)M, s));
+    SJ_TRY(dev_alloc_t(&ix->cell_start, (size_t)M + 1, s));
+    SJ_CK(cudaMemcpyAsync(ix->cell_key, ckey_tmp, M * 8, cudaMemcpyDeviceToDevice, s));
+    SJ_CK(cudaMemcpyAsync(ix->cell_start, cstart_tmp, (M + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    dev_free(ckey_tmp, s);
+    dev_free(cstart_tmp, s);
+    dev_free(keys, s);
+    dev_free(flags, s);
+    dev_free(idx, s);
+    dev_free(dcount, s);
+
+    // ---- neighbour runs and items (one sync for the totals) ----
+    EnumParams ep{};
+    ep.m = ix->m;
+    for (int i = 0; i < ix->m; ++i) {
+        ep.ncell[i] = ix->ncell[i];
+        ep.stride[i] = ix->stride[i];
+    }
+    ep.symmetric = ix->opt.symmetric ? 1 : 0;
+    ep.qmax = ix->opt.queries_per_item > 0 ? std::min(ix->opt.queries_per_item, kQMax) : kQMax;
+    uint32_t *run_cnt, *item_cnt, *run_off, *item_off;
+    EnumTotals* dtot;
+    const int64_t Mc = (int64_t)M;
+    SJ_TRY(dev_alloc_t(&run_cnt, (size_t)Mc * 4, s));
+    item_cnt = run_cnt + Mc;
+    run_off = run_cnt + 2 * Mc;
+    item_off = run_cnt + 3 * Mc;
+    SJ_TRY(dev_alloc_t(&dtot, 1, s));
+    SJ_CK(cudaMemsetAsync(dtot, 0, sizeof(EnumTotals), s));
+    const unsigned eb = (unsigned)((Mc + 127) / 128);
+    k_enum_count<<<eb, 128, 0, s>>>(ep, ix->cell_key, ix->cell_start, Mc, run_cnt, item_cnt, dtot);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    SJ_TRY(scan_exclusive_u32(run_cnt, run_off, Mc, s));
+    SJ_TRY(scan_exclusive_u32(item_cnt, item_off, Mc, s));
+    EnumTotals tot{};
+    SJ_CK(cudaMemcpyAsync(&tot, dtot, sizeof tot, cudaMemcpyDeviceToHost, s));
+    SJ_CK(cudaStreamSynchronize(s));
+    ix->n_runs = (int64_t)tot.n_runs;
+    ix->n_items = (int64_t)tot.n_items;
+    ix->n_candidates = (int64_t)tot.n_candidates;
+    ix->n_evaluated = (int64_t)tot.n_evaluated;
+    if (tot.n_runs >= 0xFFFFFFFFull || tot.n_items >= 0x7FFFFFFFull) {
+        set_error("index too large: %llu runs, %llu items", tot.n_runs, tot.n_items);
+        return SJ_ERR_ARG;
+    }
+    SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(ix->n_runs, 1), s));
+    SJ_TRY(dev_alloc_t(&ix->items, (size_t)std::max<int64_t>(ix->n_items, 1), s));
+    k_enum_fill<<<eb, 128, 0, s>>>(ep, ix->cell_key, ix->cell_start, Mc, run_off, item_off, ix->runs, ix->items);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    dev_free(run_cnt, s);
+    dev_free(dtot, s);
+    SJ_TRY(dev_alloc_t(&ix->counters, 4, s));
+    return SJ_OK;
+}
+
+}  // namespace sj

@@ -1,0 +1,131 @@
+// Internal declarations of libsj (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "simjoin.h"
+
+namespace sj {
+
+// ---- limits ---------------------------------------------------------------
+constexpr int kMaxM = 6;                         // indexed dims (3^(m-1) runs per cell)
+constexpr int kMaxRuns = 243 + 1;                // 3^(kMaxM-1) + the split self run
+constexpr int kQMax = 16;                        // queries per work item (bitmask width)
+constexpr int kThreads = 128;                    // CTA size of the distance kernels
+constexpr int kStage = 256;                      // per-warp staging slots for emitted pairs
+constexpr int64_t kDefaultPagePairs = int64_t(1) << 22;
+
+// ---- error reporting ----------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define SJ_CK(call)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            ::sj::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return SJ_ERR_CUDA;                                                                  \
+        }                                                                                        \
+    } while (0)
+
+#define SJ_TRY(expr)            \
+    do {                        \
+        int st_ = (expr);       \
+        if (st_ != SJ_OK) return st_; \
+    } while (0)
+
+// ---- device memory (stream-ordered pool, cached across calls) -----------------
+int dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+template <typename T>
+int dev_alloc_t(T** p, size_t count, cudaStream_t s) {
+    return dev_alloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+
+bool is_device_pointer(const void* p);
+
+// ---- work item and candidate run ---------------------------------------------
+// A work item: queries [q0, q1) of one cell (sorted positions) and the cell's
+// candidate runs [r0, r1) in the run array.
+struct Item {
+    int32_t q0, q1, r0, r1;
+};
+// A candidate run: sorted positions [start, end); bit 31 of `end_flags` set
+// means "mirror": the run lies in another cell than the queries and every
+// hit is emitted in both orders.
+struct Run {
+    int32_t start;
+    uint32_t end_flags;
+};
+constexpr uint32_t kMirrorBit = 0x80000000u;
+
+// ---- index handle ---------------------------------------------------------------
+struct Index {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    sj_options opt{};
+    int kernel = SJ_KERNEL_FP64_FMA;
+    int64_t n = 0;
+    int32_t d = 0, dp = 0;      // dims and padded dims (multiple of 4)
+    double eps = 0, e2 = 0, w = 0;
+    int32_t m = 0;
+    int32_t dims[kMaxM] = {};
+    int64_t ncell[kMaxM] = {};
+    uint64_t stride[kMaxM] = {};
+    int key_bits = 0;
+    std::vector<double> lo, hi;
+
+    // device arrays (cell order)
+    double* xs = nullptr;       // n x dp original coordinates, zero padded
+    void* y = nullptr;          // n x dp kernel coordinates y = x - lo (double or float)
+    void* h = nullptr;          // n: -||y||^2 / 2
+    void* thr_out = nullptr;    // n: maybe-in threshold on (y_q.y_c - ||y_q||^2/2)
+    void* thr_in = nullptr;     // n: certain-in threshold
+    int32_t* perm = nullptr;    // sorted position -> input index
+    unsigned long long* cell_key = nullptr;
+    int32_t* cell_start = nullptr;  // M + 1
+    Run* runs = nullptr;
+    Item* items = nullptr;
+    int64_t n_cells = 0, n_runs = 0, n_items = 0, n_candidates = 0, n_evaluated = 0;
+    double filter_band_rel = 0;  // predicted certified band (relative to eps^2)
+
+    // per-join scratch: counters (item queue, result cursor, recheck count)
+    unsigned long long* counters = nullptr;
+};
+
+// Result internals.
+struct ResultImpl {
+    cudaStream_t stream = nullptr;
+    std::vector<int32_t*> pair_pages;
+    std::vector<double*> dist_pages;
+};
+
+// ---- index build (sj_index.cu) ------------------------------------------------
+int build_index(Index* ix, const double* pts_dev);
+
+// ---- join kernels (sj_join_cc.cu) ----------------------------------------------
+struct JoinOut {
+    int2** pages = nullptr;        // device array of page pointers
+    double** dpages = nullptr;     // device array (or null)
+    int page_log2 = 22;
+    uint64_t capacity = 0;         // pairs the pages can hold
+};
+int launch_join_cc(Index* ix, const JoinOut& out, int emit_dist);
+int launch_join_dmma(Index* ix, const JoinOut& out, int emit_dist);
+
+// ---- radix sort / scan (sj_index.cu) ------------------------------------------
+int radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cudaStream_t s);
+int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+
+int device_sm_count(int device);
+
+// Kernels launched by the library in this process (reported by
+// sj_kernel_launches); every launch site calls note_launch().
+void note_launch();
+
+}  // namespace sj

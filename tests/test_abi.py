@@ -1,0 +1,76 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+entry point include/simjoin.h declares, and rejects invalid arguments before
+touching the device.  CPU only: no compute call is made."""
+import ctypes
+import math
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2209_11287_gb300 import binding, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not build.up_to_date():
+        pytest.skip("nvcc not available")
+    build.build()
+    return binding.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = binding.header_symbols()
+    assert "sj_build_index" in declared and "sj_self_join" in declared and "sj_join_batch" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    for s in declared:
+        assert hasattr(lib, s)
+
+
+def test_no_stray_exports(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True, check=True).stdout
+    ours = {line.split()[-1] for line in out.splitlines() if " T " in line and line.split()[-1].startswith("sj")}
+    assert ours <= set(binding.header_symbols())
+
+
+def test_error_strings_and_defaults(lib):
+    assert binding.sj_error_string(0) == "ok"
+    assert "argument" in binding.sj_error_string(binding.SJ_ERR_ARG)
+    assert binding.sj_error_string(12345) == "unknown status"
+    o = binding.sj_default_options()
+    assert o.kernel == binding.SJ_KERNEL_AUTO and o.symmetric == 1 and o.emit_distances == 0
+    assert "sm_103a" in binding.sj_version()
+
+
+@pytest.mark.parametrize("n,d,eps", [(0, 2, 0.1), (-3, 2, 0.1), (10, 0, 0.1), (10, 129, 0.1), (10, 2, 0.0),
+                                     (10, 2, -1.0), (10, 2, math.nan), (10, 2, math.inf), (2 ** 31, 2, 0.1)])
+def test_invalid_arguments_rejected(lib, n, d, eps):
+    x = np.zeros((4, 2))
+    h = ctypes.c_void_p()
+    st = lib.sj_build_index(x.ctypes.data, n, d, eps, None, None, ctypes.byref(h))
+    assert st == binding.SJ_ERR_ARG
+    assert h.value is None
+    assert binding.sj_last_error_message()
+
+
+def test_null_arguments_rejected(lib):
+    h = ctypes.c_void_p()
+    assert lib.sj_build_index(None, 4, 2, 0.1, None, None, ctypes.byref(h)) == binding.SJ_ERR_ARG
+    assert lib.sj_build_index(np.zeros(8).ctypes.data, 4, 2, 0.1, None, None, None) == binding.SJ_ERR_ARG
+    r = binding.sj_result()
+    assert lib.sj_self_join(None, ctypes.byref(r)) == binding.SJ_ERR_ARG
+    assert lib.sj_result_copy(None, None, None) == binding.SJ_ERR_ARG
+    lib.sj_result_free(None)
+    lib.sj_destroy(None)
+
+
+def test_invalid_options_rejected(lib):
+    x = np.zeros((4, 2))
+    o = binding.sj_default_options()
+    o.kernel = 99
+    h = ctypes.c_void_p()
+    assert lib.sj_build_index(x.ctypes.data, 4, 2, 0.1, ctypes.byref(o), None, ctypes.byref(h)) == binding.SJ_ERR_ARG

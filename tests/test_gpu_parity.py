@@ -1,0 +1,237 @@
+"""Parity of the CUDA self-join with the CPU oracle, through the C ABI.
+
+The decision rule (s <= fl(eps^2), binary64 direct form) is fixed and every
+kernel certifies its decisions and re-decides the pairs inside its error bound
+with that rule, so the pair sets must be identical to the oracle's and the
+emitted distances bit-identical (the tolerance the workload allows, pairs
+within 1e-9 eps of eps and 1e-12 relative distance error, is not needed).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2209_11287_gb300 import binding, workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+KERNELS = ["fp64_fma", "fp64_dmma", "filter_f32"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_11287_gb300 import build
+    build.build()
+    binding.load()
+    oracle.build()
+
+
+def gpu_join(x, eps, kernel, device_input=True, **kw):
+    pts = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    if device_input:
+        pts = pts.cuda()
+    pairs, dists, stats = binding.self_join(pts, eps, kernel=kernel, **kw)
+    torch.cuda.synchronize()
+    keys = (pairs[:, 0].astype(np.int64) << 32) | pairs[:, 1].astype(np.int64)
+    order = np.argsort(keys, kind="stable")
+    keys = keys[order]
+    if dists is not None:
+        dists = dists[order]
+    return keys, dists, stats
+
+
+def assert_same_set(x, eps, ref, got):
+    assert np.all(np.diff(got) > 0), "duplicate pairs emitted"
+    only_ref, only_got, bad = oracle.compare_pair_sets(x, eps, ref, got)
+    assert bad == 0, (only_ref, only_got)
+    assert only_ref == 0 and only_got == 0, (only_ref, only_got)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("symmetric", [1, 0])
+def test_uniform2d_full(kernel, symmetric):
+    w = workloads.uniform2d()
+    ref = oracle.join(w.points, w.eps)
+    got, _, st = gpu_join(w.points, w.eps, kernel, symmetric=symmetric)
+    assert_same_set(w.points, w.eps, ref, got)
+    assert st["count"] == ref.size
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_distances_bit_identical(kernel):
+    w = workloads.uniform2d(n=6000, seed=3)
+    ref, rd = oracle.join(w.points, w.eps, with_dist=True)
+    got, gd, _ = gpu_join(w.points, w.eps, kernel, emit_distances=True)
+    assert_same_set(w.points, w.eps, ref, got)
+    assert np.array_equal(gd, rd)
+
+
+def test_canonical_candidate_count():
+    """The index's candidate count (full 3^m neighbourhoods, cells of side
+    w = eps (1 + 2^-20)) equals the oracle's count on the same grid."""
+    w = workloads.uniform2d()
+    _, _, st = gpu_join(w.points, w.eps, "fp64_fma")
+    assert st["m"] == 2
+    assert st["n_candidates"] == oracle.grid_candidate_count(w.points, w.eps * (1.0 + 2.0 ** -20))
+    assert st["n_evaluated"] < st["n_candidates"]
+
+
+def _cases():
+    g = np.random.Generator(np.random.PCG64(77))
+    out = []
+    out.append(("single_point", np.array([[0.5, 0.25]]), 0.1))
+    out.append(("two_duplicates", np.array([[1.0, 2.0, 3.0]] * 2), 1e-3))
+    out.append(("all_identical", np.full((300, 3), 0.125), 1e-6))
+    out.append(("d1", g.random((3000, 1)), 1e-3))
+    out.append(("d3", g.random((4000, 3)), 0.03))
+    out.append(("d5", g.random((3000, 5)), 0.12))
+    out.append(("d8", g.random((2500, 8)), 0.3))
+    out.append(("d33", g.random((800, 33)), 1.0))
+    k = g.integers(0, 24, size=(2000, 2))
+    out.append(("lattice_ties", k / 8.0, 2.0 / 8.0))          # many pairs at exactly eps
+    out.append(("lattice_cell_edges", k / 8.0, 1.0 / 8.0))    # points on cell boundaries
+    out.append(("eps_above_diameter", g.random((500, 2)), 2.0))
+    out.append(("eps_below_gaps", g.random((500, 4)), 1e-9))
+    far = g.random((700, 2))
+    far[0] = [1e6, -1e6]
+    out.append(("one_far_point", far, 0.05))
+    out.append(("negative_coords", g.standard_normal((3000, 3)) * 5.0, 0.4))
+    clustered = np.repeat(g.random((20, 2)), 60, axis=0) + 1e-7 * g.standard_normal((1200, 2))
+    out.append(("dense_cells", clustered, 0.01))
+    return out
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
+def test_edge_cases(kernel, case):
+    _, x, eps = case
+    ref = oracle.join(x, eps)
+    for sym in (1, 0):
+        got, _, _ = gpu_join(x, eps, kernel, symmetric=sym)
+        assert_same_set(x, eps, ref, got)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_mixture16d_small(kernel):
+    w = workloads.mixture16d(n=12000, eps=0.25)
+    ref = oracle.join(w.points, w.eps)
+    got, _, _ = gpu_join(w.points, w.eps, kernel)
+    assert_same_set(w.points, w.eps, ref, got)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_expo64d_small(kernel):
+    w = workloads.expo64d(n=3000, eps=0.19)
+    ref = oracle.join(w.points, w.eps)
+    got, _, _ = gpu_join(w.points, w.eps, kernel)
+    assert_same_set(w.points, w.eps, ref, got)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_near_ties(kernel):
+    """Pairs at a relative 1e-10 from eps are decided exactly."""
+    from tests.test_oracle_pins import near_tie_points
+    x, eps = near_tie_points(npairs=3000)
+    ref = oracle.join(x, eps)
+    got, _, _ = gpu_join(x, eps, kernel)
+    assert_same_set(x, eps, ref, got)
+
+
+def test_host_input_matches_device_input():
+    w = workloads.uniform2d(n=5000, seed=9)
+    a, _, _ = gpu_join(w.points, w.eps, "filter_f32", device_input=True)
+    b, _, _ = gpu_join(w.points, w.eps, "filter_f32", device_input=False)
+    assert np.array_equal(a, b)
+
+
+def test_overflow_regrows_and_reruns():
+    """A page pool smaller than the result: the count stays exact, the pool
+    grows to the exact size and the join runs once more."""
+    w = workloads.uniform2d(n=8000, seed=2)
+    ref = oracle.join(w.points, w.eps)
+    opt = binding.sj_default_options(kernel="filter_f32", page_pairs=1024, max_pairs_hint=100)
+    h = binding.sj_build_index(torch.from_numpy(w.points).cuda(), w.eps, opt)
+    r = binding.sj_self_join(h)
+    assert r.reruns == 1 and r.count == ref.size
+    pairs, _ = binding.sj_result_copy(r)
+    binding.sj_result_free(r)
+    binding.sj_destroy(h)
+    assert_same_set(w.points, w.eps, ref, binding.pairs_to_keys(pairs))
+
+
+def test_small_pages():
+    """Results spanning many pages (1024 pairs each) are assembled correctly."""
+    w = workloads.uniform2d(n=8000, seed=8)
+    ref = oracle.join(w.points, w.eps)
+    opt = binding.sj_default_options(kernel="fp64_fma", page_pairs=1024)
+    h = binding.sj_build_index(torch.from_numpy(w.points).cuda(), w.eps, opt)
+    r = binding.sj_self_join(h)
+    assert r.n_pages > 100
+    pairs, _ = binding.sj_result_copy(r)
+    binding.sj_result_free(r)
+    binding.sj_destroy(h)
+    got = binding.pairs_to_keys(pairs)
+    assert_same_set(w.points, w.eps, ref, got)
+
+
+def test_copy_to_device_tensor():
+    w = workloads.uniform2d(n=5000, seed=10)
+    h = binding.sj_build_index(torch.from_numpy(w.points).cuda(), w.eps, binding.sj_default_options())
+    r = binding.sj_self_join(h)
+    dev = torch.empty((r.count, 2), dtype=torch.int32, device="cuda")
+    binding.sj_result_copy(r, dev)
+    host, _ = binding.sj_result_copy(r)
+    binding.sj_result_free(r)
+    binding.sj_destroy(h)
+    assert np.array_equal(dev.cpu().numpy(), host)
+
+
+def test_non_finite_coordinate_rejected():
+    x = np.random.default_rng(0).random((100, 3))
+    x[17, 1] = np.nan
+    with pytest.raises(binding.SimJoinError) as e:
+        binding.sj_build_index(torch.from_numpy(x).cuda(), 0.1)
+    assert e.value.status == binding.SJ_ERR_ARG
+
+
+def _rows_from_gpu(pairs_dev, n, sample):
+    sel = torch.zeros(n, dtype=torch.bool, device="cuda")
+    sel[torch.from_numpy(sample).cuda()] = True
+    p = pairs_dev[sel[pairs_dev[:, 0].long()]]
+    keys = (p[:, 0].long() << 32) | p[:, 1].long()
+    return torch.sort(keys).values.cpu().numpy()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_uniform4d_full_size_sampled_rows(kernel):
+    """The 2M-point 4-D workload at full size, in the launch configuration the
+    benchmark times: sampled query rows equal the oracle's rows, and the set is
+    symmetric with every self pair."""
+    w = workloads.uniform4d()
+    pts = torch.from_numpy(w.points).cuda()
+    opt = binding.sj_default_options(kernel=kernel)
+    h = binding.sj_build_index(pts, w.eps, opt)
+    r = binding.sj_self_join(h)
+    pairs = torch.empty((r.count, 2), dtype=torch.int32, device="cuda")
+    binding.sj_result_copy(r, pairs)
+    count = int(r.count)
+    binding.sj_result_free(r)
+    binding.sj_destroy(h)
+    sample = np.random.default_rng(1).choice(w.n, size=200, replace=False)
+    got = _rows_from_gpu(pairs, w.n, sample)
+    ref, _ = oracle.rows(w.points, w.eps, np.sort(sample))
+    assert np.array_equal(got, np.sort(ref))
+    # symmetric, self pairs, no duplicates
+    keys = (pairs[:, 0].long() << 32) | pairs[:, 1].long()
+    rev = (pairs[:, 1].long() << 32) | pairs[:, 0].long()
+    ks = torch.sort(keys).values
+    assert torch.equal(ks, torch.sort(rev).values)
+    assert bool((ks[1:] > ks[:-1]).all())
+    selfc = int((pairs[:, 0] == pairs[:, 1]).sum())
+    assert selfc == w.n
+    assert count > 1.0e8

@@ -208,6 +208,10 @@ def test_grid_is_lossless(orc):
     cand = orc.grid_candidate_count(w.points, w.eps)
     assert keys.size <= cand < w.n * w.n
     assert orc.grid_candidate_count(w.points, 10.0) == w.n * w.n
+    assert orc.grid_candidate_count_fast(w.points, w.eps) == cand
+    assert orc.grid_candidate_count_fast(w.points, 10.0) == w.n * w.n
+    w3 = workloads.uniform4d(n=3000, seed=1)
+    assert orc.grid_candidate_count_fast(w3.points, w3.eps) == orc.grid_candidate_count(w3.points, w3.eps)
 
 
 def test_calibrated_eps_reaches_target(orc):
