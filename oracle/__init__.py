@@ -187,14 +187,16 @@ def compare_pair_sets(x, eps: float, ref_keys, got_keys, rel: float = 1e-9):
 # --------------------------------------------------------------------------
 
 def grid_cells(x, w: float, dims=None) -> np.ndarray:
-    """Integer cell coordinates floor((x_k - lo_k) / w) over the indexed dims,
-    lo_k the minimum of dim k (one binary64 subtraction and one division)."""
+    """Integer cell coordinates floor((x_k - lo_k) * (1 / w)) over the indexed
+    dims, lo_k the minimum of dim k (binary64: 1 / w rounded once, then one
+    subtraction and one product per coordinate)."""
     x = _pts(x)
     if dims is None:
         dims = list(range(x.shape[1]))
     sub = x[:, dims]
     lo = sub.min(axis=0)
-    return np.floor((sub - lo) / w).astype(np.int64)
+    inv_w = 1.0 / float(w)
+    return np.floor((sub - lo) * inv_w).astype(np.int64)
 
 
 def grid_candidate_count(x, w: float, dims=None) -> int:

@@ -82,3 +82,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+
+
+def build_peaks() -> str:
+    """Build the arithmetic-throughput micro-benchmark (peaks/sj_peaks.cu) as
+    the executable _build/sj_peaks."""
+    os.makedirs(BUILD, exist_ok=True)
+    src = os.path.join(HERE, "peaks", "sj_peaks.cu")
+    exe = os.path.join(BUILD, "sj_peaks")
+    if os.path.exists(exe) and os.path.getmtime(exe) >= os.path.getmtime(src):
+        return exe
+    subprocess.run([_nvcc(), *ARCH, "-O3", "-std=c++17", "-o", exe, src], check=True)
+    return exe

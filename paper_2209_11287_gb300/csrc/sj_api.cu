@@ -254,52 +254,57 @@ int sj_index_info(sj_handle h, int64_t* n_cells, int64_t* n_items, int32_t* m, i
     return SJ_OK;
 }
 
+// The page pool is one allocation sliced into pages (one pool call per join
+// instead of one per page); growing it replaces the allocation.
 static int alloc_pages(ResultImpl* ri, int64_t pages_needed, int64_t page_pairs, bool dist, cudaStream_t s) {
-    while ((int64_t)ri->pair_pages.size() < pages_needed) {
-        int32_t* p = nullptr;
-        SJ_TRY(dev_alloc_t(&p, (size_t)page_pairs * 2, s));
-        ri->pair_pages.push_back(p);
-        if (dist) {
-            double* q = nullptr;
-            SJ_TRY(dev_alloc_t(&q, (size_t)page_pairs, s));
-            ri->dist_pages.push_back(q);
-        }
+    if ((int64_t)ri->pair_pages.size() >= pages_needed) return SJ_OK;
+    dev_free(ri->block, s);
+    dev_free(ri->dblock, s);
+    ri->block = nullptr;
+    ri->dblock = nullptr;
+    ri->pair_pages.clear();
+    ri->dist_pages.clear();
+    SJ_TRY(dev_alloc_t(&ri->block, (size_t)pages_needed * page_pairs * 2, s));
+    if (dist) SJ_TRY(dev_alloc_t(&ri->dblock, (size_t)pages_needed * page_pairs, s));
+    for (int64_t p = 0; p < pages_needed; ++p) {
+        ri->pair_pages.push_back(ri->block + p * page_pairs * 2);
+        if (dist) ri->dist_pages.push_back(ri->dblock + p * page_pairs);
     }
     return SJ_OK;
 }
 
 static void free_result_impl(ResultImpl* ri) {
     if (!ri) return;
-    for (int32_t* p : ri->pair_pages) dev_free(p, ri->stream);
-    for (double* p : ri->dist_pages) dev_free(p, ri->stream);
+    dev_free(ri->block, ri->stream);
+    dev_free(ri->dblock, ri->stream);
     delete ri;
 }
 
-static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, int page_log2, bool dist,
-                    unsigned long long* count_out, unsigned long long* rechecked_out) {
+static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist, unsigned long long* count_out,
+                    unsigned long long* rechecked_out) {
     cudaStream_t s = ix->stream;
     const int64_t np = (int64_t)ri->pair_pages.size();
-    // device page tables
-    int2** dpt = nullptr;
-    double** ddt = nullptr;
-    SJ_TRY(dev_alloc_t(&dpt, (size_t)std::max<int64_t>(np, 1), s));
-    if (dist) SJ_TRY(dev_alloc_t(&ddt, (size_t)std::max<int64_t>(np, 1), s));
-    if (np > 0) {
-        SJ_CK(cudaMemcpyAsync(dpt, ri->pair_pages.data(), np * sizeof(void*), cudaMemcpyHostToDevice, s));
-        if (dist) SJ_CK(cudaMemcpyAsync(ddt, ri->dist_pages.data(), np * sizeof(void*), cudaMemcpyHostToDevice, s));
-    }
     SJ_CK(cudaMemsetAsync(ix->counters, 0, 4 * sizeof(unsigned long long), s));
+    // deferred-recheck queue: band pairs (and, with distances, every
+    // maybe-in pair); pairs past its end are re-decided in place
+    const unsigned long long ev = (unsigned long long)std::max<int64_t>(ix->n_evaluated, 1);
+    unsigned long long band_cap = dist ? std::max<unsigned long long>(1ull << 20, ev / 8) : std::max<unsigned long long>(1ull << 20, ev / 64);
+    band_cap = std::min<unsigned long long>(band_cap, ev);
+    int2* band = nullptr;
+    SJ_TRY(dev_alloc_t(&band, (size_t)band_cap, s));
     JoinOut jo;
-    jo.pages = dpt;
-    jo.dpages = ddt;
-    jo.page_log2 = page_log2;
+    jo.out_pairs = reinterpret_cast<int2*>(ri->block);
+    jo.out_dist = ri->dblock;
     jo.capacity = (unsigned long long)np * (unsigned long long)page_pairs;
+    jo.band = band;
+    jo.band_cap = band_cap;
     int st = SJ_OK;
     if (ix->n_items > 0) {
         if (ix->kernel == SJ_KERNEL_FP64_DMMA)
             st = launch_join_dmma(ix, jo, dist ? 1 : 0);
         else
             st = launch_join_cc(ix, jo, dist ? 1 : 0);
+        if (st == SJ_OK) st = launch_recheck(ix, jo, dist ? 1 : 0);
     }
     unsigned long long c[4] = {0, 0, 0, 0};
     if (st == SJ_OK) {
@@ -310,8 +315,7 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, int page_l
             st = SJ_ERR_CUDA;
         }
     }
-    dev_free(dpt, s);
-    dev_free(ddt, s);
+    dev_free(band, s);
     *count_out = c[1];
     *rechecked_out = c[2];
     return st;
@@ -347,14 +351,14 @@ int sj_self_join(sj_handle h, sj_result* out) {
     int st = alloc_pages(ri, np, page_pairs, dist, h->stream);
     unsigned long long count = 0, rechecked = 0;
     int reruns = 0;
-    if (st == SJ_OK) st = run_join(h, ri, page_pairs, page_log2, dist, &count, &rechecked);
+    if (st == SJ_OK) st = run_join(h, ri, page_pairs, dist, &count, &rechecked);
     if (st == SJ_OK && count > (unsigned long long)ri->pair_pages.size() * (unsigned long long)page_pairs) {
         // overflow: grow the pool to the exact count and run again
         int64_t need = (int64_t)((count + page_pairs - 1) / page_pairs);
         st = alloc_pages(ri, need, page_pairs, dist, h->stream);
         if (st == SJ_OK) {
             reruns = 1;
-            st = run_join(h, ri, page_pairs, page_log2, dist, &count, &rechecked);
+            st = run_join(h, ri, page_pairs, dist, &count, &rechecked);
         }
         if (st == SJ_OK && count > (unsigned long long)ri->pair_pages.size() * (unsigned long long)page_pairs) {
             set_error("result of %llu pairs still exceeds the page pool", count);
@@ -365,17 +369,11 @@ int sj_self_join(sj_handle h, sj_result* out) {
         free_result_impl(ri);
         return st;
     }
-    // keep only the pages that hold pairs
+    // report only the pages that hold pairs (the allocation stays whole)
     int64_t used = (int64_t)((count + page_pairs - 1) / page_pairs);
     used = std::min<int64_t>(used, (int64_t)ri->pair_pages.size());
-    while ((int64_t)ri->pair_pages.size() > used) {
-        dev_free(ri->pair_pages.back(), ri->stream);
-        ri->pair_pages.pop_back();
-        if (dist) {
-            dev_free(ri->dist_pages.back(), ri->stream);
-            ri->dist_pages.pop_back();
-        }
-    }
+    ri->pair_pages.resize((size_t)used);
+    if (dist) ri->dist_pages.resize((size_t)used);
     out->count = (int64_t)count;
     out->page_pairs = page_pairs;
     out->n_pages = (int32_t)ri->pair_pages.size();

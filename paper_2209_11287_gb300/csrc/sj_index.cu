@@ -26,6 +26,9 @@ static double from_ord(unsigned long long o) {
 }
 
 // Per-dim min / max of the points and a flag for any non-finite coordinate.
+// The block size and the grid stride are multiples of d, so every element a
+// thread visits belongs to dim threadIdx.x % d and the thread keeps one
+// running min / max; all comparisons are on integer order keys.
 __global__ void k_extent(const double* __restrict__ x, int64_t total, int d, unsigned long long* lo,
                          unsigned long long* hi, int* bad) {
     extern __shared__ unsigned long long s_ext[];  // [2 * d]
@@ -34,23 +37,29 @@ __global__ void k_extent(const double* __restrict__ x, int64_t total, int d, uns
         s_ext[d + k] = 0ull;
     }
     __syncthreads();
+    unsigned long long mn = ~0ull, mx = 0ull;
     int local_bad = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = x[i];
-        int k = (int)(i % d);
-        if (!isfinite(v)) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += stride) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x[i]);
+        if (((b >> 52) & 0x7FFull) == 0x7FFull) {  // Inf or NaN
             local_bad = 1;
             continue;
         }
-        unsigned long long o = ord_of(v);
-        atomicMin(&s_ext[k], o);
-        atomicMax(&s_ext[d + k], o);
+        const unsigned long long o = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+        mn = o < mn ? o : mn;
+        mx = o > mx ? o : mx;
     }
     if (local_bad) atomicOr(bad, 1);
+    const int k = threadIdx.x % d;
+    if (mn <= mx) {
+        atomicMin(&s_ext[k], mn);
+        atomicMax(&s_ext[d + k], mx);
+    }
     __syncthreads();
-    for (int k = threadIdx.x; k < d; k += blockDim.x) {
-        atomicMin(&lo[k], s_ext[k]);
-        atomicMax(&hi[k], s_ext[d + k]);
+    for (int k2 = threadIdx.x; k2 < d; k2 += blockDim.x) {
+        atomicMin(&lo[k2], s_ext[k2]);
+        atomicMax(&hi[k2], s_ext[d + k2]);
     }
 }
 
@@ -60,12 +69,14 @@ struct GridParams {
     double lo[kMaxM];
     int64_t ncell[kMaxM];
     unsigned long long stride[kMaxM];
-    double w;
+    double inv_w;
 };
 
-// Cell coordinate of one value: floor((x - lo) / w), clamped to the grid.
-__device__ __forceinline__ int64_t cell_coord(double v, double lo, double w, int64_t ncell) {
-    double t = floor((v - lo) / w);
+// Cell coordinate of one value: floor((x - lo) * (1 / w)), clamped to the
+// grid.  (1 / w is rounded once; the relative margin of w over eps absorbs
+// the three roundings, see choose_grid.)
+__device__ __forceinline__ int64_t cell_coord(double v, double lo, double inv_w, int64_t ncell) {
+    double t = floor(__dmul_rn(__dsub_rn(v, lo), inv_w));
     int64_t c = (int64_t)t;
     return c < 0 ? 0 : (c >= ncell ? ncell - 1 : c);
 }
@@ -76,7 +87,7 @@ __global__ void k_cell_keys(const double* __restrict__ x, int64_t n, int d, Grid
     if (i >= n) return;
     unsigned long long key = 0;
     for (int k = 0; k < g.m; ++k) {
-        int64_t c = cell_coord(x[i * d + g.dims[k]], g.lo[k], g.w, g.ncell[k]);
+        int64_t c = cell_coord(x[i * d + g.dims[k]], g.lo[k], g.inv_w, g.ncell[k]);
         key += (unsigned long long)c * g.stride[k];
     }
     keys[i] = key;
@@ -335,10 +346,9 @@ __global__ void k_cells(const unsigned long long* __restrict__ keys, const uint3
 // ---------------------------------------------------------------------------
 struct PackParams {
     double lo[SJ_MAX_D];
-    double e2, eps;
-    double pbound;   // upper bound of ||y||^2 over all points
-    double delta;    // bound on |y_k - (x_k - lo_k)| per coordinate
-    double ulp_t;    // unit roundoff of the kernel type
+    // thresholds as affine functions of the computed norm pc (see below)
+    double a_out, b_out, a_in, b_in;
+    int has_in;
     int d, dp;
 };
 
@@ -349,30 +359,52 @@ __host__ __device__ inline double gamma_n(double u, int k) { return k * u / (1.0
 // pc.  With s_y = ||y_q - y_c||^2 = ||y_c||^2 - 2 a_exact, the evaluation
 // error satisfies |s_y - (pc - 2 a)| <= 3 gamma_T(dp) (||y_q||^2 + ||y_c||^2)
 // (norm chains and the dot-product chain); doubled for safety:
-//   E_s = 6.2 gamma_T(dp + 1) (pbound + pc).
+//   E_s = c1 (P + pc),  c1 = 6.2 gamma_T(dp + 1),  P >= every ||y||^2.
 // The coordinates carry |y_k - (x_k - lo_k)| <= delta, so
 // |sqrt(s_y) - sqrt(s)| <= eta = 2 delta sqrt(d), s the exact squared
 // distance of the inputs.  The decision rule's s differs from the exact one by
 // at most gamma_64(d + 3) s; g = 2 gamma_64(d + 3) covers it.  Then
 //   a <  thr_out  =>  s > e2 (1 + g)     => out for the decision rule,
 //   a >= thr_in   =>  s <= e2 (1 - g)    => in for the decision rule,
-// with thr_out = (pc - (eps (1 + g) + eta)^2 - E_s) / 2 rounded down and
-// thr_in = (pc - (eps (1 - g) - eta)^2 + E_s) / 2 rounded up (+inf when
-// eps (1 - g) <= eta); both get a further 4 u_T relative margin for their
-// own rounding.
-template <typename T>
-__device__ __forceinline__ T round_down_to(double v);
-template <>
-__device__ __forceinline__ double round_down_to<double>(double v) { return v; }
-template <>
-__device__ __forceinline__ float round_down_to<float>(double v) { return __double2float_rd(v); }
-template <typename T>
-__device__ __forceinline__ T round_up_to(double v);
-template <>
-__device__ __forceinline__ double round_up_to<double>(double v) { return v; }
-template <>
-__device__ __forceinline__ float round_up_to<float>(double v) { return __double2float_ru(v); }
+// with, S_o = (eps (1 + g) + eta)^2 and S_i = (eps (1 - g) - eta)^2,
+//   thr_out = (pc - S_o - E_s) / 2 - 4 u_T (pc + S_o + E_s)  = a_out pc - b_out
+//   thr_in  = (pc - S_i + E_s) / 2 + 4 u_T (pc + S_i + E_s)  = a_in pc + b_in
+// (thr_in = +inf when eps (1 - g) <= eta).  The affine coefficients are
+// formed on the host in binary64, rounded outward to T, and each threshold is
+// one fma rounded down (thr_out) or up (thr_in), so the stored values are on
+// the safe side of the exact ones.
+void pack_coefficients(double eps, double pbound, double delta, double u_t, int d, int dp, PackParams* pp) {
+    const double g = 2.0 * gamma_n(ldexp(1.0, -53), d + 3);
+    const double eta = 2.0 * delta * sqrt((double)d) * (1.0 + ldexp(1.0, -40));
+    const double c1 = 6.2 * gamma_n(u_t, dp + 1);
+    const double so_r = eps * (1.0 + g) + eta;
+    const double so = so_r * so_r * (1.0 + ldexp(1.0, -50));
+    const double m = 4.0 * u_t;
+    // thr_out = pc (1/2 - c1/2 - m (1 + c1)) - ((so + c1 P)/2 + m (so + c1 P))
+    pp->a_out = nextafter(0.5 - 0.5 * c1 - m * (1.0 + c1), 0.0);
+    pp->b_out = nextafter((so + c1 * pbound) * 0.5 + m * (so + c1 * pbound), INFINITY);
+    const double si_r = eps * (1.0 - g) - eta;
+    pp->has_in = si_r > 0 ? 1 : 0;
+    const double si = si_r * si_r * (1.0 - ldexp(1.0, -50));
+    // thr_in = pc (1/2 + c1/2 + m (1 + c1)) + ((c1 P - si)/2 + m (si + c1 P))
+    pp->a_in = nextafter(0.5 + 0.5 * c1 + m * (1.0 + c1), INFINITY);
+    pp->b_in = nextafter((c1 * pbound - si) * 0.5 + m * (si + c1 * pbound), INFINITY);
+}
 
+__device__ __forceinline__ float fma_pack(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_pack(double a, double b, double c) { return __fma_rn(a, b, c); }
+// outward-rounded affine thresholds
+__device__ __forceinline__ float thr_down(double a, float pc, double b) {
+    return __fmaf_rd(__double2float_rd(a), pc, -__double2float_ru(b));
+}
+__device__ __forceinline__ double thr_down(double a, double pc, double b) { return __fma_rd(a, pc, -b); }
+__device__ __forceinline__ float thr_up(double a, float pc, double b) {
+    return __fmaf_ru(__double2float_ru(a), pc, __double2float_ru(b));
+}
+__device__ __forceinline__ double thr_up(double a, double pc, double b) { return __fma_ru(a, pc, b); }
+
+// One thread per point: its row is gathered through perm and written in cell
+// order, with its kernel coordinates, norm and thresholds.
 template <typename T>
 __global__ void k_pack(const double* __restrict__ x, const int32_t* __restrict__ perm, int64_t n,
                        const PackParams* __restrict__ pp, double* xs, T* y, T* h, T* thr_out, T* thr_in) {
@@ -382,32 +414,15 @@ __global__ void k_pack(const double* __restrict__ x, const int32_t* __restrict__
     const int64_t src = (int64_t)perm[p] * d;
     T nrm = T(0);
     for (int k = 0; k < dp; ++k) {
-        double v = k < d ? x[src + k] : 0.0;
+        const double v = k < d ? x[src + k] : 0.0;
         xs[p * dp + k] = v;
-        T yk = k < d ? T(v - pp->lo[k]) : T(0);
+        const T yk = k < d ? T(v - pp->lo[k]) : T(0);
         y[p * dp + k] = yk;
-        nrm = fma(yk, yk, nrm);
+        nrm = fma_pack(yk, yk, nrm);
     }
     h[p] = -nrm * T(0.5);
-    const double u = pp->ulp_t;
-    const double pc = (double)nrm;
-    const double g = 2.0 * gamma_n(ldexp(1.0, -53), d + 3);
-    const double eta = 2.0 * pp->delta * sqrt((double)d) * (1.0 + ldexp(1.0, -40));
-    const double es = 6.2 * gamma_n(u, dp + 1) * (pp->pbound + pc);
-    const double so_r = pp->eps * (1.0 + g) + eta;
-    const double so = so_r * so_r;
-    double to = (pc - so - es) * 0.5;
-    to -= 4.0 * u * (pc + so + es);
-    thr_out[p] = round_down_to<T>(to);
-    const double si_r = pp->eps * (1.0 - g) - eta;
-    if (si_r > 0) {
-        const double si = si_r * si_r;
-        double ti = (pc - si + es) * 0.5;
-        ti += 4.0 * u * (pc + si + es);
-        thr_in[p] = round_up_to<T>(ti);
-    } else {
-        thr_in[p] = T(INFINITY);
-    }
+    thr_out[p] = thr_down(pp->a_out, nrm, pp->b_out);
+    thr_in[p] = pp->has_in ? thr_up(pp->a_in, nrm, pp->b_in) : T(INFINITY);
 }
 
 // ---------------------------------------------------------------------------
@@ -419,6 +434,7 @@ struct EnumParams {
     unsigned long long stride[kMaxM];
     int symmetric;
     int qmax;
+    const int32_t* table;  // dense key -> cell index (-1 = empty), or null
 };
 
 __device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long* a, int64_t n, unsigned long long v) {
@@ -433,6 +449,28 @@ __device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long* a, 
     return lo;
 }
 
+// Non-empty cells with keys in [k_lo, k_hi] (at most three consecutive
+// keys): the index range [ca, cb) of the cell table.
+__device__ __forceinline__ void cells_in_key_range(const EnumParams& e, const unsigned long long* __restrict__ cell_key,
+                                                   int64_t n_cells, unsigned long long k_lo, unsigned long long k_hi,
+                                                   int64_t& ca, int64_t& cb) {
+    if (e.table) {
+        ca = -1;
+        cb = -1;
+        for (unsigned long long k = k_lo; k <= k_hi; ++k) {
+            const int32_t c = e.table[k];
+            if (c >= 0) {
+                if (ca < 0) ca = c;
+                cb = c + 1;
+            }
+        }
+        if (ca < 0) ca = cb = 0;
+    } else {
+        ca = lower_bound_u64(cell_key, n_cells, k_lo);
+        cb = lower_bound_u64(cell_key, n_cells, k_hi + 1);
+    }
+}
+
 // Visits the candidate runs of cell c: for every offset vector o of the
 // first m-1 indexed dims in {-1,0,1} inside the grid, the cells whose last
 // coordinate is within one of c's form one contiguous key range, hence one
@@ -443,7 +481,7 @@ template <typename F>
 __device__ void visit_runs(const EnumParams& e, const unsigned long long* __restrict__ cell_key,
                            const int32_t* __restrict__ cell_start, int64_t n_cells, int64_t c, F&& f) {
     if (e.m == 0) {  // a single cell holding every point
-        f(cell_start[0], cell_start[n_cells], false, true);
+        f(cell_start[0], cell_start[n_cells], false);
         return;
     }
     const unsigned long long key = cell_key[c];
@@ -453,91 +491,88 @@ __device__ void visit_runs(const EnumParams& e, const unsigned long long* __rest
     int nvec = 1;
     for (int k = 0; k < mm; ++k) nvec *= 3;
     const int64_t last = cc[mm];
+    const int64_t lo_l = last > 0 ? last - 1 : 0;
+    const int64_t hi_l = last + 1 < e.ncell[mm] ? last + 1 : e.ncell[mm] - 1;
     for (int vi = 0; vi < nvec; ++vi) {
+        // offset digit k is (vi / 3^k) % 3 - 1; the lexicographic sign is
+        // that of the first non-zero digit in k order
         int rem = vi;
         long long delta = 0;
-        int sign = 0;  // lexicographic sign of the offset vector
+        int sign = 0;
         bool inside = true;
         for (int k = 0; k < mm; ++k) {
-            int o = rem % 3 - 1;
+            const int o = rem % 3 - 1;
             rem /= 3;
-            // digits are produced least-significant first; lexicographic order
-            // is on k ascending, so record the first non-zero from k = 0
+            if (sign == 0 && o != 0) sign = o;
             if (cc[k] + o < 0 || cc[k] + o >= e.ncell[k]) inside = false;
             delta += (long long)o * (long long)e.stride[k];
         }
         if (!inside) continue;
-        {
-            int rem2 = vi;
-            for (int k = 0; k < mm; ++k) {
-                int o = rem2 % 3 - 1;
-                rem2 /= 3;
-                if (sign == 0 && o != 0) sign = o;
-            }
-        }
+        if (e.symmetric && sign < 0) continue;
         const unsigned long long base = (unsigned long long)((long long)key + delta);
-        int64_t lo_l = last > 0 ? last - 1 : 0;
-        int64_t hi_l = last + 1 < e.ncell[mm] ? last + 1 : e.ncell[mm] - 1;
-        auto emit_range = [&](int64_t a_l, int64_t b_l, bool mirror, bool self) {
+        auto emit_range = [&](int64_t a_l, int64_t b_l, bool mirror) {
             if (a_l > b_l) return;
-            unsigned long long k_lo = base - (unsigned long long)(last - a_l);
-            unsigned long long k_hi = base + (unsigned long long)(b_l - last);
-            int64_t ca = lower_bound_u64(cell_key, n_cells, k_lo);
-            int64_t cb = lower_bound_u64(cell_key, n_cells, k_hi + 1);
+            int64_t ca, cb;
+            cells_in_key_range(e, cell_key, n_cells, base - (unsigned long long)(last - a_l),
+                               base + (unsigned long long)(b_l - last), ca, cb);
             if (ca >= cb) return;
-            f(cell_start[ca], cell_start[cb], mirror, self);
+            f(cell_start[ca], cell_start[cb], mirror);
         };
         if (!e.symmetric) {
-            emit_range(lo_l, hi_l, false, sign == 0);
+            emit_range(lo_l, hi_l, false);
         } else if (sign > 0) {
-            emit_range(lo_l, hi_l, true, false);
-        } else if (sign == 0) {
-            emit_range(last, last, false, true);
-            emit_range(last + 1, hi_l, true, false);
+            emit_range(lo_l, hi_l, true);
+        } else {
+            emit_range(last, last, false);
+            emit_range(last + 1, hi_l, true);
         }
     }
 }
 
 struct EnumTotals {
-    unsigned long long n_runs, n_items, n_candidates, n_evaluated;
+    unsigned long long n_runs, n_items, n_evaluated, sum_sq;
 };
 
+__global__ void k_table(const unsigned long long* __restrict__ cell_key, int64_t n_cells, int32_t* table) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c < n_cells) table[cell_key[c]] = (int32_t)c;
+}
+
+// Per cell: its run count, its item count, and the pair evaluations of its
+// queries.  The canonical candidate count (full neighbourhoods, ordered) is
+// the evaluations when not symmetric, else 2 * evaluations - sum_c |c|^2
+// (each unordered pair of distinct adjacent cells is evaluated once and
+// stands for both orders; a cell with itself is evaluated once).
 __global__ void k_enum_count(EnumParams e, const unsigned long long* __restrict__ cell_key,
                              const int32_t* __restrict__ cell_start, int64_t n_cells, uint32_t* run_cnt,
                              uint32_t* item_cnt, EnumTotals* tot) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long my_cand = 0, my_eval = 0, my_runs = 0, my_items = 0;
+    unsigned long long my_sq = 0, my_eval = 0, my_runs = 0, my_items = 0;
     if (c < n_cells) {
         const int64_t q = cell_start[c + 1] - cell_start[c];
         uint32_t nr = 0;
         unsigned long long ev = 0;
-        visit_runs(e, cell_key, cell_start, n_cells, c, [&](int32_t a, int32_t b, bool, bool) {
+        visit_runs(e, cell_key, cell_start, n_cells, c, [&](int32_t a, int32_t b, bool) {
             ++nr;
             ev += (unsigned long long)(b - a);
         });
-        // canonical candidate count: the full neighbourhood
-        unsigned long long full = 0;
-        EnumParams ef = e;
-        ef.symmetric = 0;
-        visit_runs(ef, cell_key, cell_start, n_cells, c,
-                   [&](int32_t a, int32_t b, bool, bool) { full += (unsigned long long)(b - a); });
         run_cnt[c] = nr;
         uint32_t ni = (uint32_t)((q + e.qmax - 1) / e.qmax);
         item_cnt[c] = ni;
-        my_cand = full * (unsigned long long)q;
+        my_sq = (unsigned long long)q * (unsigned long long)q;
         my_eval = ev * (unsigned long long)q;
         my_runs = nr;
         my_items = ni;
     }
     // warp reduction then one atomic per warp
     for (int o = 16; o > 0; o >>= 1) {
-        my_cand += __shfl_down_sync(0xffffffffu, my_cand, o);
+        my_sq += __shfl_down_sync(0xffffffffu, my_sq, o);
         my_eval += __shfl_down_sync(0xffffffffu, my_eval, o);
         my_runs += __shfl_down_sync(0xffffffffu, my_runs, o);
         my_items += __shfl_down_sync(0xffffffffu, my_items, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&tot->n_candidates, my_cand);
+        atomicAdd(&tot->sum_sq, my_sq);
         atomicAdd(&tot->n_evaluated, my_eval);
         atomicAdd(&tot->n_runs, my_runs);
         atomicAdd(&tot->n_items, my_items);
@@ -552,7 +587,7 @@ __global__ void k_enum_fill(EnumParams e, const unsigned long long* __restrict__
     if (c >= n_cells) return;
     uint32_t r = run_off[c];
     const uint32_t r0 = r;
-    visit_runs(e, cell_key, cell_start, n_cells, c, [&](int32_t a, int32_t b, bool mirror, bool) {
+    visit_runs(e, cell_key, cell_start, n_cells, c, [&](int32_t a, int32_t b, bool mirror) {
         Run rr;
         rr.start = a;
         rr.end_flags = (uint32_t)b | (mirror ? kMirrorBit : 0u);
@@ -576,8 +611,11 @@ __global__ void k_enum_fill(EnumParams e, const unsigned long long* __restrict__
 static int choose_grid(Index* ix) {
     const int d = ix->d;
     // w >= eps with a relative margin that absorbs the rounding of
-    // (x - lo) / w, so two coordinates within eps are never two cells apart.
+    // (x - lo) * (1 / w), so two coordinates within eps are never two cells
+    // apart; dims with 2^30 cells or more are not indexed (there the margin
+    // would no longer cover the rounding).
     ix->w = ix->eps * (1.0 + ldexp(1.0, -20));
+    const double inv_w = 1.0 / ix->w;
     struct Cand {
         int k;
         int64_t ncell;
@@ -585,7 +623,7 @@ static int choose_grid(Index* ix) {
     std::vector<Cand> cand;
     for (int k = 0; k < d; ++k) {
         double r = ix->hi[k] - ix->lo[k];
-        double cells = floor(r / ix->w) + 1.0;
+        double cells = floor(r * inv_w) + 1.0;
         if (!(cells < ldexp(1.0, 30))) continue;  // too fine for a safe cell coordinate
         cand.push_back({k, (int64_t)cells});
     }
@@ -656,9 +694,10 @@ int build_index(Index* ix, const double* pts) {
     init[2 * d] = 0;
     SJ_CK(cudaMemcpyAsync(ext, init.data(), init.size() * 8, cudaMemcpyHostToDevice, s));
     {
-        int64_t total = n * d;
-        int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)device_sm_count(ix->device) * 8);
-        k_extent<<<blocks, 256, 2 * d * sizeof(unsigned long long), s>>>(
+        const int64_t total = n * d;
+        const int bs = 256 - (256 % d);  // a multiple of d (d <= 128)
+        const int blocks = (int)std::min<int64_t>((total + bs - 1) / bs, (int64_t)device_sm_count(ix->device) * 8);
+        k_extent<<<blocks, bs, 2 * d * sizeof(unsigned long long), s>>>(
             pts, total, d, ext, ext + d, reinterpret_cast<int*>(ext + 2 * d));
         note_launch();
         SJ_CK(cudaGetLastError());
@@ -685,7 +724,7 @@ int build_index(Index* ix, const double* pts) {
     SJ_TRY(dev_alloc_t(&ix->perm, (size_t)n, s));
     GridParams gp{};
     gp.m = ix->m;
-    gp.w = ix->w;
+    gp.inv_w = 1.0 / ix->w;
     for (int i = 0; i < ix->m; ++i) {
         gp.dims[i] = ix->dims[i];
         gp.lo[i] = ix->lo[ix->dims[i]];
@@ -719,28 +758,24 @@ int build_index(Index* ix, const double* pts) {
     SJ_TRY(dev_alloc_t(&ix->xs, (size_t)n * ix->dp, s));
     PackParams hp{};
     for (int k = 0; k < d; ++k) hp.lo[k] = ix->lo[k];
-    hp.e2 = ix->e2;
-    hp.eps = ix->eps;
     double pb = 0, rmax = 0;
     for (int k = 0; k < d; ++k) {
         double r = ix->hi[k] - ix->lo[k];
         pb += r * r;
         rmax = std::max(rmax, r);
     }
-    hp.pbound = pb * (1.0 + ldexp(1.0, -20));
+    const double pbound = pb * (1.0 + ldexp(1.0, -20));
     hp.d = d;
     hp.dp = ix->dp;
     const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32;
-    hp.ulp_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
-    hp.delta = 1.01 * (use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53)) * rmax;
+    const double u_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
+    const double delta = 1.01 * u_t * rmax;
+    pack_coefficients(ix->eps, pbound, delta, u_t, d, ix->dp, &hp);
     if (use_f32)
         SJ_TRY(pack_points<float>(ix, pts, hp));
     else
         SJ_TRY(pack_points<double>(ix, pts, hp));
-    {
-        double es = 6.2 * gamma_n(hp.ulp_t, ix->dp + 1) * 2.0 * hp.pbound;
-        ix->filter_band_rel = 2.0 * es / ix->e2;
-    }
+    ix->filter_band_rel = 2.0 * 6.2 * gamma_n(u_t, ix->dp + 1) * 2.0 * pbound / ix->e2;
 
     unsigned long long M = 0;
     SJ_CK(cudaMemcpyAsync(&M, dcount, 8, cudaMemcpyDeviceToHost, s));
@@ -766,9 +801,23 @@ int build_index(Index* ix, const double* pts) {
     }
     ep.symmetric = ix->opt.symmetric ? 1 : 0;
     ep.qmax = ix->opt.queries_per_item > 0 ? std::min(ix->opt.queries_per_item, kQMax) : kQMax;
+    const int64_t Mc = (int64_t)M;
+    // dense key -> cell table when the key space is small (neighbour lookups
+    // become O(1) instead of binary searches over the cell keys)
+    int32_t* table = nullptr;
+    long double kspace = 1;
+    for (int i = 0; i < ix->m; ++i) kspace *= (long double)ix->ncell[i];
+    if (ix->m > 0 && kspace <= (long double)std::max<int64_t>(4 * ix->n, int64_t(1) << 22)) {
+        const size_t K = (size_t)kspace;
+        SJ_TRY(dev_alloc_t(&table, K, s));
+        SJ_CK(cudaMemsetAsync(table, 0xFF, K * sizeof(int32_t), s));
+        k_table<<<(unsigned)((Mc + 255) / 256), 256, 0, s>>>(ix->cell_key, Mc, table);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+    }
+    ep.table = table;
     uint32_t *run_cnt, *item_cnt, *run_off, *item_off;
     EnumTotals* dtot;
-    const int64_t Mc = (int64_t)M;
     SJ_TRY(dev_alloc_t(&run_cnt, (size_t)Mc * 4, s));
     item_cnt = run_cnt + Mc;
     run_off = run_cnt + 2 * Mc;
@@ -786,10 +835,11 @@ int build_index(Index* ix, const double* pts) {
     SJ_CK(cudaStreamSynchronize(s));
     ix->n_runs = (int64_t)tot.n_runs;
     ix->n_items = (int64_t)tot.n_items;
-    ix->n_candidates = (int64_t)tot.n_candidates;
     ix->n_evaluated = (int64_t)tot.n_evaluated;
+    ix->n_candidates = ep.symmetric ? (int64_t)(2 * tot.n_evaluated - tot.sum_sq) : (int64_t)tot.n_evaluated;
     if (tot.n_runs >= 0xFFFFFFFFull || tot.n_items >= 0x7FFFFFFFull) {
         set_error("index too large: %llu runs, %llu items", tot.n_runs, tot.n_items);
+        dev_free(table, s);
         return SJ_ERR_ARG;
     }
     SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(ix->n_runs, 1), s));
@@ -799,6 +849,7 @@ int build_index(Index* ix, const double* pts) {
     SJ_CK(cudaGetLastError());
     dev_free(run_cnt, s);
     dev_free(dtot, s);
+    dev_free(table, s);
     SJ_TRY(dev_alloc_t(&ix->counters, 4, s));
     return SJ_OK;
 }

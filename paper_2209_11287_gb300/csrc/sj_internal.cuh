@@ -101,6 +101,8 @@ struct Index {
 // Result internals.
 struct ResultImpl {
     cudaStream_t stream = nullptr;
+    int32_t* block = nullptr;   // the page pool: pages are slices of it
+    double* dblock = nullptr;
     std::vector<int32_t*> pair_pages;
     std::vector<double*> dist_pages;
 };
@@ -110,12 +112,14 @@ int build_index(Index* ix, const double* pts_dev);
 
 // ---- join kernels (sj_join_cc.cu) ----------------------------------------------
 struct JoinOut {
-    int2** pages = nullptr;        // device array of page pointers
-    double** dpages = nullptr;     // device array (or null)
-    int page_log2 = 22;
-    uint64_t capacity = 0;         // pairs the pages can hold
+    int2* out_pairs = nullptr;     // the result pool (one allocation)
+    double* out_dist = nullptr;    // distances (or null)
+    uint64_t capacity = 0;         // pairs the pool can hold
+    int2* band = nullptr;          // deferred-recheck queue
+    unsigned long long band_cap = 0;
 };
 int launch_join_cc(Index* ix, const JoinOut& out, int emit_dist);
+int launch_recheck(Index* ix, const JoinOut& out, int emit_dist);
 int launch_join_dmma(Index* ix, const JoinOut& out, int emit_dist);
 
 // ---- radix sort / scan (sj_index.cu) ------------------------------------------

@@ -10,136 +10,317 @@
 // thresholds (computed at packing) certify the decision: a < thr_out means
 // out, a >= thr_in means in; pairs in between are re-decided with the
 // decision rule itself (binary64 direct form, dimension order, no
-// contraction), so the returned set equals the rule's.
+// contraction) by k_recheck, so the returned set equals the rule's.
 //
 // T = double is the plain FP64 join (Eq. 3/4 evaluated on FP64 CUDA cores);
 // T = float is the certified FP32 filter.
+//
+// Work decomposition: every warp takes work items on its own (an atomic
+// queue, the next index fetched one item ahead), so no block-wide barrier
+// ever stalls a tile.  A warp evaluates its item in chunks of 32 x TC
+// candidates: each lane holds TC candidates in registers and walks the
+// item's queries, broadcast from shared memory.  For d <= 8 the threshold
+// test is fused into the query loop (and FP32 pairs of candidates use the
+// paired FMA, one rounding per lane as for the scalar FMA); for larger d
+// the accumulators of all queries are kept and tested after the d-loop.  The
+// "maybe in" pairs of a chunk (a >= thr_out) are compacted into a per-warp
+// list with one warp scan, and the list is classified 32 entries at a time,
+// so the rare work (certain-in test, queueing for the recheck, emission)
+// runs with every lane busy.
+#include <type_traits>
+
 #include "sj_join_common.cuh"
 
 namespace sj {
 
+// Warps per CTA (independent of each other): as many as keep the per-warp
+// shared memory of a CTA within the 48 KB of static shared memory, at most 4.
+template <typename WS>
+constexpr int cc_warps() {
+    return sizeof(WS) * 4 <= 46 * 1024 ? 4 : sizeof(WS) * 2 <= 46 * 1024 ? 2 : 1;
+}
+
+template <typename T, int DP, int TC, bool EMIT>
+struct CcWarpSmem {
+    ItemSmem<T, DP> it;
+    int32_t cj[32 * TC];               // sorted position of each candidate slot
+    int32_t cperm[32 * TC];            // its input index
+    uint8_t cmir[32 * TC];             // its mirror flag
+    uint16_t list[32 * TC * kQMax];    // maybe-in entries: certain << 15 | slot << 4 | query
+    int2 stage[kStage];
+    double sdist[EMIT ? kStage : 1];
+};
+
+// Maybe-in bitmasks of TC candidates against all queries of the item, d <= 8:
+// the threshold test follows each query's fma chain.
 template <typename T, int DP, int TC>
-__global__ void __launch_bounds__(kThreads) k_join_cc(JoinParams P) {
-    constexpr int KC = DP < 8 ? DP : 8;  // dims per register chunk
-    __shared__ ItemSmem<T, DP> S;
-    __shared__ int2 s_stage[kThreads / 32][kStage];
-    __shared__ double s_sdist[kThreads / 32][kStage];
-    __shared__ long long s_item;
+__device__ __forceinline__ void tile_fused(const ItemSmem<T, DP>& S, int Q, const T (&c)[TC][DP], const T (&to)[TC],
+                                           const T (&ti)[TC], uint32_t (&bits)[TC], uint32_t (&cbits)[TC]) {
+#pragma unroll
+    for (int t = 0; t < TC; ++t) bits[t] = cbits[t] = 0;
+    if constexpr (std::is_same<T, float>::value && TC % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < kQMax; ++q) {
+            if (q >= Q) break;
+            const float h = S.qh[q];
+#pragma unroll
+            for (int t = 0; t < TC; t += 2) {
+                float2 a = make_float2(h, h);
+#pragma unroll
+                for (int k = 0; k < DP; ++k) {
+                    const float qv = S.qy[q][k];
+                    a = __ffma2_rn(make_float2(qv, qv), make_float2(c[t][k], c[t + 1][k]), a);
+                }
+                if (a.x >= to[t]) bits[t] |= 1u << q;
+                if (a.y >= to[t + 1]) bits[t + 1] |= 1u << q;
+                if (a.x >= ti[t]) cbits[t] |= 1u << q;
+                if (a.y >= ti[t + 1]) cbits[t + 1] |= 1u << q;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kQMax; ++q) {
+            if (q >= Q) break;
+            const T h = S.qh[q];
+#pragma unroll
+            for (int t = 0; t < TC; ++t) {
+                T a = h;
+#pragma unroll
+                for (int k = 0; k < DP; ++k) a = fma_t(S.qy[q][k], c[t][k], a);
+                if (ge_threshold(a, to[t])) bits[t] |= 1u << q;
+                if (ge_threshold(a, ti[t])) cbits[t] |= 1u << q;
+            }
+        }
+    }
+}
+
+// Minimum resident CTAs per SM requested from the register allocator: the
+// FP32 small-d tile is latency-bound, so it is held to 64 registers.
+template <typename T, int DP>
+constexpr int cc_min_blocks() {
+    return std::is_same<T, float>::value && DP <= 8 ? 8 : 1;
+}
+
+template <typename T, int DP, int TC, bool EMIT, int NW>
+__global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(JoinParams P) {
+    constexpr bool FUSED = DP <= 8;
+    constexpr int KC = DP < 8 ? DP : 8;  // dims per register chunk (unfused path)
+    constexpr int SLOTS = 32 * TC;
+    static_assert(SLOTS <= 2048, "slot index must fit in 11 bits");
+    __shared__ CcWarpSmem<T, DP, TC, EMIT> smem[NW];
 
     const T* __restrict__ Y = static_cast<const T*>(P.y);
     const T* __restrict__ TO = static_cast<const T*>(P.thr_out);
     const T* __restrict__ TI = static_cast<const T*>(P.thr_in);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpStage st{s_stage[wid], s_sdist[wid], 0};
+    CcWarpSmem<T, DP, TC, EMIT>& W = smem[wid];
+    ItemSmem<T, DP>& S = W.it;
+    WarpStage st{W.stage, EMIT ? W.sdist : nullptr, 0};
     unsigned long long rechecked = 0;
 
+    long long next = 0;
+    if (lane == 0) next = (long long)atomicAdd(&P.counters[0], 1ull);
+    next = __shfl_sync(0xffffffffu, next, 0);
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&P.counters[0], 1ull);
-        __syncthreads();
-        const long long it = s_item;
+        const long long it = next;
         if (it >= P.n_items) break;
+        if (lane == 0) next = (long long)atomicAdd(&P.counters[0], 1ull);  // used next iteration
+        next = __shfl_sync(0xffffffffu, next, 0);
         const Item I = P.items[it];
         const int Q = I.q1 - I.q0;
         const int nr = I.r1 - I.r0;
-        const uint32_t C = load_item<T, DP>(S, P, I);
+        const uint32_t C = load_item_warp<T, DP>(S, P, I, lane);
 
-        for (uint32_t base = 0; base < C; base += (uint32_t)(kThreads * TC)) {
+        for (uint32_t base = 0; base < C; base += (uint32_t)SLOTS) {
             int32_t j[TC];
-            bool mir[TC], valid[TC];
-            T to[TC];
+            bool valid[TC];
+            T to[TC], ti[TC];
 #pragma unroll
             for (int t = 0; t < TC; ++t) {
-                const uint32_t v = base + (uint32_t)(t * kThreads) + threadIdx.x;
+                const int slot = t * 32 + lane;
+                const uint32_t v = base + (uint32_t)slot;
                 valid[t] = v < C;
                 j[t] = 0;
-                mir[t] = false;
-                to[t] = T(0);
+                to[t] = T(INFINITY);  // an empty slot is never maybe-in
+                ti[t] = T(INFINITY);
                 if (valid[t]) {
-                    j[t] = map_candidate<T, DP>(S, nr, v, mir[t]);
+                    bool mir;
+                    j[t] = map_candidate<T, DP>(S, nr, v, mir);
                     to[t] = TO[j[t]];
+                    ti[t] = TI[j[t]];
+                    W.cj[slot] = j[t];
+                    W.cperm[slot] = P.perm[j[t]];
+                    W.cmir[slot] = mir ? 1 : 0;
                 }
             }
-            T acc[TC][kQMax];
-#pragma unroll
-            for (int q = 0; q < kQMax; ++q)
-#pragma unroll
-                for (int t = 0; t < TC; ++t) acc[t][q] = S.qh[q];
-#pragma unroll
-            for (int kc = 0; kc < DP; kc += KC) {
-                T c[TC][KC];
+            uint32_t bits[TC], cbits[TC];
+            if constexpr (FUSED) {
+                T c[TC][DP];
 #pragma unroll
                 for (int t = 0; t < TC; ++t)
 #pragma unroll
-                    for (int kk = 0; kk < KC; ++kk) c[t][kk] = valid[t] ? Y[(int64_t)j[t] * DP + kc + kk] : T(0);
-#pragma unroll
-                for (int q = 0; q < kQMax; ++q) {
-                    if (q >= Q) break;
-#pragma unroll
-                    for (int kk = 0; kk < KC; ++kk) {
-                        const T qv = S.qy[q][kc + kk];
-#pragma unroll
-                        for (int t = 0; t < TC; ++t) acc[t][q] = fma(qv, c[t][kk], acc[t][q]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < TC; ++t) {
-                uint32_t bits = 0;
+                    for (int k = 0; k < DP; ++k) c[t][k] = valid[t] ? Y[(int64_t)j[t] * DP + k] : T(0);
+                tile_fused<T, DP, TC>(S, Q, c, to, ti, bits, cbits);
+            } else {
+                T acc[TC][kQMax];
 #pragma unroll
                 for (int q = 0; q < kQMax; ++q)
-                    if (q < Q && acc[t][q] >= to[t]) bits |= 1u << q;
-                if (!valid[t]) bits = 0;
-                // emission: one maybe-in pair per lane per round
-                while (__any_sync(0xffffffffu, bits != 0)) {
-                    int nout = 0;
-                    double dist = 0.0;
-                    int32_t qid = 0, cid = 0;
-                    if (bits) {
-                        const int q = __ffs(bits) - 1;
-                        bits &= bits - 1u;
-                        const int64_t jj = j[t];
-                        // the same fma chain as above, so the same value
-                        T a = S.qh[q];
 #pragma unroll
-                        for (int k = 0; k < DP; ++k) a = fma(S.qy[q][k], Y[jj * DP + k], a);
-                        bool in = a >= TI[jj];
-                        double s = 0.0;
-                        if (!in || P.emit_dist) s = direct_sq(P.xs + (int64_t)(I.q0 + q) * DP, P.xs + jj * DP, P.d);
-                        if (!in) {
-                            in = s <= P.e2;
-                            ++rechecked;
-                        }
-                        if (in) {
-                            nout = mir[t] ? 2 : 1;
-                            dist = P.emit_dist ? sqrt(s) : 0.0;
-                            qid = S.qid[q];
-                            cid = P.perm[jj];
+                    for (int t = 0; t < TC; ++t) acc[t][q] = S.qh[q];
+#pragma unroll
+                for (int kc = 0; kc < DP; kc += KC) {
+                    T c[TC][KC];
+#pragma unroll
+                    for (int t = 0; t < TC; ++t)
+#pragma unroll
+                        for (int kk = 0; kk < KC; ++kk) c[t][kk] = valid[t] ? Y[(int64_t)j[t] * DP + kc + kk] : T(0);
+#pragma unroll
+                    for (int q = 0; q < kQMax; ++q) {
+                        if (q >= Q) break;
+#pragma unroll
+                        for (int kk = 0; kk < KC; ++kk) {
+                            const T qv = S.qy[q][kc + kk];
+#pragma unroll
+                            for (int t = 0; t < TC; ++t) acc[t][q] = fma_t(qv, c[t][kk], acc[t][q]);
                         }
                     }
-                    stage_emit(st, P, lane, nout, qid, cid, dist);
+                }
+#pragma unroll
+                for (int t = 0; t < TC; ++t) {
+                    uint32_t b = 0, cb = 0;
+#pragma unroll
+                    for (int q = 0; q < kQMax; ++q) {
+                        if (q < Q && ge_threshold(acc[t][q], to[t])) b |= 1u << q;
+                        if (q < Q && ge_threshold(acc[t][q], ti[t])) cb |= 1u << q;
+                    }
+                    bits[t] = b;
+                    cbits[t] = cb;
                 }
             }
+            // compact the maybe-in pairs with one warp scan
+            int cnt = 0;
+#pragma unroll
+            for (int t = 0; t < TC; ++t) cnt += __popc(bits[t]);
+            int total;
+            int off = warp_excl_scan(cnt, lane, &total);
+#pragma unroll
+            for (int t = 0; t < TC; ++t) {
+                uint32_t b = bits[t];
+                while (b) {
+                    const int q = __ffs(b) - 1;
+                    b &= b - 1u;
+                    const int certain = (cbits[t] >> q) & 1u;
+                    W.list[off++] = (uint16_t)((certain << 15) | ((t * 32 + lane) << 4) | q);
+                }
+            }
+            __syncwarp();
+            for (int e0 = 0; e0 < total; e0 += 32) {
+                const int e = e0 + lane;
+                int nout = 0;
+                int32_t qid = 0, cid = 0;
+                double dist = 0.0;
+                bool band = false, mir = false;
+                int q = 0;
+                int64_t jj = 0;
+                if (e < total) {
+                    const int ent = W.list[e];
+                    const int slot = (ent >> 4) & 0x7FF;
+                    q = ent & 15;
+                    jj = W.cj[slot];
+                    mir = W.cmir[slot] != 0;
+                    if ((ent >> 15) && !EMIT) {  // certain in
+                        nout = mir ? 2 : 1;
+                        qid = S.qid[q];
+                        cid = W.cperm[slot];
+                    } else {
+                        band = true;  // re-decided (and measured) in binary64
+                    }
+                }
+                const bool queued = band_push(P, lane, band, I.q0 + q, (int32_t)jj, mir);
+                if (band && !queued) {  // queue full: decide here
+                    const double s = direct_sq(P.xs + (int64_t)(I.q0 + q) * DP, P.xs + jj * DP, P.d);
+                    ++rechecked;
+                    if (s <= P.e2) {
+                        nout = mir ? 2 : 1;
+                        qid = S.qid[q];
+                        cid = W.cperm[(W.list[e] >> 4) & 0x7FF];
+                        if (EMIT) dist = sqrt(s);
+                    }
+                }
+                if (EMIT)
+                    stage_emit(st, P, lane, nout, qid, cid, dist);
+                else
+                    stage_emit_pairs(st, P, lane, nout, qid, cid);
+            }
+            __syncwarp();
         }
-        __syncthreads();
+        __syncwarp();
     }
     stage_flush(st, P, lane);
     for (int o = 16; o > 0; o >>= 1) rechecked += __shfl_down_sync(0xffffffffu, rechecked, o);
     if (lane == 0 && rechecked) atomicAdd(&P.counters[2], rechecked);
 }
 
-template <typename T, int DP>
-static int launch_dp(Index* ix, const JoinParams& p) {
-    constexpr int TC = 2;
-    auto kern = k_join_cc<T, DP, TC>;
+// Re-decides the queued pairs with the decision rule (binary64 direct form),
+// 32 pairs per warp instruction, and emits the members (both orders for
+// mirrored entries) with their distances when requested.
+template <int DP, bool EMIT>
+__global__ void __launch_bounds__(128) k_recheck(JoinParams P) {
+    __shared__ int2 s_stage[4][kStage];
+    __shared__ double s_sdist[4][EMIT ? kStage : 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpStage st{s_stage[wid], EMIT ? s_sdist[wid] : nullptr, 0};
+    const unsigned long long queued = P.counters[3];
+    const unsigned long long count = queued < P.band_cap ? queued : P.band_cap;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * 4 + wid;
+    const unsigned long long nw = (unsigned long long)gridDim.x * 4;
+    for (unsigned long long b = gw * 32; b < count; b += nw * 32) {
+        const unsigned long long i = b + lane;
+        int nout = 0;
+        int32_t qid = 0, cid = 0;
+        double dist = 0.0;
+        if (i < count) {
+            const int2 e = P.band[i];
+            const int32_t qs = e.x;
+            const int32_t cs = (int32_t)((uint32_t)e.y & ~kMirrorBit);
+            const bool mir = ((uint32_t)e.y & kMirrorBit) != 0;
+            const double s = direct_sq(P.xs + (int64_t)qs * DP, P.xs + (int64_t)cs * DP, P.d);
+            if (s <= P.e2) {
+                nout = mir ? 2 : 1;
+                qid = P.perm[qs];
+                cid = P.perm[cs];
+                if (EMIT) dist = sqrt(s);
+            }
+        }
+        if (EMIT)
+            stage_emit(st, P, lane, nout, qid, cid, dist);
+        else
+            stage_emit_pairs(st, P, lane, nout, qid, cid);
+    }
+    stage_flush(st, P, lane);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && count) atomicAdd(&P.counters[2], count);
+}
+
+template <typename T, int DP, bool EMIT>
+static int launch_dpe(Index* ix, const JoinParams& p) {
+    constexpr int TC = DP <= 8 ? 4 : 2;
+    constexpr int NW = cc_warps<CcWarpSmem<T, DP, TC, EMIT>>();
+    auto kern = k_join_cc<T, DP, TC, EMIT, NW>;
     int per_sm = 0;
-    SJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
+    SJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, 0));
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)device_sm_count(ix->device) * per_sm;
-    if (blocks > ix->n_items) blocks = ix->n_items > 0 ? ix->n_items : 1;
-    kern<<<(unsigned)blocks, kThreads, 0, ix->stream>>>(p);
+    const long long need = (ix->n_items + NW - 1) / NW;
+    if (blocks > need) blocks = need > 0 ? need : 1;
+    kern<<<(unsigned)blocks, NW * 32, 0, ix->stream>>>(p);
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
+}
+
+template <typename T, int DP>
+static int launch_dp(Index* ix, const JoinParams& p) {
+    return p.emit_dist ? launch_dpe<T, DP, true>(ix, p) : launch_dpe<T, DP, false>(ix, p);
 }
 
 template <typename T>
@@ -158,6 +339,34 @@ static int launch_t(Index* ix, const JoinParams& p) {
     }
 }
 
+template <int DP>
+static int launch_recheck_dp(Index* ix, const JoinParams& p) {
+    const unsigned blocks = (unsigned)device_sm_count(ix->device) * 4;
+    if (p.emit_dist)
+        k_recheck<DP, true><<<blocks, 128, 0, ix->stream>>>(p);
+    else
+        k_recheck<DP, false><<<blocks, 128, 0, ix->stream>>>(p);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    return SJ_OK;
+}
+
+int launch_recheck(Index* ix, const JoinOut& out, int emit_dist) {
+    const JoinParams p = make_join_params(ix, out, emit_dist);
+    switch (ix->dp) {
+        case 2: return launch_recheck_dp<2>(ix, p);
+        case 4: return launch_recheck_dp<4>(ix, p);
+        case 8: return launch_recheck_dp<8>(ix, p);
+        case 16: return launch_recheck_dp<16>(ix, p);
+        case 32: return launch_recheck_dp<32>(ix, p);
+        case 64: return launch_recheck_dp<64>(ix, p);
+        case 128: return launch_recheck_dp<128>(ix, p);
+        default:
+            set_error("no recheck kernel for padded dimension %d", ix->dp);
+            return SJ_ERR_UNSUPPORTED;
+    }
+}
+
 JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist) {
     JoinParams p{};
     p.y = ix->y;
@@ -170,13 +379,14 @@ JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist) {
     p.runs = ix->runs;
     p.n_items = ix->n_items;
     p.counters = ix->counters;
-    p.pages = out.pages;
-    p.dpages = out.dpages;
-    p.page_log2 = out.page_log2;
+    p.out_pairs = out.out_pairs;
+    p.out_dist = out.out_dist;
     p.capacity = out.capacity;
     p.e2 = ix->e2;
     p.d = ix->d;
     p.emit_dist = emit_dist;
+    p.band = out.band;
+    p.band_cap = out.band_cap;
     return p;
 }
 

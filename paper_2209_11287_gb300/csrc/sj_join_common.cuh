@@ -20,16 +20,40 @@ struct JoinParams {
     const Run* runs;
     long long n_items;
     unsigned long long* counters;  // [0] item queue, [1] result cursor, [2] rechecked
-    int2* const* pages;
-    double* const* dpages;
-    int page_log2;
-    unsigned long long capacity;
+    int2* out_pairs;               // the result pool (pages are views of it)
+    double* out_dist;              // distances, or null
+    unsigned long long capacity;   // pairs the pool holds
     double e2;
     int d;
     int emit_dist;
+    // deferred re-decisions: pairs whose certified bound straddles eps (and,
+    // when distances are emitted, every maybe-in pair) are queued here and
+    // re-decided by k_recheck with whole warps.  Entry: (query sorted
+    // position, candidate sorted position | kMirrorBit).  counters[3] counts
+    // queued entries; past `band_cap` a pair is re-decided in place.
+    int2* band;
+    unsigned long long band_cap;
 };
 
 JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist);
+
+// Fused multiply-add in the kernel type, one rounding (explicit intrinsics so
+// a float chain never runs on the FP64 pipe).
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Order key of a binary64 value as a signed 64-bit integer: for non-NaN
+// values, a < b  <=>  key(a) < key(b) (with -0 ordered just below +0).
+// Comparing keys moves the threshold test of the FP64 kernels from the FP64
+// pipe to the integer ALUs.
+__device__ __forceinline__ long long order_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+// a >= t for a float / double against a threshold whose order key (double)
+// or value (float) is given.
+__device__ __forceinline__ bool ge_threshold(float a, float t) { return a >= t; }
+__device__ __forceinline__ bool ge_threshold(double a, double t) { return order_key(a) >= order_key(t); }
 
 // Squared distance in the decision rule's operation order: binary64, k
 // ascending, subtraction, product and sum each rounded (no fma).
@@ -56,13 +80,11 @@ __device__ __forceinline__ void stage_flush(WarpStage& st, const JoinParams& P, 
     unsigned long long base = 0;
     if (lane == 0 && st.cnt > 0) base = atomicAdd(&P.counters[1], (unsigned long long)st.cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    const unsigned long long pmask = (1ull << P.page_log2) - 1ull;
     for (int i = lane; i < st.cnt; i += 32) {
-        unsigned long long p = base + (unsigned long long)i;
+        const unsigned long long p = base + (unsigned long long)i;
         if (p < P.capacity) {
-            unsigned long long pg = p >> P.page_log2, off = p & pmask;
-            P.pages[pg][off] = st.pairs[i];
-            if (P.emit_dist) P.dpages[pg][off] = st.dist[i];
+            P.out_pairs[p] = st.pairs[i];
+            if (P.emit_dist) P.out_dist[p] = st.dist[i];
         }
     }
     __syncwarp();
@@ -89,6 +111,50 @@ __device__ __forceinline__ void stage_emit(WarpStage& st, const JoinParams& P, i
         st.dist[pos + 1] = dist;
     }
     st.cnt += tot;
+}
+
+// Warp-collective emission without distances (nothing of binary64 is touched).
+__device__ __forceinline__ void stage_emit_pairs(WarpStage& st, const JoinParams& P, int lane, int nout,
+                                                 int32_t qid, int32_t cid) {
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned b1 = __ballot_sync(0xffffffffu, nout >= 1);
+    const unsigned b2 = __ballot_sync(0xffffffffu, nout == 2);
+    const int tot = __popc(b1) + __popc(b2);
+    if (tot == 0) return;
+    if (st.cnt + tot > kStage) stage_flush(st, P, lane);
+    const int pos = st.cnt + __popc(b1 & lt) + __popc(b2 & lt);
+    if (nout >= 1) st.pairs[pos] = make_int2(qid, cid);
+    if (nout == 2) st.pairs[pos + 1] = make_int2(cid, qid);
+    st.cnt += tot;
+}
+
+// Warp-collective: lanes with `want` queue (qs, cs | mirror) for the
+// deferred recheck, one atomic per warp.  Returns, per lane, whether its entry
+// found room (if not, the caller re-decides the pair itself).
+__device__ __forceinline__ bool band_push(const JoinParams& P, int lane, bool want, int32_t qs, int32_t cs,
+                                          bool mirror) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (m == 0) return false;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&P.counters[3], (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (!want) return false;
+    const unsigned long long pos = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+    if (pos >= P.band_cap) return false;
+    P.band[pos] = make_int2(qs, (int32_t)((uint32_t)cs | (mirror ? kMirrorBit : 0u)));
+    return true;
+}
+
+// Warp-wide exclusive prefix sum of v; *total gets the sum.
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total) {
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
 }
 
 // Shared-memory image of one work item.
@@ -142,6 +208,44 @@ __device__ __forceinline__ uint32_t load_item(ItemSmem<T, DP>& S, const JoinPara
     }
     __syncthreads();
     return S.rpre[nr];
+}
+
+// Warp-level variant of load_item: the calling warp alone fills S (its own
+// copy) and the result is visible to the warp after the returned __syncwarp.
+template <typename T, int DP>
+__device__ __forceinline__ uint32_t load_item_warp(ItemSmem<T, DP>& S, const JoinParams& P, const Item& I,
+                                                   int lane) {
+    const T* __restrict__ Y = static_cast<const T*>(P.y);
+    const T* __restrict__ H = static_cast<const T*>(P.h);
+    const int Q = I.q1 - I.q0;
+    const int nr = I.r1 - I.r0;
+    for (int i = lane; i < kQMax * DP; i += 32) S.qy[i / DP][i % DP] = i < Q * DP ? Y[(int64_t)I.q0 * DP + i] : T(0);
+    if (lane < kQMax) {
+        S.qh[lane] = lane < Q ? H[I.q0 + lane] : T(0);
+        S.qid[lane] = lane < Q ? P.perm[I.q0 + lane] : 0;
+    }
+    uint32_t carry = 0;
+    for (int b = 0; b < nr; b += 32) {
+        const int r = b + lane;
+        uint32_t len = 0;
+        if (r < nr) {
+            const Run R = P.runs[I.r0 + r];
+            S.rstart[r] = R.start;
+            S.rmir[r] = (uint8_t)(R.end_flags >> 31);
+            len = (uint32_t)((int32_t)(R.end_flags & ~kMirrorBit) - R.start);
+        }
+        uint32_t v = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (r < nr) S.rpre[r + 1] = carry + v;
+        carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) S.rpre[0] = 0;
+    __syncwarp();
+    return carry;
 }
 
 // Candidate v (0 <= v < C) of the item: its sorted position and mirror flag.

@@ -23,7 +23,7 @@ __device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, dou
                  : "d"(a), "d"(b));
 }
 
-template <int DP>
+template <int DP, bool EMIT>
 __global__ void __launch_bounds__(kThreads) k_join_dmma(JoinParams P) {
     static_assert(DP % 4 == 0, "DMMA needs the padded dimension to be a multiple of 4");
     constexpr int KS = DP / 4;  // k-steps
@@ -90,23 +90,32 @@ __global__ void __launch_bounds__(kThreads) k_join_dmma(JoinParams P) {
                     int nout = 0;
                     double dist = 0.0;
                     int32_t qid = 0, cid = 0;
-                    if (q < Q && jc[i] >= 0 && a >= to[i]) {
-                        bool in = a >= ti[i];
-                        double s = 0.0;
-                        if (!in || P.emit_dist)
-                            s = direct_sq(P.xs + (int64_t)(I.q0 + q) * DP, P.xs + (int64_t)jc[i] * DP, P.d);
-                        if (!in) {
-                            in = s <= P.e2;
-                            ++rechecked;
-                        }
-                        if (in) {
+                    bool band = false;
+                    if (q < Q && jc[i] >= 0 && ge_threshold(a, to[i])) {
+                        if (ge_threshold(a, ti[i]) && !EMIT) {
                             nout = mc[i] ? 2 : 1;
-                            dist = P.emit_dist ? sqrt(s) : 0.0;
                             qid = S.qid[q];
                             cid = P.perm[jc[i]];
+                        } else {
+                            band = true;  // re-decided (and measured) in binary64
                         }
                     }
-                    stage_emit(st, P, lane, nout, qid, cid, dist);
+                    const bool queued = band_push(P, lane, band, I.q0 + q, jc[i], band && mc[i]);
+                    if (band && !queued) {  // queue full: decide here
+                        const double s =
+                            direct_sq(P.xs + (int64_t)(I.q0 + q) * DP, P.xs + (int64_t)jc[i] * DP, P.d);
+                        ++rechecked;
+                        if (s <= P.e2) {
+                            nout = mc[i] ? 2 : 1;
+                            qid = S.qid[q];
+                            cid = P.perm[jc[i]];
+                            if (EMIT) dist = sqrt(s);
+                        }
+                    }
+                    if (EMIT)
+                        stage_emit(st, P, lane, nout, qid, cid, dist);
+                    else
+                        stage_emit_pairs(st, P, lane, nout, qid, cid);
                 }
             }
         }
@@ -117,9 +126,9 @@ __global__ void __launch_bounds__(kThreads) k_join_dmma(JoinParams P) {
     if (lane == 0 && rechecked) atomicAdd(&P.counters[2], rechecked);
 }
 
-template <int DP>
-static int launch_dp(Index* ix, const JoinParams& p) {
-    auto kern = k_join_dmma<DP>;
+template <int DP, bool EMIT>
+static int launch_dpe(Index* ix, const JoinParams& p) {
+    auto kern = k_join_dmma<DP, EMIT>;
     int per_sm = 0;
     SJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
     if (per_sm < 1) per_sm = 1;
@@ -129,6 +138,11 @@ static int launch_dp(Index* ix, const JoinParams& p) {
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
+}
+
+template <int DP>
+static int launch_dp(Index* ix, const JoinParams& p) {
+    return p.emit_dist ? launch_dpe<DP, true>(ix, p) : launch_dpe<DP, false>(ix, p);
 }
 
 int launch_join_dmma(Index* ix, const JoinOut& out, int emit_dist) {
