@@ -186,6 +186,45 @@ SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj
 SJ_API int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps,
                   int32_t count, const sj_options* opt, void* stream, sj_result* per_instance_out);
 
+/* ---- self-join without allocation -------------------------------------- */
+/*
+ * No counterpart in the paper: an entry point for callers that must not
+ * allocate memory while they run, for instance code inside a CUDA stream
+ * capture, a process whose device memory another allocator has reserved up
+ * front, or a runtime that forbids cudaMalloc / cudaFree after start-up.
+ *
+ * Computes the same set as sj_join with SJ_KERNEL_FP64_FMA (the decision rule
+ * above) by brute force: all n points form one cell, so every pair is tiled.
+ * Every working array lives in one static device array of about 6 MB
+ * compiled into the library, which each GPU that loads the library keeps
+ * until the process exits; the call makes no cudaMalloc / cudaFree and no
+ * other allocation.
+ *
+ *   pts        device pointer, n x d row-major binary64, caller-owned
+ *   n, d       1 <= n <= SJ_NOALLOC_MAX_N, 1 <= d <= SJ_NOALLOC_MAX_D;
+ *              larger sizes are rejected with SJ_ERR_ARG
+ *   eps        > 0 and finite
+ *   pairs_out  device pointer to room for `capacity` pairs (2 * capacity
+ *              int32, (i, j) interleaved, input indices, unspecified order)
+ *   count_out  host pointer; receives |R| (exact even when it exceeds
+ *              capacity, in which case SJ_ERR_RESULT_OVERFLOW is returned and
+ *              pairs_out holds `capacity` of the pairs)
+ *   stream     cudaStream_t as void*; the call returns after its work on
+ *              `stream` has finished (it reads the count back)
+ *
+ * The first call on a device looks up the device address of the static
+ * array (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  All calls on a device share the one array and each
+ * call resets what it needs, so calls that overlap on the GPU (from several
+ * streams or threads at once) race and must be serialised by the caller.
+ * Errors: SJ_ERR_ARG (sizes, NULL or host pointers, non-finite coordinate),
+ * SJ_ERR_RESULT_OVERFLOW, SJ_ERR_CUDA.
+ */
+#define SJ_NOALLOC_MAX_N 32768
+#define SJ_NOALLOC_MAX_D 8
+SJ_API int sj_self_join_noalloc(const double* pts, int64_t n, int32_t d, double eps, int32_t* pairs_out,
+                                int64_t capacity, int64_t* count_out, void* stream);
+
 /* ---- status ------------------------------------------------------------ */
 SJ_API const char* sj_error_string(int status);
 /* Detail of the calling thread's last error (empty string if none). */

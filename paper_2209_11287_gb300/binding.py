@@ -131,6 +131,8 @@ def load():
         lib.sj_version.restype = ctypes.c_char_p
         lib.sj_kernel_launches.argtypes = []
         lib.sj_kernel_launches.restype = ctypes.c_int64
+        lib.sj_self_join_noalloc.argtypes = [_vp, _i64, _i32, ctypes.c_double, _vp, _i64, ctypes.POINTER(_i64), _vp]
+        lib.sj_self_join_noalloc.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -277,6 +279,22 @@ def sj_join_batch(points_list, eps_list, options: sj_options | None = None, stre
     _check(load().sj_join_batch(ptrs, ns, ds, es, count, ctypes.byref(options) if options is not None else None,
                                 _stream_ptr(stream), res))
     return list(res)
+
+
+def sj_self_join_noalloc(points, eps: float, pairs_out, stream=None) -> int:
+    """The allocation-free self-join for callers that cannot allocate while
+    they run: ``points`` an n x d float64 CUDA tensor (n <= 32768, d <= 8),
+    ``pairs_out`` a preallocated CUDA int32 tensor of shape (capacity, 2).
+    Returns the pair count (raises on overflow, with the count in the
+    message)."""
+    ptr, n, d, keep = _points_ptr(points)
+    if not hasattr(pairs_out, "data_ptr") or str(pairs_out.dtype) != "torch.int32" or not pairs_out.is_contiguous():
+        raise ValueError("pairs_out must be a contiguous int32 CUDA tensor of shape (capacity, 2)")
+    cnt = _i64(0)
+    _check(load().sj_self_join_noalloc(ptr, n, d, float(eps), pairs_out.data_ptr(), pairs_out.numel() // 2,
+                                       ctypes.byref(cnt), _stream_ptr(stream)))
+    del keep
+    return int(cnt.value)
 
 
 def sj_error_string(status: int) -> str:

@@ -855,3 +855,41 @@ int build_index(Index* ix, const double* pts) {
 }
 
 }  // namespace sj
+
+namespace sj {
+
+// Launchers used by the allocation-free entry point (sj_noalloc.cu): the
+// extent reduction and the FP64 packing on caller-provided memory.
+int launch_extent_raw(const double* pts, int64_t n, int d, unsigned long long* ext, cudaStream_t s) {
+    const int64_t total = n * d;
+    const int bs = 256 - (256 % d);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + bs - 1) / bs, 152 * 8));
+    k_extent<<<blocks, bs, 2 * d * sizeof(unsigned long long), s>>>(pts, total, d, ext, ext + d,
+                                                                    reinterpret_cast<int*>(ext + 2 * d));
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    return SJ_OK;
+}
+
+size_t pack_params_size() { return sizeof(PackParams); }
+
+int pack_params_fill(void* host_pp, const double* lo, int d, int dp, double eps, double pbound, double delta) {
+    PackParams* pp = static_cast<PackParams*>(host_pp);
+    memset(pp, 0, sizeof *pp);
+    for (int k = 0; k < d; ++k) pp->lo[k] = lo[k];
+    pp->d = d;
+    pp->dp = dp;
+    pack_coefficients(eps, pbound, delta, ldexp(1.0, -53), d, dp, pp);
+    return SJ_OK;
+}
+
+int launch_pack_f64_raw(const double* pts, const int32_t* perm, int64_t n, const void* pp_dev, double* xs, double* y,
+                        double* h, double* to, double* ti, cudaStream_t s) {
+    k_pack<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, perm, n, static_cast<const PackParams*>(pp_dev),
+                                                             xs, y, h, to, ti);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    return SJ_OK;
+}
+
+}  // namespace sj
