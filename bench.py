@@ -37,7 +37,9 @@ HEADLINE = "filter_f32"
 VARIANTS = ["filter_f32", "fp64_fma", "fp64_dmma"]
 L2_FLUSH_BYTES = 256 << 20
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
-FP64_PEAK_TFLOPS = 1.25                                   # GB300 nominal FP64
+FP64_DFMA_TFLOPS = 1.009                                  # measured, profiles/fp64_peaks_gb300.txt
+FP64_DMMA_TFLOPS = 1.050                                  # measured, profiles/fp64_peaks_gb300.txt
+KERNEL_NAMES = {"filter_f32": "k_join_cc<float>", "fp64_fma": "k_join_cc<double>", "fp64_dmma": "k_join_dmma"}
 
 
 def parse():
@@ -50,6 +52,7 @@ def parse():
     ap.add_argument("--variants", default=",".join(VARIANTS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0 = sized for ~15 s)")
+    ap.add_argument("--hint", type=int, default=0, help="expected result pairs (0 = the library's automatic pool)")
     return ap.parse_args()
 
 
@@ -164,7 +167,8 @@ def run_native(args):
         r = binding.sj_self_join(h)
         if host_out is not None:
             binding.sj_result_copy(r, host_out)
-        info = (int(r.count), int(r.n_candidates), int(r.n_evaluated), int(r.n_rechecked), int(r.reruns))
+        info = (int(r.count), int(r.n_candidates), int(r.n_evaluated), int(r.n_rechecked), int(r.reruns),
+                float(r.ms_tile))
         binding.sj_result_free(r)
         binding.sj_destroy(h)
         return info
@@ -173,38 +177,42 @@ def run_native(args):
     sampler = ClockSampler(local)
     variants = [v for v in args.variants.split(",") if v]
     for vi, kname in enumerate(variants):
-        opt = binding.sj_default_options(kernel=kname)
+        opt = binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint)
         for _ in range(args.warmup):
             one_step(opt)
         barrier()
         if vi == 0:
-            sampler.start()
+            sampler.start()  # sampled over the timed steps of every kernel
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         launches0 = binding.sj_kernel_launches()
         info = None
+        tile_ms = []
         for k in range(args.steps):
             flush.fill_(float(k))  # evict the inputs from L2 between steps
             ev[k][0].record(stream)
             info = one_step(opt)
             ev[k][1].record(stream)
+            tile_ms.append(info[5])
         barrier()
         launches = binding.sj_kernel_launches() - launches0
-        clocks = sampler.stop() if vi == 0 else None
+        clocks = sampler.stop() if vi == len(variants) - 1 else None
         times = [a.elapsed_time(b) for a, b in ev]
         ms = max_over_ranks(sum(times) / len(times))
-        count, cand, evald, rech, reruns = info
+        count, cand, evald, rech, reruns, _ = info
         results[kname] = {"ms_per_step": ms, "count": count, "n_candidates": cand, "n_evaluated": evald,
                           "n_rechecked": rech, "reruns": reruns, "launches": launches, "clocks": clocks,
-                          "ms_min": min(times), "ms_max": max(times)}
+                          "ms_min": min(times), "ms_max": max(times),
+                          "tile_ms": max_over_ranks(statistics.mean(tile_ms))}
 
-    # kernel-only time of the headline's distance kernel, CUDA events on its stream
+    # the distance-tile kernel's duration: CUDA events the library records on
+    # its stream around the launch, averaged over the timed steps
     head = results[variants[0]]
-    kern_ms = kernel_time(binding, torch, w, pts, stream, variants[0], flush, args)
+    kern_ms = head["tile_ms"]
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     host_pts = torch.from_numpy(w.points).pin_memory()
     host_out = torch.empty((head["count"] + 16, 2), dtype=torch.int32).pin_memory()
-    opt = binding.sj_default_options(kernel=variants[0])
+    opt = binding.sj_default_options(kernel=variants[0], max_pairs_hint=args.hint)
     one_step(opt, host_pts, host_out)
     barrier()
     t_e2e = []
@@ -228,38 +236,26 @@ def run_native(args):
         dist.destroy_process_group()
 
 
-def kernel_time(binding, torch, w, pts, stream, kname, flush, args):
-    """Average duration of the distance-tile kernel alone: the join is run on a
-    built index with CUDA events around sj_self_join's kernel (the count read
-    back is outside the events only by the host synchronisation)."""
-    opt = binding.sj_default_options(kernel=kname)
-    h = binding.sj_build_index(pts, w.eps, opt, stream)
-    for _ in range(2):
-        binding.sj_result_free(binding.sj_self_join(h))
-    ts = []
-    for k in range(max(3, args.steps)):
-        flush.fill_(float(k))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        r = binding.sj_self_join(h)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-        binding.sj_result_free(r)
-    binding.sj_destroy(h)
-    return statistics.mean(ts)
+def kernel_source_sha(kname):
+    """Short hash of the sources of a distance kernel (its file and the shared
+    tile header), to tie committed counters to the code they were taken on."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2209_11287_gb300", "csrc")
+    files = ["sj_join_dmma.cu" if kname == "fp64_dmma" else "sj_join_cc.cu", "sj_join_common.cuh"]
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def read_traffic(kname):
     """DRAM bytes per launch of the distance kernel from the committed ncu
     summary (a line 'dram_bytes_per_launch: <int>' and 'kernel_source_sha:
     <sha>'), or None when absent or taken on different kernel sources."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", f"join_{kname}_uniform4d.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2209_11287_gb300", "csrc", "sj_join_cc.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha(kname)
     vals = {}
     for line in open(path):
         if ":" in line:
@@ -273,40 +269,55 @@ def read_traffic(kname):
         return None
 
 
-def make_line(args, w, results, variants, world, kern_ms, e2e_s, head):
-    kname = variants[0]
-    cand = head["n_candidates"]
-    value = world * cand / (head["ms_per_step"] * 1e-3)
-    # roofline of the distance kernel: FP32 FMA work of the evaluated pairs
-    # (d fma = 2d flop per pair) against the FP32 FMA peak, and its bytes
-    # (points read once + 8 bytes per emitted pair) against HBM
-    flops = 2.0 * w.d * head["n_evaluated"]
-    tfl = flops / (kern_ms * 1e-3) / 1e12
-    bytes_alg = w.n * (4 * 4 + 4 * 3) + 8 * head["count"]
-    gbs = bytes_alg / (kern_ms * 1e-3) / 1e9
+def roofline(kname, w, r, kern_ms):
+    """Roofline of one distance-tile kernel launch.  Arithmetic: d fused
+    multiply-adds (2d flop) per evaluated (query, candidate) pair, in FP32 for
+    the filter (peak from the SM count, FP32 lanes and maximum clock) and in
+    FP64 for the plain kernels (peaks of the committed micro-benchmark,
+    profiles/fp64_peaks_gb300.txt).  Bytes: every packed point read once
+    (coordinates, norm, two thresholds, input index) plus 8 bytes per emitted
+    pair, against the measured HBM copy bandwidth.  The larger fraction is the
+    binding one."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    fp_peak = FP32_FMA_PEAK_TFLOPS if kname != "fp64_fma" else FP64_PEAK_TFLOPS
+    elt = 4 if kname.startswith("filter") else 8
+    dp = 2
+    while dp < w.d:
+        dp *= 2
+    flops = 2.0 * w.d * r["n_evaluated"]
+    tfl = flops / (kern_ms * 1e-3) / 1e12
+    bytes_alg = w.n * (elt * (dp + 3) + 4) + 8 * r["count"]
+    gbs = bytes_alg / (kern_ms * 1e-3) / 1e9
+    fp_peak = {"fp64_fma": FP64_DFMA_TFLOPS, "fp64_dmma": FP64_DMMA_TFLOPS}.get(kname, FP32_FMA_PEAK_TFLOPS)
     frac_alu, frac_hbm = tfl / fp_peak, gbs / hbm_peak
-    traffic = read_traffic(kname)
+    common = {"traffic": read_traffic(kname), "kernel": KERNEL_NAMES.get(kname, kname),
+              "kernel_ms": round(kern_ms, 4), "flop_per_launch": flops, "bytes_per_launch": bytes_alg}
     if frac_alu >= frac_hbm:
-        roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(fp_peak, 2), "unit": "TFLOP/s",
-                "frac": round(frac_alu, 4), "traffic": traffic, "kernel": f"k_join_cc ({kname})",
-                "kernel_ms": round(kern_ms, 4), "hbm_frac": round(frac_hbm, 4)}
-    else:
-        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(frac_hbm, 4), "traffic": traffic, "kernel": f"k_join_cc ({kname})",
-                "kernel_ms": round(kern_ms, 4), "alu_frac": round(frac_alu, 4)}
+        return {"bound": "alu", "achieved": round(tfl, 3), "peak": round(fp_peak, 3), "unit": "TFLOP/s",
+                "frac": round(frac_alu, 4), "hbm_frac": round(frac_hbm, 4), **common}
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(frac_hbm, 4), "alu_frac": round(frac_alu, 4), **common}
+
+
+def make_line(args, w, results, variants, world, kern_ms, e2e_s, head):
+    kname = variants[0]
+    cand = head["n_candidates"]
+    value = world * cand / (head["ms_per_step"] * 1e-3)
+    roof = roofline(kname, w, head, kern_ms)
     var = {}
     for k in variants:
         r = results[k]
-        var[k] = {"ms_per_step": round(r["ms_per_step"], 4), "candidate_pairs_per_s": world * r["n_candidates"] / (r["ms_per_step"] * 1e-3),
+        rk = roofline(k, w, r, r["tile_ms"])
+        var[k] = {"ms_per_step": round(r["ms_per_step"], 4),
+                  "candidate_pairs_per_s": world * r["n_candidates"] / (r["ms_per_step"] * 1e-3),
                   "result_pairs_per_s": world * r["count"] / (r["ms_per_step"] * 1e-3), "result_pairs": r["count"],
-                  "evaluated_pairs": r["n_evaluated"], "rechecked_pairs": r["n_rechecked"], "reruns": r["reruns"]}
+                  "evaluated_pairs": r["n_evaluated"], "rechecked_pairs": r["n_rechecked"], "reruns": r["reruns"],
+                  "tile_kernel_ms": round(r["tile_ms"], 4),
+                  "tile_roofline": {key: rk[key] for key in ("bound", "achieved", "peak", "unit", "frac")}}
     e2e_val = world * cand / e2e_s
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -320,7 +331,7 @@ def make_line(args, w, results, variants, world, kern_ms, e2e_s, head):
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": w.n * w.d * 8,
                 "d2h_bytes_per_step": head["count"] * 8, "ms_per_step": round(e2e_s * 1e3, 3)},
         "gpu_launches": int(head["launches"]),
-        "clocks": head["clocks"],
+        "clocks": results[variants[-1]]["clocks"],
     }
     return line
 

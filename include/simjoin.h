@@ -143,6 +143,9 @@ typedef struct sj_result {
     int64_t n_rechecked;      /* pairs re-decided by the FP64 direct form */
     int32_t reruns;           /* reruns after the page pool overflowed */
     int32_t kernel;           /* SJ_KERNEL_* actually used */
+    double ms_tile;           /* device time of the distance-tile kernel of the
+                                 (last) run, from CUDA events recorded on the
+                                 handle's stream around its launch */
     void* internal;           /* library-owned */
 } sj_result;
 

@@ -74,6 +74,7 @@ class sj_result(ctypes.Structure):
         ("n_rechecked", ctypes.c_int64),
         ("reruns", ctypes.c_int32),
         ("kernel", ctypes.c_int32),
+        ("ms_tile", ctypes.c_double),
         ("internal", ctypes.c_void_p),
     ]
 

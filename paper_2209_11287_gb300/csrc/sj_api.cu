@@ -111,6 +111,8 @@ static void release_index(Index* ix) {
     dev_free(ix->runs, s);
     dev_free(ix->items, s);
     dev_free(ix->counters, s);
+    if (ix->ev_tile[0]) cudaEventDestroy(ix->ev_tile[0]);
+    if (ix->ev_tile[1]) cudaEventDestroy(ix->ev_tile[1]);
 }
 
 static int pick_kernel(const Index* ix) {
@@ -299,11 +301,17 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
     jo.band = band;
     jo.band_cap = band_cap;
     int st = SJ_OK;
+    if (!ix->ev_tile[0]) {
+        SJ_CK(cudaEventCreate(&ix->ev_tile[0]));
+        SJ_CK(cudaEventCreate(&ix->ev_tile[1]));
+    }
     if (ix->n_items > 0) {
+        SJ_CK(cudaEventRecord(ix->ev_tile[0], s));
         if (ix->kernel == SJ_KERNEL_FP64_DMMA)
             st = launch_join_dmma(ix, jo, dist ? 1 : 0);
         else
             st = launch_join_cc(ix, jo, dist ? 1 : 0);
+        if (st == SJ_OK) SJ_CK(cudaEventRecord(ix->ev_tile[1], s));
         if (st == SJ_OK) st = launch_recheck(ix, jo, dist ? 1 : 0);
     }
     unsigned long long c[4] = {0, 0, 0, 0};
@@ -316,6 +324,11 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
         }
     }
     dev_free(band, s);
+    ix->last_tile_ms = 0.0;
+    if (st == SJ_OK && ix->n_items > 0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ix->ev_tile[0], ix->ev_tile[1]) == cudaSuccess) ix->last_tile_ms = ms;
+    }
     *count_out = c[1];
     *rechecked_out = c[2];
     return st;
@@ -385,6 +398,7 @@ int sj_self_join(sj_handle h, sj_result* out) {
     out->n_rechecked = (int64_t)rechecked;
     out->reruns = reruns;
     out->kernel = h->kernel;
+    out->ms_tile = h->last_tile_ms;
     out->internal = ri;
     return st;
 }

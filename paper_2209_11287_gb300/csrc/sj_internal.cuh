@@ -94,8 +94,12 @@ struct Index {
     int64_t n_cells = 0, n_runs = 0, n_items = 0, n_candidates = 0, n_evaluated = 0;
     double filter_band_rel = 0;  // predicted certified band (relative to eps^2)
 
-    // per-join scratch: counters (item queue, result cursor, recheck count)
+    // per-join scratch: counters (item queue, result cursor, recheck count,
+    // recheck queue fill)
     unsigned long long* counters = nullptr;
+    // events around the distance-tile kernel and its last duration
+    cudaEvent_t ev_tile[2] = {nullptr, nullptr};
+    double last_tile_ms = 0.0;
 };
 
 // Result internals.
