@@ -106,6 +106,8 @@ static void release_index(Index* ix) {
     dev_free(ix->thr_out, s);
     dev_free(ix->thr_in, s);
     dev_free(ix->perm, s);
+    dev_free(ix->rows_a, s);
+    dev_free(ix->rows_b, s);
     dev_free(ix->cell_key, s);
     dev_free(ix->cell_start, s);
     dev_free(ix->runs, s);
@@ -115,10 +117,14 @@ static void release_index(Index* ix) {
     if (ix->ev_tile[1]) cudaEventDestroy(ix->ev_tile[1]);
 }
 
+// AUTO: the certified filters always beat the plain FP64 kernels on this part
+// (FP64 runs at ~1/70 of FP32); the tensor-core filter wins once the dot
+// product is long enough to amortise its tiles (measured: d = 64 2.6x faster
+// than the FP32 filter, d = 16 2x slower), the FP32 CUDA-core filter below.
 static int pick_kernel(const Index* ix) {
     int k = ix->opt.kernel;
     if (k != SJ_KERNEL_AUTO) return k;
-    return SJ_KERNEL_FILTER_F32;
+    return (ix->d > 16 && ix->d <= 64) ? SJ_KERNEL_FILTER_BF16X3 : SJ_KERNEL_FILTER_F32;
 }
 
 static int round_dim(int d) {
@@ -202,8 +208,8 @@ int sj_build_index(const double* pts, int64_t n, int32_t d, double eps, const sj
     ix->eps = eps;
     ix->e2 = eps * eps;
     ix->kernel = pick_kernel(ix);
-    if (ix->kernel == SJ_KERNEL_FILTER_BF16X3) {
-        set_error("kernel %d not available in this build", ix->kernel);
+    if (ix->kernel == SJ_KERNEL_FILTER_BF16X3 && ix->dp > 64) {
+        set_error("the tensor-core filter supports d <= 64 (got d = %d)", (int)d);
         delete ix;
         return SJ_ERR_UNSUPPORTED;
     }
@@ -286,7 +292,7 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
                     unsigned long long* rechecked_out) {
     cudaStream_t s = ix->stream;
     const int64_t np = (int64_t)ri->pair_pages.size();
-    SJ_CK(cudaMemsetAsync(ix->counters, 0, 4 * sizeof(unsigned long long), s));
+    SJ_CK(cudaMemsetAsync(ix->counters, 0, kCounters * sizeof(unsigned long long), s));
     // deferred-recheck queue: band pairs (and, with distances, every
     // maybe-in pair); pairs past its end are re-decided in place
     const unsigned long long ev = (unsigned long long)std::max<int64_t>(ix->n_evaluated, 1);
@@ -309,18 +315,23 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
         SJ_CK(cudaEventRecord(ix->ev_tile[0], s));
         if (ix->kernel == SJ_KERNEL_FP64_DMMA)
             st = launch_join_dmma(ix, jo, dist ? 1 : 0);
+        else if (ix->kernel == SJ_KERNEL_FILTER_BF16X3)
+            st = launch_join_tc(ix, jo, dist ? 1 : 0);
         else
             st = launch_join_cc(ix, jo, dist ? 1 : 0);
         if (st == SJ_OK) SJ_CK(cudaEventRecord(ix->ev_tile[1], s));
         if (st == SJ_OK) st = launch_recheck(ix, jo, dist ? 1 : 0);
     }
-    unsigned long long c[4] = {0, 0, 0, 0};
+    unsigned long long c[kCounters] = {};
     if (st == SJ_OK) {
         cudaError_t e = cudaMemcpyAsync(c, ix->counters, sizeof c, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             set_error("join: %s", cudaGetErrorString(e));
             st = SJ_ERR_CUDA;
+        } else if ((int)c[4] != 0) {
+            set_error("a bounded wait in the tensor-core kernel expired");
+            st = SJ_ERR_TIMEOUT;
         }
     }
     dev_free(band, s);

@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <numeric>
 
+#include <cuda_bf16.h>
+
 #include "sj_internal.cuh"
 
 namespace sj {
@@ -373,10 +375,14 @@ __host__ __device__ inline double gamma_n(double u, int k) { return k * u / (1.0
 // formed on the host in binary64, rounded outward to T, and each threshold is
 // one fma rounded down (thr_out) or up (thr_in), so the stored values are on
 // the safe side of the exact ones.
-void pack_coefficients(double eps, double pbound, double delta, double u_t, int d, int dp, PackParams* pp) {
+//
+// `c1_override` > 0 replaces c1 for arithmetic with another error model (the
+// tensor-core filter, see build_index).
+void pack_coefficients(double eps, double pbound, double delta, double u_t, int d, int dp, PackParams* pp,
+                       double c1_override = -1.0) {
     const double g = 2.0 * gamma_n(ldexp(1.0, -53), d + 3);
     const double eta = 2.0 * delta * sqrt((double)d) * (1.0 + ldexp(1.0, -40));
-    const double c1 = 6.2 * gamma_n(u_t, dp + 1);
+    const double c1 = c1_override > 0 ? c1_override : 6.2 * gamma_n(u_t, dp + 1);
     const double so_r = eps * (1.0 + g) + eta;
     const double so = so_r * so_r * (1.0 + ldexp(1.0, -50));
     const double m = 4.0 * u_t;
@@ -679,6 +685,63 @@ static int pack_points(Index* ix, const double* pts, const PackParams& hp) {
     return SJ_OK;
 }
 
+// Exact split of an FP32 value into three bf16 terms (8 significant bits
+// each; y has 24, so y = t1 + t2 + t3 with no rounding error, for normal
+// values): each term is the round-to-nearest bf16 of what is left.
+__device__ __forceinline__ void split3(float y, __nv_bfloat16& t1, __nv_bfloat16& t2, __nv_bfloat16& t3) {
+    t1 = __float2bfloat16_rn(y);
+    const float r1 = y - __bfloat162float(t1);
+    t2 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(t2);
+    t3 = __float2bfloat16_rn(r2);
+}
+
+// Operand rows of the tensor-core filter for every packed point: K slot
+// 6k .. 6k+5 of dim k holds (c1, c2, c1, c3, c2, c1) in the candidate row and
+// (q1, q1, q2, q1, q2, q3) in the query row, so their dot product keeps the
+// six split products with term indices summing to at most 4; slots 6 dp ..
+// 6 dp + 2 hold the split of -||y||^2 / 2 (query row) against ones
+// (candidate row); the rest is zero.
+__global__ void k_pack_split(const float* __restrict__ y, const float* __restrict__ h, int64_t n, int dp, int kp,
+                             __nv_bfloat16* rows_a, __nv_bfloat16* rows_b) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    __nv_bfloat16* a = rows_a + p * kp;
+    __nv_bfloat16* b = rows_b + p * kp;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+    for (int k = 0; k < dp; ++k) {
+        __nv_bfloat16 t1, t2, t3;
+        split3(y[p * dp + k], t1, t2, t3);
+        a[6 * k + 0] = t1; a[6 * k + 1] = t2; a[6 * k + 2] = t1;
+        a[6 * k + 3] = t3; a[6 * k + 4] = t2; a[6 * k + 5] = t1;
+        b[6 * k + 0] = t1; b[6 * k + 1] = t1; b[6 * k + 2] = t2;
+        b[6 * k + 3] = t1; b[6 * k + 4] = t2; b[6 * k + 5] = t3;
+    }
+    __nv_bfloat16 h1, h2, h3;
+    split3(h[p], h1, h2, h3);
+    const int o = 6 * dp;
+    a[o] = one; a[o + 1] = one; a[o + 2] = one;
+    b[o] = h1; b[o + 1] = h2; b[o + 2] = h3;
+    for (int k = o + 3; k < kp; ++k) a[k] = b[k] = zero;
+}
+
+static int pack_split_rows(Index* ix) {
+    cudaStream_t s = ix->stream;
+    const int64_t n = ix->n;
+    ix->kp = tc_kp(ix->dp);
+    __nv_bfloat16 *ra = nullptr, *rb = nullptr;
+    SJ_TRY(dev_alloc_t(&ra, (size_t)n * ix->kp, s));
+    SJ_TRY(dev_alloc_t(&rb, (size_t)n * ix->kp, s));
+    ix->rows_a = ra;
+    ix->rows_b = rb;
+    k_pack_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(static_cast<const float*>(ix->y),
+                                                            static_cast<const float*>(ix->h), n, ix->dp, ix->kp,
+                                                            ra, rb);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    return SJ_OK;
+}
+
 int build_index(Index* ix, const double* pts) {
     cudaStream_t s = ix->stream;
     const int64_t n = ix->n;
@@ -756,26 +819,38 @@ int build_index(Index* ix, const double* pts) {
 
     // ---- packing (independent of the cell count) ----
     SJ_TRY(dev_alloc_t(&ix->xs, (size_t)n * ix->dp, s));
+    // kernel coordinates y = x - centre of the extent: |y_k| <= R_k / 2, which
+    // keeps the norms in the expanded form (and the certified band) small
     PackParams hp{};
-    for (int k = 0; k < d; ++k) hp.lo[k] = ix->lo[k];
     double pb = 0, rmax = 0;
     for (int k = 0; k < d; ++k) {
-        double r = ix->hi[k] - ix->lo[k];
+        hp.lo[k] = 0.5 * (ix->lo[k] + ix->hi[k]);
+        const double r = 0.5 * (ix->hi[k] - ix->lo[k]) * (1.0 + ldexp(1.0, -40));
         pb += r * r;
         rmax = std::max(rmax, r);
     }
     const double pbound = pb * (1.0 + ldexp(1.0, -20));
     hp.d = d;
     hp.dp = ix->dp;
-    const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32;
+    const bool tensor = ix->kernel == SJ_KERNEL_FILTER_BF16X3;
+    const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32 || tensor;
     const double u_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
     const double delta = 1.01 * u_t * rmax;
-    pack_coefficients(ix->eps, pbound, delta, u_t, d, ix->dp, &hp);
+    // tensor-core filter: |s_y - (pc - 2a)| <= gamma_32(dp) (Pq + Pc) for the
+    // FP32 norms plus twice the dot-product error, which is at most
+    // (1.02 K 2^-22 + 2^-23) (Pq + Pc): the split products dropped (three per
+    // dim, below 2^-23 relative together) and an FP32 accumulation of K terms
+    // whose every addition is taken to lose up to 2^-22 relative (truncation).
+    // Doubled for safety.
+    double c1 = -1.0;
+    if (tensor) c1 = 2.0 * gamma_n(ldexp(1.0, -24), ix->dp) + (4.1 * tc_kp(ix->dp) + 2.0) * ldexp(1.0, -22);
+    pack_coefficients(ix->eps, pbound, delta, u_t, d, ix->dp, &hp, c1);
     if (use_f32)
         SJ_TRY(pack_points<float>(ix, pts, hp));
     else
         SJ_TRY(pack_points<double>(ix, pts, hp));
-    ix->filter_band_rel = 2.0 * 6.2 * gamma_n(u_t, ix->dp + 1) * 2.0 * pbound / ix->e2;
+    if (tensor) SJ_TRY(pack_split_rows(ix));
+    ix->filter_band_rel = 2.0 * (c1 > 0 ? c1 : 6.2 * gamma_n(u_t, ix->dp + 1)) * 2.0 * pbound / ix->e2;
 
     unsigned long long M = 0;
     SJ_CK(cudaMemcpyAsync(&M, dcount, 8, cudaMemcpyDeviceToHost, s));
@@ -800,7 +875,8 @@ int build_index(Index* ix, const double* pts) {
         ep.stride[i] = ix->stride[i];
     }
     ep.symmetric = ix->opt.symmetric ? 1 : 0;
-    ep.qmax = ix->opt.queries_per_item > 0 ? std::min(ix->opt.queries_per_item, kQMax) : kQMax;
+    const int qcap = ix->kernel == SJ_KERNEL_FILTER_BF16X3 ? kTcN : kQMax;
+    ep.qmax = ix->opt.queries_per_item > 0 ? std::min(ix->opt.queries_per_item, qcap) : qcap;
     const int64_t Mc = (int64_t)M;
     // dense key -> cell table when the key space is small (neighbour lookups
     // become O(1) instead of binary searches over the cell keys)
@@ -850,7 +926,7 @@ int build_index(Index* ix, const double* pts) {
     dev_free(run_cnt, s);
     dev_free(dtot, s);
     dev_free(table, s);
-    SJ_TRY(dev_alloc_t(&ix->counters, 4, s));
+    SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
     return SJ_OK;
 }
 

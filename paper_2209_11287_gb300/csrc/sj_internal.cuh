@@ -15,6 +15,7 @@ namespace sj {
 constexpr int kMaxM = 6;                         // indexed dims (3^(m-1) runs per cell)
 constexpr int kMaxRuns = 243 + 1;                // 3^(kMaxM-1) + the split self run
 constexpr int kQMax = 16;                        // queries per work item (bitmask width)
+constexpr int kTcN = 64;                         // queries per work item of the tensor-core filter
 constexpr int kThreads = 128;                    // CTA size of the distance kernels
 constexpr int kStage = 256;                      // per-warp staging slots for emitted pairs
 constexpr int64_t kDefaultPagePairs = int64_t(1) << 22;
@@ -87,6 +88,9 @@ struct Index {
     void* thr_out = nullptr;    // n: maybe-in threshold on (y_q.y_c - ||y_q||^2/2)
     void* thr_in = nullptr;     // n: certain-in threshold
     int32_t* perm = nullptr;    // sorted position -> input index
+    void* rows_a = nullptr;     // tensor-core filter: n x kp bf16 split rows, candidate role
+    void* rows_b = nullptr;     // n x kp bf16 split rows, query role
+    int kp = 0;                 // their padded K
     unsigned long long* cell_key = nullptr;
     int32_t* cell_start = nullptr;  // M + 1
     Run* runs = nullptr;
@@ -123,7 +127,15 @@ struct JoinOut {
     unsigned long long band_cap = 0;
 };
 int launch_join_cc(Index* ix, const JoinOut& out, int emit_dist);
+int launch_join_tc(Index* ix, const JoinOut& out, int emit_dist);
 int launch_recheck(Index* ix, const JoinOut& out, int emit_dist);
+
+// Padded K of the tensor-core filter for padded dimension dp: 6 products per
+// dim plus 3 slots for the query term, rounded up to the MMA K of 16.
+constexpr int tc_kp(int dp) { return (6 * dp + 3 + 15) / 16 * 16; }
+// Number of counters of a join (item queue, result cursor, rechecked,
+// recheck-queue fill, error flag, spare).
+constexpr int kCounters = 8;
 int launch_join_dmma(Index* ix, const JoinOut& out, int emit_dist);
 
 // ---- radix sort / scan (sj_index.cu) ------------------------------------------

@@ -384,6 +384,7 @@ JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist) {
     p.capacity = out.capacity;
     p.e2 = ix->e2;
     p.d = ix->d;
+    p.dp = ix->dp;
     p.emit_dist = emit_dist;
     p.band = out.band;
     p.band_cap = out.band_cap;

@@ -25,6 +25,7 @@ struct JoinParams {
     unsigned long long capacity;   // pairs the pool holds
     double e2;
     int d;
+    int dp;            // padded dimension (row stride of xs)
     int emit_dist;
     // deferred re-decisions: pairs whose certified bound straddles eps (and,
     // when distances are emitted, every maybe-in pair) are queued here and
@@ -246,6 +247,21 @@ __device__ __forceinline__ uint32_t load_item_warp(ItemSmem<T, DP>& S, const Joi
     if (lane == 0) S.rpre[0] = 0;
     __syncwarp();
     return carry;
+}
+
+// Candidate v (0 <= v < C) of an item whose runs are (rstart, rpre, rmir).
+__device__ __forceinline__ int32_t map_candidate_tc(const int32_t* rstart, const uint32_t* rpre, const uint8_t* rmir,
+                                                    int nr, uint32_t v, bool& mirror) {
+    int lo = 0, hi = nr - 1;  // last r with rpre[r] <= v
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rpre[mid] <= v)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    mirror = rmir[lo] != 0;
+    return rstart[lo] + (int32_t)(v - rpre[lo]);
 }
 
 // Candidate v (0 <= v < C) of the item: its sorted position and mirror flag.

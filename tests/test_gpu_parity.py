@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-KERNELS = ["fp64_fma", "fp64_dmma", "filter_f32"]
+KERNELS = ["fp64_fma", "fp64_dmma", "filter_f32", "filter_bf16x3"]
 
 
 @pytest.fixture(scope="module", autouse=True)
