@@ -179,12 +179,26 @@ SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj
 
 /* ---- batched joins ----------------------------------------------------- */
 /*
- * Runs `count` independent self-joins (instance k: pts[k] with n[k] points of
- * dimension d[k] and distance eps[k]; pts[k] host or device) with all
- * indexes built by segmented kernels and all distance tiles in one
- * persistent launch; results go to per_instance_out[k] (each released with
- * sj_result_free).  Errors as for sj_build_index / sj_self_join; on error no
- * result needs freeing.
+ * Runs `count` independent self-joins (instance k: pts[k], n[k] row-major
+ * points of dimension d[k], distance eps[k]; pts[k] host or device memory,
+ * read only during the call).  This is the batched form of the paper's
+ * Sec. III join for many small problems: instances of the same padded
+ * dimension (the next power of two >= d, at least 2) form one group; a
+ * group's index is built by segmented kernels over composite cell keys
+ * (instance << S | cell key of the instance's own grid, Sec. III-A) and all
+ * of the group's work items run in one persistent distance-tile launch
+ * (kernels SJ_KERNEL_FILTER_F32, the AUTO choice, or SJ_KERNEL_FP64_FMA;
+ * others give SJ_ERR_UNSUPPORTED).  Pairs carry instance-local indices and
+ * satisfy the same decision rule as sj_self_join.  The device takes each
+ * instance's result pages from one shared pool (opt->page_pairs rounded up
+ * to a power of two of at least 64, default 65536 pairs a page); when the
+ * pool runs out the joins are rerun with pools sized from the exact counts
+ * (reruns in every result).  per_instance_out[k] gets instance k's result (n_candidates and
+ * n_evaluated per instance, n_rechecked 0, ms_tile the summed tile-kernel
+ * time of all groups); release each with sj_result_free (the pool is freed
+ * with the last of them).  Errors: SJ_ERR_ARG (a bad instance, named in
+ * sj_last_error_message), SJ_ERR_OOM, SJ_ERR_CUDA, SJ_ERR_UNSUPPORTED,
+ * SJ_ERR_RESULT_OVERFLOW; on error no result needs freeing.
  */
 SJ_API int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps,
                   int32_t count, const sj_options* opt, void* stream, sj_result* per_instance_out);

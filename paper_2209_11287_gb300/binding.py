@@ -337,6 +337,26 @@ def self_join(points, eps: float, kernel="auto", emit_distances=False, symmetric
     return pairs, dists, stats
 
 
+def join_batch(points_list, eps_list, kernel="auto", emit_distances=False, symmetric=True, page_pairs=0,
+               max_pairs_hint=0, stream=None):
+    """Batched self-joins in one call: returns one (pairs, distances or None,
+    stats) per instance, the results already copied to the host and freed."""
+    opt = sj_default_options(kernel=kernel, emit_distances=int(emit_distances), symmetric=int(symmetric),
+                             page_pairs=page_pairs, max_pairs_hint=max_pairs_hint)
+    res = sj_join_batch(points_list, eps_list, opt, stream)
+    out = []
+    try:
+        for r in res:
+            pairs, dists = sj_result_copy(r)
+            out.append((pairs, dists, dict(count=int(r.count), n_candidates=int(r.n_candidates),
+                                           n_evaluated=int(r.n_evaluated), reruns=int(r.reruns),
+                                           kernel=int(r.kernel), ms_tile=float(r.ms_tile))))
+    finally:
+        for r in res:
+            sj_result_free(r)
+    return out
+
+
 def pairs_to_keys(pairs: np.ndarray) -> np.ndarray:
     """Sorted 64-bit keys (i << 32) | j of an (i, j) int32 pair array."""
     p = np.asarray(pairs).astype(np.int64)

@@ -281,6 +281,18 @@ static int alloc_pages(ResultImpl* ri, int64_t pages_needed, int64_t page_pairs,
     return SJ_OK;
 }
 
+// The page pool shared by the results of one batched join, freed with the
+// last of them.
+struct PoolHolder {
+    cudaStream_t stream = nullptr;
+    int32_t* block = nullptr;
+    double* dblock = nullptr;
+    ~PoolHolder() {
+        dev_free(block, stream);
+        dev_free(dblock, stream);
+    }
+};
+
 static void free_result_impl(ResultImpl* ri) {
     if (!ri) return;
     dev_free(ri->block, ri->stream);
@@ -353,7 +365,7 @@ int sj_self_join(sj_handle h, sj_result* out) {
     }
     memset(out, 0, sizeof *out);
     int64_t page_pairs = h->opt.page_pairs > 0 ? h->opt.page_pairs : kDefaultPagePairs;
-    int page_log2 = 0;
+    int page_log2 = 6;  // at least 64 pairs a page (one claiming lane per page in a warp's flush)
     while ((int64_t(1) << page_log2) < page_pairs) ++page_log2;
     page_pairs = int64_t(1) << page_log2;
     const bool dist = h->opt.emit_distances != 0;
@@ -462,10 +474,318 @@ int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj_option
 int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps, int32_t count,
                   const sj_options* opt, void* stream, sj_result* per_instance_out) {
     clear_error();
-    (void)pts; (void)n; (void)d; (void)eps; (void)opt; (void)stream; (void)per_instance_out;
-    if (count < 0) return SJ_ERR_ARG;
-    set_error("batched joins are not built yet");
-    return SJ_ERR_UNSUPPORTED;
+    if (!pts || !n || !d || !eps || !per_instance_out || count < 1) {
+        set_error("invalid batch arguments");
+        return SJ_ERR_ARG;
+    }
+    for (int32_t k = 0; k < count; ++k) {
+        if (!pts[k] || n[k] < 1 || n[k] > 0x7FFFFFFFll || d[k] < 1 || d[k] > SJ_MAX_D || !(eps[k] > 0) ||
+            !isfinite(eps[k])) {
+            set_error("invalid batch instance %d: n=%lld d=%d eps=%g", (int)k, (long long)n[k], (int)d[k], eps[k]);
+            return SJ_ERR_ARG;
+        }
+        memset(&per_instance_out[k], 0, sizeof(sj_result));
+    }
+    sj_options o;
+    sj_default_options(&o);
+    if (opt) o = *opt;
+    int kernel = o.kernel == SJ_KERNEL_AUTO ? SJ_KERNEL_FILTER_F32 : o.kernel;
+    if (kernel != SJ_KERNEL_FILTER_F32 && kernel != SJ_KERNEL_FP64_FMA) {
+        set_error("batched joins run the FP32 filter or the FP64 CUDA-core kernel (got kernel %d)", kernel);
+        return SJ_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    SJ_CK(cudaGetDevice(&dev));
+    const bool dist = o.emit_distances != 0;
+
+    // ---- groups by padded dimension; host inputs are staged on the device ----
+    std::vector<double*> staged;
+    std::vector<std::unique_ptr<BatchGroup>> groups;
+    int st = SJ_OK;
+    auto cleanup = [&]() {
+        for (auto& g : groups) {
+            release_index(&g->ix);
+            dev_free(g->d_off, s);
+            dev_free(g->d_gid, s);
+            dev_free(g->d_e2, s);
+            dev_free(g->d_inst_of_sorted, s);
+            dev_free(g->d_item_inst, s);
+        }
+        for (double* p : staged) dev_free(p, s);
+        cudaStreamSynchronize(s);
+    };
+    {
+        std::vector<int> order(count);
+        for (int k = 0; k < count; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return round_dim(d[a]) < round_dim(d[b]); });
+        size_t i = 0;
+        while (i < order.size() && st == SJ_OK) {
+            const int dp = round_dim(d[order[i]]);
+            auto g = std::make_unique<BatchGroup>();
+            g->ix.device = dev;
+            g->ix.stream = s;
+            g->ix.opt = o;
+            g->ix.kernel = kernel;
+            g->ix.d = dp;
+            g->ix.dp = dp;
+            g->off.push_back(0);
+            std::vector<const double*> src;
+            std::vector<int32_t> dof;
+            for (; i < order.size() && round_dim(d[order[i]]) == dp; ++i) {
+                const int k = order[i];
+                const double* p = pts[k];
+                if (!is_device_pointer(p)) {
+                    double* c = nullptr;
+                    st = dev_alloc_t(&c, (size_t)n[k] * d[k], s);
+                    if (st != SJ_OK) break;
+                    staged.push_back(c);
+                    cudaError_t e = cudaMemcpyAsync(c, p, (size_t)n[k] * d[k] * sizeof(double),
+                                                    cudaMemcpyHostToDevice, s);
+                    if (e != cudaSuccess) {
+                        set_error("host-to-device copy: %s", cudaGetErrorString(e));
+                        st = SJ_ERR_CUDA;
+                        break;
+                    }
+                    p = c;
+                }
+                src.push_back(p);
+                dof.push_back(d[k]);
+                g->gids.push_back(k);
+                g->eps.push_back(eps[k]);
+                g->off.push_back(g->off.back() + n[k]);
+            }
+            if (st != SJ_OK) break;
+            g->n_inst = (int)g->gids.size();
+            g->ix.n = g->off.back();
+            if (g->ix.n > 0x7FFFFFFFll) {
+                set_error("a batch group holds more than 2^31 - 1 points");
+                st = SJ_ERR_ARG;
+                break;
+            }
+            st = build_batch_group(g.get(), src.data(), dof.data());
+            if (st == SJ_OK) st = dev_alloc_t(&g->d_gid, (size_t)g->n_inst, s);
+            if (st == SJ_OK) {
+                cudaError_t e = cudaMemcpyAsync(g->d_gid, g->gids.data(), g->n_inst * sizeof(int32_t),
+                                                cudaMemcpyHostToDevice, s);
+                if (e != cudaSuccess) st = SJ_ERR_CUDA;
+            }
+            groups.push_back(std::move(g));
+        }
+    }
+    if (st != SJ_OK) {
+        cleanup();
+        return st;
+    }
+
+    // ---- output: per-instance page tables over one shared pool ----
+    int64_t page_pairs = o.page_pairs > 0 ? o.page_pairs : (int64_t(1) << 16);
+    int page_log2 = 6;  // at least 64 pairs a page (one claiming lane per page in a warp's flush)
+    while ((int64_t(1) << page_log2) < page_pairs) ++page_log2;
+    page_pairs = int64_t(1) << page_log2;
+    std::vector<int64_t> cand(count, 0), eval(count, 0);
+    for (auto& g : groups)
+        for (int i = 0; i < g->n_inst; ++i) {
+            cand[g->gids[i]] = g->cand[i];
+            eval[g->gids[i]] = g->eval[i];
+        }
+    std::vector<long long> toff(count + 1, 0);
+    std::vector<int32_t> maxp(count);
+    for (int k = 0; k < count; ++k) {
+        const long long bound = std::min<long long>(cand[k], (long long)n[k] * n[k]);
+        maxp[k] = (int32_t)((bound + page_pairs - 1) / page_pairs);
+        toff[k + 1] = toff[k] + maxp[k];
+    }
+    // every page is claimed once, so the exact counts fill exactly this many
+    auto pool_pages_for = [&](const std::vector<long long>& want) {
+        long long pages = 0;
+        for (int k = 0; k < count; ++k) pages += (want[k] + page_pairs - 1) / page_pairs;
+        return std::max<long long>(pages, 1);
+    };
+    std::vector<long long> want(count);
+    for (int k = 0; k < count; ++k)
+        want[k] = o.max_pairs_hint > 0 ? o.max_pairs_hint / count : std::min<long long>(cand[k], 64ll * n[k]);
+    long long n_pages = pool_pages_for(want);
+
+    int32_t* table = nullptr;
+    long long* dtoff = nullptr;
+    int32_t* dmaxp = nullptr;
+    unsigned long long* cursor = nullptr;  // count cursors, pool_next, error flag
+    BatchJoin* dbj = nullptr;
+    std::shared_ptr<PoolHolder> pool;
+    auto free_meta = [&]() {
+        dev_free(table, s);
+        dev_free(dtoff, s);
+        dev_free(dmaxp, s);
+        dev_free(cursor, s);
+        dev_free(dbj, s);
+    };
+    if ((st = dev_alloc_t(&table, (size_t)std::max<long long>(toff[count], 1), s)) == SJ_OK &&
+        (st = dev_alloc_t(&dtoff, (size_t)count, s)) == SJ_OK && (st = dev_alloc_t(&dmaxp, (size_t)count, s)) == SJ_OK &&
+        (st = dev_alloc_t(&cursor, (size_t)count + 2, s)) == SJ_OK &&
+        (st = dev_alloc_t(&dbj, groups.size(), s)) == SJ_OK) {
+        cudaError_t e = cudaMemcpyAsync(dtoff, toff.data(), count * sizeof(long long), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dmaxp, maxp.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) st = SJ_ERR_CUDA;
+    }
+    std::vector<unsigned long long> cur(count + 2, 0);
+    int reruns = 0;
+    double tile_ms = 0.0;
+    for (int attempt = 0; attempt < 3 && st == SJ_OK; ++attempt) {
+        pool = std::make_shared<PoolHolder>();
+        pool->stream = s;
+        st = dev_alloc_t(&pool->block, (size_t)n_pages * page_pairs * 2, s);
+        if (st == SJ_OK && dist) st = dev_alloc_t(&pool->dblock, (size_t)n_pages * page_pairs, s);
+        if (st != SJ_OK) break;
+        cudaError_t e = cudaMemsetAsync(table, 0xFF, std::max<long long>(toff[count], 1) * sizeof(int32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, (count + 2) * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) {
+            set_error("batch reset: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+            break;
+        }
+        tile_ms = 0.0;
+        for (size_t gi = 0; gi < groups.size() && st == SJ_OK; ++gi) {
+            BatchGroup& g = *groups[gi];
+            BatchJoin bj{};
+            bj.item_inst = g.d_item_inst;
+            bj.inst_of_sorted = g.d_inst_of_sorted;
+            bj.inst_off = g.d_off;
+            bj.inst_gid = g.d_gid;
+            bj.inst_e2 = g.d_e2;
+            bj.pool = reinterpret_cast<int2*>(pool->block);
+            bj.dpool = pool->dblock;
+            bj.page_log2 = page_log2;
+            bj.n_pages = n_pages;
+            bj.pool_next = cursor + count;
+            bj.page_table = table;
+            bj.table_off = dtoff;
+            bj.max_pages = dmaxp;
+            bj.cursor = cursor;
+            bj.error = cursor + count + 1;
+            e = cudaMemcpyAsync(dbj + gi, &bj, sizeof bj, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                st = SJ_ERR_CUDA;
+                break;
+            }
+            Index* ix = &g.ix;
+            if (ix->n_items == 0) continue;
+            const unsigned long long ev = (unsigned long long)std::max<int64_t>(ix->n_evaluated, 1);
+            unsigned long long band_cap =
+                std::min<unsigned long long>(ev, std::max<unsigned long long>(1ull << 20, dist ? ev / 8 : ev / 64));
+            int2* band = nullptr;
+            if ((st = dev_alloc_t(&band, (size_t)band_cap, s)) != SJ_OK) break;
+            JoinOut jo;
+            jo.band = band;
+            jo.band_cap = band_cap;
+            jo.batch = dbj + gi;
+            e = cudaMemsetAsync(ix->counters, 0, kCounters * sizeof(unsigned long long), s);
+            if (e == cudaSuccess && !ix->ev_tile[0]) {
+                e = cudaEventCreate(&ix->ev_tile[0]);
+                if (e == cudaSuccess) e = cudaEventCreate(&ix->ev_tile[1]);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ix->ev_tile[0], s);
+            if (e != cudaSuccess) st = SJ_ERR_CUDA;
+            if (st == SJ_OK) st = launch_join_cc(ix, jo, dist ? 1 : 0);
+            if (st == SJ_OK && cudaEventRecord(ix->ev_tile[1], s) != cudaSuccess) st = SJ_ERR_CUDA;
+            if (st == SJ_OK) st = launch_recheck(ix, jo, dist ? 1 : 0);
+            dev_free(band, s);
+        }
+        if (st != SJ_OK) break;
+        e = cudaMemcpyAsync(cur.data(), cursor, (count + 2) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("batch join: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+            break;
+        }
+        for (auto& g : groups) {
+            float ms = 0.f;
+            if (g->ix.n_items > 0 && cudaEventElapsedTime(&ms, g->ix.ev_tile[0], g->ix.ev_tile[1]) == cudaSuccess)
+                tile_ms += ms;
+        }
+        if (cur[count + 1] != 0) {
+            set_error("a wait for a result page claim expired");
+            st = SJ_ERR_TIMEOUT;
+            break;
+        }
+        bool overflow = cur[count] > (unsigned long long)n_pages;
+        int bad = -1;
+        for (int k = 0; k < count && bad < 0; ++k)
+            if (cur[k] > (unsigned long long)maxp[k] * (unsigned long long)page_pairs) bad = k;
+        if (bad >= 0) {  // a count above the instance's candidate count: cannot happen
+            set_error("instance %d emitted %llu pairs, above its %lld candidates", bad, cur[bad],
+                      (long long)cand[bad]);
+            st = SJ_ERR_CUDA;
+            break;
+        }
+        if (!overflow) break;
+        if (attempt == 2) {
+            set_error("batched result larger than its page pool (%llu pages wanted, %lld held)", cur[count],
+                      n_pages);
+            st = SJ_ERR_RESULT_OVERFLOW;
+            break;
+        }
+        // regrow to the exact counts and run the joins once more
+        for (int k = 0; k < count; ++k) want[k] = (long long)cur[k];
+        n_pages = pool_pages_for(want);
+        reruns = attempt + 1;
+    }
+    if (st != SJ_OK) {
+        free_meta();
+        pool.reset();
+        cleanup();
+        return st;
+    }
+    std::vector<int32_t> htable((size_t)std::max<long long>(toff[count], 1));
+    if (cudaMemcpyAsync(htable.data(), table, htable.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("batch page table read-back failed");
+        free_meta();
+        pool.reset();
+        cleanup();
+        return SJ_ERR_CUDA;
+    }
+    for (int k = 0; k < count; ++k) {
+        ResultImpl* ri = new (std::nothrow) ResultImpl();
+        if (!ri) {
+            for (int j = 0; j < k; ++j) sj_result_free(&per_instance_out[j]);
+            free_meta();
+            pool.reset();
+            cleanup();
+            return SJ_ERR_OOM;
+        }
+        ri->stream = s;
+        ri->shared_pool = pool;
+        const long long cnt = (long long)cur[k];
+        const long long used = std::min<long long>((cnt + page_pairs - 1) / page_pairs, maxp[k]);
+        for (long long i = 0; i < used; ++i) {
+            const int32_t pg = htable[(size_t)(toff[k] + i)];
+            if (pg < 0) break;  // (only after an overflow)
+            ri->pair_pages.push_back(pool->block + (size_t)pg * page_pairs * 2);
+            if (dist) ri->dist_pages.push_back(pool->dblock + (size_t)pg * page_pairs);
+        }
+        sj_result& r = per_instance_out[k];
+        r.count = cnt;
+        r.page_pairs = page_pairs;
+        r.n_pages = (int32_t)ri->pair_pages.size();
+        r.has_distances = dist ? 1 : 0;
+        r.pair_pages = ri->pair_pages.data();
+        r.dist_pages = dist ? ri->dist_pages.data() : nullptr;
+        r.n_candidates = cand[k];
+        r.n_evaluated = eval[k];
+        r.n_rechecked = 0;
+        r.reruns = reruns;
+        r.kernel = kernel;
+        r.ms_tile = tile_ms;
+        r.internal = ri;
+    }
+    free_meta();
+    pool.reset();
+    cleanup();
+    return st;
 }
 
 }  // extern "C"

@@ -441,6 +441,10 @@ struct EnumParams {
     int symmetric;
     int qmax;
     const int32_t* table;  // dense key -> cell index (-1 = empty), or null
+    // a cell key is prefix | local key: the grid arithmetic uses the local
+    // part (key & local_mask), neighbour keys keep the prefix (a batched
+    // index puts the instance number there; a single index has no prefix)
+    unsigned long long local_mask;
 };
 
 __device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long* a, int64_t n, unsigned long long v) {
@@ -490,7 +494,8 @@ __device__ void visit_runs(const EnumParams& e, const unsigned long long* __rest
         f(cell_start[0], cell_start[n_cells], false);
         return;
     }
-    const unsigned long long key = cell_key[c];
+    const unsigned long long key = cell_key[c] & e.local_mask;
+    const unsigned long long prefix = cell_key[c] & ~e.local_mask;
     int64_t cc[kMaxM];
     for (int k = 0; k < e.m; ++k) cc[k] = (int64_t)((key / e.stride[k]) % (unsigned long long)e.ncell[k]);
     const int mm = e.m - 1;
@@ -515,7 +520,7 @@ __device__ void visit_runs(const EnumParams& e, const unsigned long long* __rest
         }
         if (!inside) continue;
         if (e.symmetric && sign < 0) continue;
-        const unsigned long long base = (unsigned long long)((long long)key + delta);
+        const unsigned long long base = prefix | (unsigned long long)((long long)key + delta);
         auto emit_range = [&](int64_t a_l, int64_t b_l, bool mirror) {
             if (a_l > b_l) return;
             int64_t ca, cb;
@@ -641,7 +646,7 @@ static int choose_grid(Index* ix) {
     for (const Cand& c : cand) {
         if ((int)take.size() >= want) break;
         if (ix->opt.indexed_dims <= 0 && c.ncell < 3) continue;  // no pruning from <3 cells
-        if (prod * (long double)c.ncell > ldexpl(1.0L, 62)) continue;
+        if (prod * (long double)c.ncell > ldexpl(1.0L, ix->key_bits_cap)) continue;
         prod *= (long double)c.ncell;
         take.push_back(c);
     }
@@ -892,6 +897,7 @@ int build_index(Index* ix, const double* pts) {
         SJ_CK(cudaGetLastError());
     }
     ep.table = table;
+    ep.local_mask = ~0ull;
     uint32_t *run_cnt, *item_cnt, *run_off, *item_off;
     EnumTotals* dtot;
     SJ_TRY(dev_alloc_t(&run_cnt, (size_t)Mc * 4, s));
@@ -965,6 +971,449 @@ int launch_pack_f64_raw(const double* pts, const int32_t* perm, int64_t n, const
                                                              xs, y, h, to, ti);
     note_launch();
     SJ_CK(cudaGetLastError());
+    return SJ_OK;
+}
+
+}  // namespace sj
+
+// ===========================================================================
+// Batched index (sj_join_batch): the instances of one group (same padded
+// dimension) share one index whose cell keys are instance << S | local key,
+// built with segmented versions of the kernels above.
+// ===========================================================================
+namespace sj {
+
+// Grid and threshold parameters of one instance.
+struct BInst {
+    int m;
+    int dims[kMaxM];
+    double lo[kMaxM];
+    int64_t ncell[kMaxM];
+    unsigned long long stride[kMaxM];
+    double inv_w;
+    double a_out, b_out, a_in, b_in;
+    int has_in;
+};
+
+__device__ __forceinline__ int inst_of_position(const long long* __restrict__ off, int n_inst, long long p) {
+    int lo = 0, hi = n_inst - 1;  // last instance whose first point is <= p
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= p)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Copies the instances' points (device pointers) into one row-major array of
+// padded rows, zero beyond each instance's d, and records each point's instance.
+__global__ void k_bgather(const double* const* __restrict__ src, const int32_t* __restrict__ d_of,
+                          const long long* __restrict__ off, int n_inst, int64_t n, int dp, double* X,
+                          int32_t* inst_of) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int k = inst_of_position(off, n_inst, p);
+    const int d = d_of[k];
+    const double* row = src[k] + (p - off[k]) * d;
+    for (int c = 0; c < dp; ++c) X[p * dp + c] = c < d ? row[c] : 0.0;
+    inst_of[p] = k;
+}
+
+// One block per instance: per-dim min / max as order keys and a flag for a
+// non-finite coordinate; ext[k] holds 2 dp + 1 words.
+__global__ void k_bextent(const double* __restrict__ X, const long long* __restrict__ off, int dp,
+                          unsigned long long* ext) {
+    extern __shared__ unsigned long long s_ext[];  // [2 * dp + 1]
+    const int k = blockIdx.x;
+    for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+        s_ext[c] = ~0ull;
+        s_ext[dp + c] = 0ull;
+    }
+    if (threadIdx.x == 0) s_ext[2 * dp] = 0ull;
+    __syncthreads();
+    const int64_t b = off[k] * dp, e = off[k + 1] * dp;
+    unsigned long long mn = ~0ull, mx = 0ull;
+    int bad = 0;
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {  // blockDim is a multiple of dp
+        const unsigned long long w = (unsigned long long)__double_as_longlong(X[i]);
+        if (((w >> 52) & 0x7FFull) == 0x7FFull) {
+            bad = 1;
+            continue;
+        }
+        const unsigned long long o = (w >> 63) ? ~w : (w | 0x8000000000000000ull);
+        mn = o < mn ? o : mn;
+        mx = o > mx ? o : mx;
+    }
+    const int c = threadIdx.x % dp;
+    if (mn <= mx) {
+        atomicMin(&s_ext[c], mn);
+        atomicMax(&s_ext[dp + c], mx);
+    }
+    if (bad) atomicOr(&s_ext[2 * dp], 1ull);
+    __syncthreads();
+    for (int c2 = threadIdx.x; c2 < 2 * dp + 1; c2 += blockDim.x) ext[(int64_t)k * (2 * dp + 1) + c2] = s_ext[c2];
+}
+
+__global__ void k_bkeys(const double* __restrict__ X, int64_t n, int dp, const int32_t* __restrict__ inst_of,
+                        const BInst* __restrict__ P, int shift, unsigned long long* keys, int32_t* ids) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = inst_of[i];
+    const BInst& g = P[k];
+    unsigned long long key = 0;
+    for (int t = 0; t < g.m; ++t) {
+        const int64_t c = cell_coord(X[i * dp + g.dims[t]], g.lo[t], g.inv_w, g.ncell[t]);
+        key += (unsigned long long)c * g.stride[t];
+    }
+    keys[i] = ((unsigned long long)k << shift) | key;
+    ids[i] = (int32_t)i;
+}
+
+template <typename T>
+__global__ void k_bpack(const double* __restrict__ X, const int32_t* __restrict__ perm,
+                        const int32_t* __restrict__ inst_of, const BInst* __restrict__ P,
+                        const double* __restrict__ centre, int64_t n, int dp, double* xs, T* y, T* h, T* thr_out,
+                        T* thr_in, int32_t* inst_of_sorted) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t src = perm[p];
+    const int k = inst_of[src];
+    const BInst& g = P[k];
+    T nrm = T(0);
+    for (int c = 0; c < dp; ++c) {
+        const double v = X[src * dp + c];
+        xs[p * dp + c] = v;
+        const T yc = T(v - centre[(int64_t)k * dp + c]);
+        y[p * dp + c] = yc;
+        nrm = fma_pack(yc, yc, nrm);
+    }
+    h[p] = -nrm * T(0.5);
+    thr_out[p] = thr_down(g.a_out, nrm, g.b_out);
+    thr_in[p] = g.has_in ? thr_up(g.a_in, nrm, g.b_in) : T(INFINITY);
+    inst_of_sorted[p] = k;
+}
+
+struct BEnum {
+    int shift, symmetric, qmax;
+};
+
+__device__ __forceinline__ EnumParams benum_params(const BEnum& b, const BInst& g) {
+    EnumParams e{};
+    e.m = g.m;
+    for (int t = 0; t < kMaxM; ++t) {
+        e.ncell[t] = g.ncell[t];
+        e.stride[t] = g.stride[t];
+    }
+    e.symmetric = b.symmetric;
+    e.qmax = b.qmax;
+    e.table = nullptr;
+    e.local_mask = (1ull << b.shift) - 1ull;
+    return e;
+}
+
+__global__ void k_benum_count(BEnum b, const BInst* __restrict__ P, const unsigned long long* __restrict__ cell_key,
+                              const int32_t* __restrict__ cell_start, int64_t n_cells, uint32_t* run_cnt,
+                              uint32_t* item_cnt, unsigned long long* inst_eval, unsigned long long* inst_sq,
+                              EnumTotals* tot) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long my_runs = 0, my_items = 0;
+    if (c < n_cells) {
+        const int k = (int)(cell_key[c] >> b.shift);
+        const EnumParams e = benum_params(b, P[k]);
+        const int64_t q = cell_start[c + 1] - cell_start[c];
+        uint32_t nr = 0;
+        unsigned long long ev = 0;
+        if (e.m == 0) {  // the instance is one cell: its own points
+            nr = 1;
+            ev = (unsigned long long)q;
+        } else {
+            visit_runs(e, cell_key, cell_start, n_cells, c, [&](int32_t a, int32_t z, bool) {
+                ++nr;
+                ev += (unsigned long long)(z - a);
+            });
+        }
+        run_cnt[c] = nr;
+        const uint32_t ni = (uint32_t)((q + e.qmax - 1) / e.qmax);
+        item_cnt[c] = ni;
+        atomicAdd(&inst_eval[k], ev * (unsigned long long)q);
+        atomicAdd(&inst_sq[k], (unsigned long long)q * (unsigned long long)q);
+        my_runs = nr;
+        my_items = ni;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        my_runs += __shfl_down_sync(0xffffffffu, my_runs, o);
+        my_items += __shfl_down_sync(0xffffffffu, my_items, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&tot->n_runs, my_runs);
+        atomicAdd(&tot->n_items, my_items);
+    }
+}
+
+__global__ void k_benum_fill(BEnum b, const BInst* __restrict__ P, const unsigned long long* __restrict__ cell_key,
+                             const int32_t* __restrict__ cell_start, int64_t n_cells,
+                             const uint32_t* __restrict__ run_off, const uint32_t* __restrict__ item_off, Run* runs,
+                             Item* items, int32_t* item_inst) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n_cells) return;
+    const int k = (int)(cell_key[c] >> b.shift);
+    const EnumParams e = benum_params(b, P[k]);
+    uint32_t r = run_off[c];
+    const uint32_t r0 = r;
+    if (e.m == 0) {
+        Run rr;
+        rr.start = cell_start[c];
+        rr.end_flags = (uint32_t)cell_start[c + 1];
+        runs[r++] = rr;
+    } else {
+        visit_runs(e, cell_key, cell_start, n_cells, c, [&](int32_t a, int32_t z, bool mirror) {
+            Run rr;
+            rr.start = a;
+            rr.end_flags = (uint32_t)z | (mirror ? kMirrorBit : 0u);
+            runs[r++] = rr;
+        });
+    }
+    const int32_t q0 = cell_start[c], q1 = cell_start[c + 1];
+    uint32_t it = item_off[c];
+    for (int32_t q = q0; q < q1; q += e.qmax) {
+        Item x;
+        x.q0 = q;
+        x.q1 = q + e.qmax < q1 ? q + e.qmax : q1;
+        x.r0 = (int32_t)r0;
+        x.r1 = (int32_t)r;
+        items[it] = x;
+        item_inst[it] = k;
+        ++it;
+    }
+}
+
+// Sorted keys -> cell table (cell_key, cell_start), with one read-back of
+// the cell count.
+static int build_cells(const unsigned long long* keys, int64_t n, unsigned long long** cell_key, int32_t** cell_start,
+                       int64_t* n_cells, cudaStream_t s) {
+    uint32_t *flags = nullptr, *idx = nullptr;
+    unsigned long long* dcount = nullptr;
+    unsigned long long* ck = nullptr;
+    int32_t* cs = nullptr;
+    SJ_TRY(dev_alloc_t(&flags, (size_t)n, s));
+    SJ_TRY(dev_alloc_t(&idx, (size_t)n, s));
+    SJ_TRY(dev_alloc_t(&dcount, 1, s));
+    SJ_TRY(dev_alloc_t(&ck, (size_t)n, s));
+    SJ_TRY(dev_alloc_t(&cs, (size_t)n + 1, s));
+    k_heads<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, flags);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    SJ_TRY(scan_exclusive_u32(flags, idx, n, s));
+    k_cells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, flags, idx, n, ck, cs, dcount);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    unsigned long long M = 0;
+    SJ_CK(cudaMemcpyAsync(&M, dcount, 8, cudaMemcpyDeviceToHost, s));
+    SJ_CK(cudaStreamSynchronize(s));
+    dev_free(flags, s);
+    dev_free(idx, s);
+    dev_free(dcount, s);
+    *cell_key = ck;
+    *cell_start = cs;
+    *n_cells = (int64_t)M;
+    return SJ_OK;
+}
+
+int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const int32_t* d_of_host) {
+    Index* ix = &g->ix;
+    cudaStream_t s = ix->stream;
+    const int K = g->n_inst;
+    const int dp = ix->dp;
+    const int64_t n = ix->n;
+    // ---- per-instance offsets, dims, source pointers ----
+    SJ_TRY(dev_alloc_t(&g->d_off, (size_t)K + 1, s));
+    SJ_CK(cudaMemcpyAsync(g->d_off, g->off.data(), (K + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+    double* X = nullptr;
+    SJ_TRY(dev_alloc_t(&X, (size_t)n * dp, s));
+    int32_t* inst_of = nullptr;
+    SJ_TRY(dev_alloc_t(&inst_of, (size_t)n, s));
+    {
+        const double** dsrc = nullptr;
+        int32_t* dd = nullptr;
+        SJ_TRY(dev_alloc_t(&dsrc, (size_t)K, s));
+        SJ_TRY(dev_alloc_t(&dd, (size_t)K, s));
+        SJ_CK(cudaMemcpyAsync(dsrc, src_dev_ptrs, K * sizeof(double*), cudaMemcpyHostToDevice, s));
+        SJ_CK(cudaMemcpyAsync(dd, d_of_host, K * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        k_bgather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, K, n, dp, X, inst_of);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        dev_free(dsrc, s);
+        dev_free(dd, s);
+    }
+    // ---- extents (one read-back) and per-instance grids ----
+    unsigned long long* ext = nullptr;
+    SJ_TRY(dev_alloc_t(&ext, (size_t)K * (2 * dp + 1), s));
+    const int eb = 256 - (256 % dp);
+    k_bextent<<<K, eb, (2 * dp + 1) * sizeof(unsigned long long), s>>>(X, g->d_off, dp, ext);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    std::vector<unsigned long long> hext((size_t)K * (2 * dp + 1));
+    SJ_CK(cudaMemcpyAsync(hext.data(), ext, hext.size() * 8, cudaMemcpyDeviceToHost, s));
+    SJ_CK(cudaStreamSynchronize(s));
+    dev_free(ext, s);
+    int inst_bits = 0;
+    while ((1ll << inst_bits) < K) ++inst_bits;
+    std::vector<BInst> hp((size_t)K);
+    std::vector<double> centre((size_t)K * dp, 0.0);
+    std::vector<double> e2((size_t)K);
+    int shift = 0;
+    const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32;
+    const double u_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
+    for (int k = 0; k < K; ++k) {
+        const unsigned long long* e = hext.data() + (size_t)k * (2 * dp + 1);
+        if (e[2 * dp] != 0) {
+            set_error("non-finite coordinate in batch instance %d", g->gids[k]);
+            return SJ_ERR_ARG;
+        }
+        Index t;
+        t.d = dp;
+        t.dp = dp;
+        t.eps = g->eps[k];
+        t.opt = ix->opt;
+        t.key_bits_cap = std::min(62, 64 - inst_bits);
+        t.lo.resize(dp);
+        t.hi.resize(dp);
+        for (int c = 0; c < dp; ++c) {
+            t.lo[c] = from_ord(e[c]);
+            t.hi[c] = from_ord(e[dp + c]);
+        }
+        SJ_TRY(choose_grid(&t));
+        BInst& b = hp[k];
+        memset(&b, 0, sizeof b);
+        b.m = t.m;
+        for (int i = 0; i < t.m; ++i) {
+            b.dims[i] = t.dims[i];
+            b.lo[i] = t.lo[t.dims[i]];
+            b.ncell[i] = t.ncell[i];
+            b.stride[i] = t.stride[i];
+        }
+        b.inv_w = 1.0 / t.w;
+        shift = std::max(shift, t.key_bits);
+        double pb = 0, rmax = 0;
+        for (int c = 0; c < dp; ++c) {
+            centre[(size_t)k * dp + c] = 0.5 * (t.lo[c] + t.hi[c]);
+            const double r = 0.5 * (t.hi[c] - t.lo[c]) * (1.0 + ldexp(1.0, -40));
+            pb += r * r;
+            rmax = std::max(rmax, r);
+        }
+        PackParams pp{};
+        pack_coefficients(t.eps, pb * (1.0 + ldexp(1.0, -20)), 1.01 * u_t * rmax, u_t, dp, dp, &pp);
+        b.a_out = pp.a_out;
+        b.b_out = pp.b_out;
+        b.a_in = pp.a_in;
+        b.b_in = pp.b_in;
+        b.has_in = pp.has_in;
+        e2[k] = t.eps * t.eps;
+    }
+    if (shift + inst_bits > 64) {
+        set_error("batched index keys need %d bits", shift + inst_bits);
+        return SJ_ERR_ARG;
+    }
+    BInst* dP = nullptr;
+    double* dcentre = nullptr;
+    SJ_TRY(dev_alloc_t(&dP, (size_t)K, s));
+    SJ_TRY(dev_alloc_t(&dcentre, (size_t)K * dp, s));
+    SJ_TRY(dev_alloc_t(&g->d_e2, (size_t)K, s));
+    SJ_CK(cudaMemcpyAsync(dP, hp.data(), K * sizeof(BInst), cudaMemcpyHostToDevice, s));
+    SJ_CK(cudaMemcpyAsync(dcentre, centre.data(), centre.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    SJ_CK(cudaMemcpyAsync(g->d_e2, e2.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
+    // ---- keys, sort, cells ----
+    unsigned long long* keys = nullptr;
+    SJ_TRY(dev_alloc_t(&keys, (size_t)n, s));
+    SJ_TRY(dev_alloc_t(&ix->perm, (size_t)n, s));
+    k_bkeys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, n, dp, inst_of, dP, shift, keys, ix->perm);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    SJ_TRY(radix_sort_pairs(reinterpret_cast<uint64_t*>(keys), ix->perm, n, shift + inst_bits, s));
+    SJ_TRY(build_cells(keys, n, &ix->cell_key, &ix->cell_start, &ix->n_cells, s));
+    dev_free(keys, s);
+    // ---- packing ----
+    SJ_TRY(dev_alloc_t(&ix->xs, (size_t)n * dp, s));
+    SJ_TRY(dev_alloc_t(&g->d_inst_of_sorted, (size_t)n, s));
+    if (use_f32) {
+        float *y, *h, *to, *ti;
+        SJ_TRY(dev_alloc_t(&y, (size_t)n * dp, s));
+        SJ_TRY(dev_alloc_t(&h, (size_t)n, s));
+        SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
+        SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
+        ix->y = y, ix->h = h, ix->thr_out = to, ix->thr_in = ti;
+        k_bpack<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, ix->perm, inst_of, dP, dcentre, n, dp, ix->xs,
+                                                                   y, h, to, ti, g->d_inst_of_sorted);
+    } else {
+        double *y, *h, *to, *ti;
+        SJ_TRY(dev_alloc_t(&y, (size_t)n * dp, s));
+        SJ_TRY(dev_alloc_t(&h, (size_t)n, s));
+        SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
+        SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
+        ix->y = y, ix->h = h, ix->thr_out = to, ix->thr_in = ti;
+        k_bpack<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, ix->perm, inst_of, dP, dcentre, n, dp,
+                                                                    ix->xs, y, h, to, ti, g->d_inst_of_sorted);
+    }
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    // perm now maps packed points to their place in the group; the join
+    // subtracts the instance's first position to get instance-local indices
+    // ---- runs and items (one read-back) ----
+    const int64_t M = ix->n_cells;
+    BEnum be{shift, ix->opt.symmetric ? 1 : 0, kQMax};
+    uint32_t* cnt = nullptr;
+    SJ_TRY(dev_alloc_t(&cnt, (size_t)M * 4, s));
+    uint32_t *run_cnt = cnt, *item_cnt = cnt + M, *run_off = cnt + 2 * M, *item_off = cnt + 3 * M;
+    unsigned long long* ev = nullptr;
+    SJ_TRY(dev_alloc_t(&ev, (size_t)2 * K, s));
+    SJ_CK(cudaMemsetAsync(ev, 0, 2 * K * sizeof(unsigned long long), s));
+    EnumTotals* dtot = nullptr;
+    SJ_TRY(dev_alloc_t(&dtot, 1, s));
+    SJ_CK(cudaMemsetAsync(dtot, 0, sizeof(EnumTotals), s));
+    k_benum_count<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(be, dP, ix->cell_key, ix->cell_start, M, run_cnt,
+                                                              item_cnt, ev, ev + K, dtot);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    SJ_TRY(scan_exclusive_u32(run_cnt, run_off, M, s));
+    SJ_TRY(scan_exclusive_u32(item_cnt, item_off, M, s));
+    EnumTotals tot{};
+    std::vector<unsigned long long> hev((size_t)2 * K);
+    SJ_CK(cudaMemcpyAsync(&tot, dtot, sizeof tot, cudaMemcpyDeviceToHost, s));
+    SJ_CK(cudaMemcpyAsync(hev.data(), ev, hev.size() * 8, cudaMemcpyDeviceToHost, s));
+    SJ_CK(cudaStreamSynchronize(s));
+    ix->n_runs = (int64_t)tot.n_runs;
+    ix->n_items = (int64_t)tot.n_items;
+    g->eval.assign(K, 0);
+    g->cand.assign(K, 0);
+    ix->n_evaluated = 0;
+    ix->n_candidates = 0;
+    for (int k = 0; k < K; ++k) {
+        g->eval[k] = (int64_t)hev[k];
+        g->cand[k] = ix->opt.symmetric ? (int64_t)(2 * hev[k] - hev[K + k]) : (int64_t)hev[k];
+        ix->n_evaluated += g->eval[k];
+        ix->n_candidates += g->cand[k];
+    }
+    if (tot.n_runs >= 0xFFFFFFFFull || tot.n_items >= 0x7FFFFFFFull) {
+        set_error("batched index too large");
+        return SJ_ERR_ARG;
+    }
+    SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(ix->n_runs, 1), s));
+    SJ_TRY(dev_alloc_t(&ix->items, (size_t)std::max<int64_t>(ix->n_items, 1), s));
+    SJ_TRY(dev_alloc_t(&g->d_item_inst, (size_t)std::max<int64_t>(ix->n_items, 1), s));
+    k_benum_fill<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(be, dP, ix->cell_key, ix->cell_start, M, run_off,
+                                                             item_off, ix->runs, ix->items, g->d_item_inst);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    dev_free(cnt, s);
+    dev_free(ev, s);
+    dev_free(dtot, s);
+    dev_free(dP, s);
+    dev_free(dcentre, s);
+    dev_free(X, s);
+    dev_free(inst_of, s);
+    SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
     return SJ_OK;
 }
 

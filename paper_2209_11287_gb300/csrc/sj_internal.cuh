@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -79,6 +80,7 @@ struct Index {
     int64_t ncell[kMaxM] = {};
     uint64_t stride[kMaxM] = {};
     int key_bits = 0;
+    int key_bits_cap = 62;      // cell keys use at most this many bits
     std::vector<double> lo, hi;
 
     // device arrays (cell order)
@@ -113,7 +115,48 @@ struct ResultImpl {
     double* dblock = nullptr;
     std::vector<int32_t*> pair_pages;
     std::vector<double*> dist_pages;
+    std::shared_ptr<void> shared_pool;  // batched results: the pool shared by all instances
 };
+
+// One group of a batched join: instances of the same padded dimension in
+// one index whose cell keys carry the instance number above the local key.
+struct BatchGroup {
+    Index ix;                       // the group's index (n = the group's points)
+    int n_inst = 0;
+    std::vector<int> gids;          // instance numbers in the batch
+    std::vector<long long> off;     // n_inst + 1 point offsets
+    std::vector<double> eps;
+    std::vector<int64_t> eval, cand;  // per instance: evaluations, canonical candidates
+    long long* d_off = nullptr;
+    int32_t* d_gid = nullptr;
+    double* d_e2 = nullptr;
+    int32_t* d_inst_of_sorted = nullptr;
+    int32_t* d_item_inst = nullptr;
+};
+// Routing of a batched join (sj_join_batch): items and sorted points belong
+// to instances; every pair goes, in instance-local indices, to its instance's
+// pages, which the device takes from a shared pool on first use.
+struct BatchJoin {
+    const int32_t* item_inst;       // per work item: group-local instance
+    const int32_t* inst_of_sorted;  // per packed point: group-local instance
+    const long long* inst_off;      // group-local instance -> its first point in the group
+    const int32_t* inst_gid;        // group-local instance -> instance number in the batch
+    const double* inst_e2;          // group-local instance -> eps^2
+    // output (indexed by instance number)
+    int2* pool;                     // n_pages pages of 2^page_log2 pairs
+    double* dpool;                  // matching distances, or null
+    int page_log2;
+    long long n_pages;
+    unsigned long long* pool_next;  // next free page
+    int32_t* page_table;            // per instance: its pages in order (-1 free, -2 being taken,
+                                    // -3 pool exhausted)
+    const long long* table_off;     // instance -> first slot of its page table
+    const int32_t* max_pages;       // instance -> slots of its page table
+    unsigned long long* cursor;     // instance -> pairs emitted (exact, even past the pool)
+    unsigned long long* error;      // set when a wait for a page claim expired
+};
+
+int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const int32_t* d_of_host);
 
 // ---- index build (sj_index.cu) ------------------------------------------------
 int build_index(Index* ix, const double* pts_dev);
@@ -125,6 +168,7 @@ struct JoinOut {
     uint64_t capacity = 0;         // pairs the pool can hold
     int2* band = nullptr;          // deferred-recheck queue
     unsigned long long band_cap = 0;
+    const void* batch = nullptr;   // device BatchJoin of a batched join, or null
 };
 int launch_join_cc(Index* ix, const JoinOut& out, int emit_dist);
 int launch_join_tc(Index* ix, const JoinOut& out, int emit_dist);

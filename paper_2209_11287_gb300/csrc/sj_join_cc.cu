@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     CcWarpSmem<T, DP, TC, EMIT>& W = smem[wid];
     ItemSmem<T, DP>& S = W.it;
-    WarpStage st{W.stage, EMIT ? W.sdist : nullptr, 0};
+    WarpStage st{W.stage, EMIT ? W.sdist : nullptr, 0, 0};
     unsigned long long rechecked = 0;
 
     long long next = 0;
@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
         const Item I = P.items[it];
         const int Q = I.q1 - I.q0;
         const int nr = I.r1 - I.r0;
+        const ItemRoute R = item_route(st, P, it, lane);
         const uint32_t C = load_item_warp<T, DP>(S, P, I, lane);
 
         for (uint32_t base = 0; base < C; base += (uint32_t)SLOTS) {
@@ -230,8 +231,8 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                     mir = W.cmir[slot] != 0;
                     if ((ent >> 15) && !EMIT) {  // certain in
                         nout = mir ? 2 : 1;
-                        qid = S.qid[q];
-                        cid = W.cperm[slot];
+                        qid = (int32_t)(S.qid[q] - R.off);
+                        cid = (int32_t)(W.cperm[slot] - R.off);
                     } else {
                         band = true;  // re-decided (and measured) in binary64
                     }
@@ -240,10 +241,10 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                 if (band && !queued) {  // queue full: decide here
                     const double s = direct_sq(P.xs + (int64_t)(I.q0 + q) * DP, P.xs + jj * DP, P.d);
                     ++rechecked;
-                    if (s <= P.e2) {
+                    if (s <= R.e2) {
                         nout = mir ? 2 : 1;
-                        qid = S.qid[q];
-                        cid = W.cperm[(W.list[e] >> 4) & 0x7FF];
+                        qid = (int32_t)(S.qid[q] - R.off);
+                        cid = (int32_t)(W.cperm[(W.list[e] >> 4) & 0x7FF] - R.off);
                         if (EMIT) dist = sqrt(s);
                     }
                 }
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(128) k_recheck(JoinParams P) {
     __shared__ int2 s_stage[4][kStage];
     __shared__ double s_sdist[4][EMIT ? kStage : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpStage st{s_stage[wid], EMIT ? s_sdist[wid] : nullptr, 0};
+    WarpStage st{s_stage[wid], EMIT ? s_sdist[wid] : nullptr, 0, 0};
     const unsigned long long queued = P.counters[3];
     const unsigned long long count = queued < P.band_cap ? queued : P.band_cap;
     const unsigned long long gw = (unsigned long long)blockIdx.x * 4 + wid;
@@ -285,13 +286,21 @@ __global__ void __launch_bounds__(128) k_recheck(JoinParams P) {
             const int32_t cs = (int32_t)((uint32_t)e.y & ~kMirrorBit);
             const bool mir = ((uint32_t)e.y & kMirrorBit) != 0;
             const double s = direct_sq(P.xs + (int64_t)qs * DP, P.xs + (int64_t)cs * DP, P.d);
-            if (s <= P.e2) {
+            if (P.batch) {  // lanes may serve different instances: one lane, one write
+                const int li = P.batch->inst_of_sorted[qs];
+                if (s <= P.batch->inst_e2[li]) {
+                    const long long off = P.batch->inst_off[li];
+                    batch_emit_one(P, P.batch->inst_gid[li], mir ? 2 : 1, (int32_t)(P.perm[qs] - off),
+                                   (int32_t)(P.perm[cs] - off), EMIT ? sqrt(s) : 0.0);
+                }
+            } else if (s <= P.e2) {
                 nout = mir ? 2 : 1;
                 qid = P.perm[qs];
                 cid = P.perm[cs];
                 if (EMIT) dist = sqrt(s);
             }
         }
+        if (P.batch) continue;
         if (EMIT)
             stage_emit(st, P, lane, nout, qid, cid, dist);
         else
@@ -388,6 +397,7 @@ JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist) {
     p.emit_dist = emit_dist;
     p.band = out.band;
     p.band_cap = out.band_cap;
+    p.batch = static_cast<const BatchJoin*>(out.batch);
     return p;
 }
 

@@ -34,6 +34,7 @@ struct JoinParams {
     // queued entries; past `band_cap` a pair is re-decided in place.
     int2* band;
     unsigned long long band_cap;
+    const BatchJoin* batch;  // null for a single join
 };
 
 JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist);
@@ -71,13 +72,88 @@ struct WarpStage {
     int2* pairs;   // kStage slots of this warp
     double* dist;  // kStage slots (used when distances are emitted)
     int cnt;       // warp-uniform fill
+    int gid;       // batched join: the instance the staged pairs belong to
 };
+
+// Batched join: the slot of pair position p of instance gid in the shared
+// pool, taking a fresh page for it on first use (a page-table slot is claimed
+// with a compare-and-swap; a thread that loses the race leaves its page
+// unused).  Returns null when the instance's table or the pool is exhausted
+// (the pair is then counted but not stored).
+// The pool page holding page `pg` of instance `gid`, taken from the pool on
+// first use; -1 when pg is past the instance's page table or the pool is
+// exhausted (the host sees both from the counters and reruns).  The first
+// caller locks the table slot (-2) and takes the next pool page (or marks the
+// slot exhausted, -3); later callers wait for it with a bounded spin whose
+// expiry raises B.error.
+__device__ __forceinline__ int32_t batch_page(const BatchJoin& B, int gid, unsigned long long pg) {
+    if (pg >= (unsigned long long)B.max_pages[gid]) return -1;
+    int32_t* slot = B.page_table + B.table_off[gid] + (long long)pg;
+    volatile int32_t* vslot = slot;
+    int32_t page = *vslot;
+    if (page == -1) {
+        const int32_t old = atomicCAS(slot, -1, -2);
+        if (old == -1) {
+            const unsigned long long fresh = atomicAdd(B.pool_next, 1ull);
+            page = fresh < (unsigned long long)B.n_pages ? (int32_t)fresh : -3;
+            atomicExch(slot, page);
+        } else {
+            page = old;
+        }
+    }
+    for (int it = 0; page == -2; ++it) {
+        if (it == (1 << 20)) {
+            atomicExch(B.error, 1ull);
+            return -1;
+        }
+        __nanosleep(64);
+        page = *vslot;
+    }
+    return page >= 0 ? page : -1;
+}
+
+static_assert(kStage / 64 + 1 <= 32, "a warp's flush must touch at most 32 pages");
+
+// Pool slot of position p of instance gid's result, or -1.
+__device__ __forceinline__ long long batch_slot(const BatchJoin& B, int gid, unsigned long long p) {
+    const int32_t page = batch_page(B, gid, p >> B.page_log2);
+    if (page < 0) return -1;
+    return ((long long)page << B.page_log2) | (long long)(p & ((1ull << B.page_log2) - 1ull));
+}
 
 // Reserves room for the warp's staged pairs with one atomic on the result
 // cursor and copies them to their pages (coalesced).  Positions past the
 // pool's capacity are counted but not written.
 __device__ __forceinline__ void stage_flush(WarpStage& st, const JoinParams& P, int lane) {
     __syncwarp();
+    if (P.batch) {
+        const BatchJoin& B = *P.batch;
+        unsigned long long base = 0;
+        if (lane == 0 && st.cnt > 0) base = atomicAdd(&B.cursor[st.gid], (unsigned long long)st.cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (st.cnt > 0) {
+            // pages of at least 64 pairs: a flush of <= kStage pairs touches
+            // at most kStage / 64 + 1 <= 32 pages, one lane resolves each
+            const unsigned long long pg0 = base >> B.page_log2;
+            const int npg = (int)(((base + (unsigned long long)st.cnt - 1ull) >> B.page_log2) - pg0) + 1;
+            const int32_t mine = lane < npg ? batch_page(B, st.gid, pg0 + (unsigned long long)lane) : -1;
+            const unsigned long long mask = (1ull << B.page_log2) - 1ull;
+            for (int i0 = 0; i0 < st.cnt; i0 += 32) {
+                const int i = i0 + lane;
+                const unsigned long long p = base + (unsigned long long)i;
+                const int src = i < st.cnt ? (int)((p >> B.page_log2) - pg0) : 0;
+                const int32_t page = __shfl_sync(0xffffffffu, mine, src);
+                if (i < st.cnt && page >= 0) {
+                    const long long s = ((long long)page << B.page_log2) | (long long)(p & mask);
+                    B.pool[s] = st.pairs[i];
+                    if (P.emit_dist) B.dpool[s] = st.dist[i];
+                }
+            }
+        }
+        __syncwarp();
+        st.cnt = 0;
+        return;
+    }
     unsigned long long base = 0;
     if (lane == 0 && st.cnt > 0) base = atomicAdd(&P.counters[1], (unsigned long long)st.cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
@@ -90,6 +166,42 @@ __device__ __forceinline__ void stage_flush(WarpStage& st, const JoinParams& P, 
     }
     __syncwarp();
     st.cnt = 0;
+}
+
+// Batched join, per work item: the instance of item `it` (its number in the
+// batch), its first point in the group and its eps^2.  The warp's stage is
+// flushed when the instance changes.
+struct ItemRoute {
+    int gid;
+    long long off;
+    double e2;
+};
+__device__ __forceinline__ ItemRoute item_route(WarpStage& st, const JoinParams& P, long long it, int lane) {
+    ItemRoute r{0, 0, P.e2};
+    if (P.batch) {
+        const int li = P.batch->item_inst[it];
+        r.gid = P.batch->inst_gid[li];
+        r.off = P.batch->inst_off[li];
+        r.e2 = P.batch->inst_e2[li];
+        if (st.cnt > 0 && st.gid != r.gid) stage_flush(st, P, lane);
+        st.gid = r.gid;
+    }
+    return r;
+}
+
+// Batched join: one pair (and its mirror when nout == 2) written by a single
+// lane (used by the recheck kernel, whose lanes may serve different instances).
+__device__ __forceinline__ void batch_emit_one(const JoinParams& P, int gid, int nout, int32_t qid, int32_t cid,
+                                               double dist) {
+    const BatchJoin& B = *P.batch;
+    const unsigned long long base = atomicAdd(&B.cursor[gid], (unsigned long long)nout);
+    for (int k = 0; k < nout; ++k) {
+        const long long s = batch_slot(B, gid, base + k);
+        if (s >= 0) {
+            B.pool[s] = k == 0 ? make_int2(qid, cid) : make_int2(cid, qid);
+            if (P.emit_dist) B.dpool[s] = dist;
+        }
+    }
 }
 
 // Warp-collective: each lane offers nout in {0, 1, 2} pairs ((qid, cid) and,

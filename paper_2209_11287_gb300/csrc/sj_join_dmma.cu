@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_join_dmma(JoinParams P) {
     const double* __restrict__ TI = static_cast<const double*>(P.thr_in);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int g = lane >> 2, tq = lane & 3;
-    WarpStage st{s_stage[wid], s_sdist[wid], 0};
+    WarpStage st{s_stage[wid], s_sdist[wid], 0, 0};
     unsigned long long rechecked = 0;
 
     for (;;) {

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(128, 1) k_join_tc(JoinParams P, TcParams T) {
     const float* __restrict__ TO = static_cast<const float*>(P.thr_out);
     const float* __restrict__ TI = static_cast<const float*>(P.thr_in);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    WarpStage st{S.stage[warp], EMIT ? S.sdist[warp] : nullptr, 0};
+    WarpStage st{S.stage[warp], EMIT ? S.sdist[warp] : nullptr, 0, 0};
     unsigned long long rechecked = 0;
 
     if (tid == 0) {
