@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0 = sized for ~15 s)")
     ap.add_argument("--hint", type=int, default=0, help="expected result pairs (0 = the library's automatic pool)")
+    ap.add_argument("--workload", default="uniform4d", choices=["uniform4d", "batched"],
+                    help="uniform4d: the 2M-point 4-D self-join (the headline); batched: 4096 independent joins")
+    ap.add_argument("--batch-count", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -395,6 +398,208 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- batched workload ------------------------------------------------------------------
+
+BATCH_METRIC = "batched self-joins: candidate pairs/s and join time, 4096 instances, n log-uniform [256, 65536], d in {2,4,8,16,32}"
+
+
+def batch_config(count, total_n, extra=None):
+    cfg = {"workload": f"batched: {count} independent self-joins, instance i drawn from PCG64(i): n = "
+                       f"floor(exp(U[ln 256, ln 65536])), d uniform over {{2,4,8,16,32}}, points uniform in "
+                       f"[0,1]^d, per-instance eps for a mean of 32 neighbours; {total_n} points in all",
+           "instances": count, "points": total_n}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def run_batched(args):
+    """One step = sj_join_batch over all instances (segmented index builds,
+    one distance-tile launch per dimension group, results in device pages)
+    until every instance's count is known; results are released after the
+    step."""
+    from paper_2209_11287_gb300 import workloads
+    rank, world, local = dist_env()
+    insts = [workloads.batch_instance(i) for i in range(args.batch_count)]
+    total_n = sum(w.n for w in insts)
+    eps = [w.eps for w in insts]
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        cores = oracle.threads(0)
+        rng = np.random.Generator(np.random.PCG64(77))
+        # per step: 64 queries of each of 32 sampled instances, scaled by n / sample per instance
+        cand_total = sum(oracle.grid_candidate_count_fast(w.points, w.eps * (1.0 + 2.0 ** -20)) for w in insts)
+        times = []
+        for k in range(args.warmup + args.steps):
+            pick = rng.choice(len(insts), size=32, replace=False)
+            est = 0.0
+            for i in pick:
+                w = insts[i]
+                q = np.sort(rng.choice(w.n, size=min(64, w.n), replace=False))
+                t0 = time.perf_counter()
+                oracle.rows(w.points, w.eps, q)
+                est += (time.perf_counter() - t0) * w.n / q.size
+            if k >= args.warmup:
+                times.append(est * len(insts) / len(pick))
+        sec = statistics.mean(times)
+        value = cand_total / sec
+        print(json.dumps({"metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "impl": "reference",
+                          "config": batch_config(len(insts), total_n, {"kernel": "oracle brute force (CPU)"}),
+                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                           "sample": "64 queries of each of 32 instances per step, scaled"},
+                          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+
+    import torch
+    from paper_2209_11287_gb300 import binding, build
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    binding.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    pts = [torch.from_numpy(w.points).to(dev) for w in insts]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def sync_all():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    dims = [w.d for w in insts]
+
+    def one_step(opt, inputs, host_out=None):
+        res = binding.sj_join_batch(inputs, eps, opt, stream)
+        cnt = cand = evald = reruns = maxc = 0
+        flops = 0.0
+        tile = 0.0
+        for k, r in enumerate(res):
+            if host_out is not None:
+                binding.sj_result_copy(r, host_out[: int(r.count)])
+            cnt += int(r.count)
+            cand += int(r.n_candidates)
+            evald += int(r.n_evaluated)
+            flops += 2.0 * dims[k] * int(r.n_evaluated)
+            maxc = max(maxc, int(r.count))
+            reruns = max(reruns, int(r.reruns))
+            tile = float(r.ms_tile)
+        for r in res:
+            binding.sj_result_free(r)
+        return cnt, cand, evald, reruns, tile, flops, maxc
+
+    variants = [v for v in args.variants.split(",") if v in ("filter_f32", "fp64_fma")] or ["filter_f32"]
+    sampler = ClockSampler(local)
+    results = {}
+    for vi, kname in enumerate(variants):
+        opt = binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint)
+        for _ in range(args.warmup):
+            one_step(opt, pts)
+        sync_all()
+        if vi == 0:
+            sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        l0 = binding.sj_kernel_launches()
+        tiles = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            info = one_step(opt, pts)
+            ev[k][1].record(stream)
+            tiles.append(info[4])
+        sync_all()
+        launches = (binding.sj_kernel_launches() - l0) // args.steps
+        clocks = sampler.stop() if vi == len(variants) - 1 else None
+        times = [a.elapsed_time(b) for a, b in ev]
+        results[kname] = {"ms_per_step": statistics.mean(times), "count": info[0], "n_candidates": info[1],
+                          "n_evaluated": info[2], "reruns": info[3], "tile_ms": statistics.mean(tiles),
+                          "flops": info[5], "max_count": info[6], "launches": launches, "clocks": clocks}
+    head = results[variants[0]]
+    # end to end: host inputs (pinned), every instance's pairs copied back to pinned host memory
+    host_pts = [torch.from_numpy(w.points).pin_memory() for w in insts]
+    host_out = torch.empty((head["max_count"] + 16, 2), dtype=torch.int32).pin_memory()
+    opt = binding.sj_default_options(kernel=variants[0], max_pairs_hint=args.hint)
+    t_e2e = []
+    for k in range(max(2, min(args.steps, 4))):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        one_step(opt, host_pts, host_out)
+        torch.cuda.synchronize(dev)
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(t_e2e)
+    if rank != 0:
+        return
+    var = {}
+    for k in variants:
+        r = results[k]
+        var[k] = {"ms_per_step": round(r["ms_per_step"], 3),
+                  "candidate_pairs_per_s": world * r["n_candidates"] / (r["ms_per_step"] * 1e-3),
+                  "instances_per_s": world * len(insts) / (r["ms_per_step"] * 1e-3),
+                  "result_pairs": r["count"], "evaluated_pairs": r["n_evaluated"], "reruns": r["reruns"],
+                  "tile_kernel_ms": round(r["tile_ms"], 3), "launches_per_step": r["launches"],
+                  "tile_roofline": batch_roofline(k, insts, r)}
+    line = {"metric": BATCH_METRIC, "value": world * head["n_candidates"] / (head["ms_per_step"] * 1e-3),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(head["ms_per_step"], 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if variants[0].startswith("filter") else "f64",
+            "data": "synthetic",
+            "config": batch_config(len(insts), total_n, {"kernel": variants[0], "symmetric": 1,
+                                                          "parallelism": f"replicas x{world}",
+                                                          "l2": "inputs (4.7 GB) larger than L2; 256 MB flush too",
+                                                          "candidate_pairs": head["n_candidates"],
+                                                          "result_pairs": head["count"]}),
+            "variants": var,
+            "e2e": {"value": world * head["n_candidates"] / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": sum(w.n * w.d * 8 for w in insts),
+                    "d2h_bytes_per_step": head["count"] * 8, "ms_per_step": round(e2e_s * 1e3, 1)},
+            "roofline": batch_roofline(variants[0], insts, head),
+            "gpu_launches": int(head["launches"]),
+            "clocks": results[variants[-1]]["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
+def batch_roofline(kname, insts, r):
+    """Roofline of the batch's distance-tile launches (one per dimension
+    group, their event times summed): 2 d flop per evaluated pair of each
+    instance against the FP32 (filter) or FP64 peak; bytes as for one join,
+    summed over instances."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    elt = 4 if kname.startswith("filter") else 8
+    nbytes = 8 * r["count"]
+    for w in insts:
+        dp = 2
+        while dp < w.d:
+            dp *= 2
+        nbytes += w.n * (elt * (dp + 3) + 4)
+    sec = r["tile_ms"] * 1e-3
+    tfl = r["flops"] / sec / 1e12
+    gbs = nbytes / sec / 1e9
+    fp_peak = FP64_DFMA_TFLOPS if kname == "fp64_fma" else FP32_FMA_PEAK_TFLOPS
+    if tfl / fp_peak >= gbs / hbm_peak:
+        return {"bound": "alu", "achieved": round(tfl, 3), "peak": round(fp_peak, 3), "unit": "TFLOP/s",
+                "frac": round(tfl / fp_peak, 4), "hbm_frac": round(gbs / hbm_peak, 4), "traffic": None,
+                "kernel": KERNEL_NAMES[kname], "kernel_ms": round(r["tile_ms"], 3)}
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(gbs / hbm_peak, 4), "alu_frac": round(tfl / fp_peak, 4), "traffic": None,
+            "kernel": KERNEL_NAMES[kname], "kernel_ms": round(r["tile_ms"], 3)}
+
+
 def canonical_candidates_host(w):
     """Candidate pairs of the full 3^d neighbourhoods on the grid of side
     eps (1 + 2^-20), counted with the oracle's grid helper."""
@@ -404,7 +609,9 @@ def canonical_candidates_host(w):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.workload == "batched":
+        run_batched(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_native(args)
