@@ -541,8 +541,19 @@ __device__ void visit_runs(const EnumParams& e, const unsigned long long* __rest
 }
 
 struct EnumTotals {
-    unsigned long long n_runs, n_items, n_evaluated, sum_sq;
+    unsigned long long n_runs, n_items, n_evaluated, sum_sq, tri_skip;
 };
+
+// Evaluations a symmetric join saves by starting each work item's self-cell
+// candidates at its own first query (the triangle of the self cell): item t
+// of a cell (queries [t qmax, t qmax + Q_t)) skips the t qmax self-cell
+// points before it.
+__device__ __forceinline__ unsigned long long tri_skip(int64_t q, int qmax) {
+    // sum over items t of t qmax Q_t: T full items, then one of r queries
+    const unsigned long long T = (unsigned long long)(q / qmax), r = (unsigned long long)(q % qmax);
+    const unsigned long long m = (unsigned long long)qmax;
+    return m * m * (T * (T - (T > 0 ? 1ull : 0ull)) / 2) + T * m * r;
+}
 
 __global__ void k_table(const unsigned long long* __restrict__ cell_key, int64_t n_cells, int32_t* table) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -558,7 +569,7 @@ __global__ void k_enum_count(EnumParams e, const unsigned long long* __restrict_
                              const int32_t* __restrict__ cell_start, int64_t n_cells, uint32_t* run_cnt,
                              uint32_t* item_cnt, EnumTotals* tot) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long my_sq = 0, my_eval = 0, my_runs = 0, my_items = 0;
+    unsigned long long my_sq = 0, my_eval = 0, my_runs = 0, my_items = 0, my_skip = 0;
     if (c < n_cells) {
         const int64_t q = cell_start[c + 1] - cell_start[c];
         uint32_t nr = 0;
@@ -574,9 +585,11 @@ __global__ void k_enum_count(EnumParams e, const unsigned long long* __restrict_
         my_eval = ev * (unsigned long long)q;
         my_runs = nr;
         my_items = ni;
+        if (e.symmetric) my_skip = tri_skip(q, e.qmax);
     }
     // warp reduction then one atomic per warp
     for (int o = 16; o > 0; o >>= 1) {
+        my_skip += __shfl_down_sync(0xffffffffu, my_skip, o);
         my_sq += __shfl_down_sync(0xffffffffu, my_sq, o);
         my_eval += __shfl_down_sync(0xffffffffu, my_eval, o);
         my_runs += __shfl_down_sync(0xffffffffu, my_runs, o);
@@ -584,6 +597,7 @@ __global__ void k_enum_count(EnumParams e, const unsigned long long* __restrict_
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&tot->sum_sq, my_sq);
+        atomicAdd(&tot->tri_skip, my_skip);
         atomicAdd(&tot->n_evaluated, my_eval);
         atomicAdd(&tot->n_runs, my_runs);
         atomicAdd(&tot->n_items, my_items);
@@ -707,41 +721,60 @@ __device__ __forceinline__ void split3(float y, __nv_bfloat16& t1, __nv_bfloat16
 // six split products with term indices summing to at most 4; slots 6 dp ..
 // 6 dp + 2 hold the split of -||y||^2 / 2 (query row) against ones
 // (candidate row); the rest is zero.
+//
+// Layout: K is cut into slices of 64 (the last one shorter); slice by slice,
+// the rows in 8-row groups, each group the K-major core matrices of the MMA
+// operand (8 rows x 16 bytes) in K order.  So one K-slice of a run of
+// consecutive groups is one contiguous block that a bulk copy moves into
+// shared memory in the layout the MMA reads.
+__device__ __forceinline__ int64_t split_at(int64_t p, int k, int kp, int64_t nrows) {
+    const int sl = k >> 6, kk = k & 63;
+    const int ks = kp - sl * 64 < 64 ? kp - sl * 64 : 64;
+    return (int64_t)sl * 64 * nrows + (((p >> 3) * (ks >> 3) + (kk >> 3)) * 8 + (p & 7)) * 8 + (kk & 7);
+}
+
 __global__ void k_pack_split(const float* __restrict__ y, const float* __restrict__ h, int64_t n, int dp, int kp,
-                             __nv_bfloat16* rows_a, __nv_bfloat16* rows_b) {
+                             int64_t nrows, __nv_bfloat16* rows_a, __nv_bfloat16* rows_b) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
-    __nv_bfloat16* a = rows_a + p * kp;
-    __nv_bfloat16* b = rows_b + p * kp;
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
     for (int k = 0; k < dp; ++k) {
         __nv_bfloat16 t1, t2, t3;
         split3(y[p * dp + k], t1, t2, t3);
-        a[6 * k + 0] = t1; a[6 * k + 1] = t2; a[6 * k + 2] = t1;
-        a[6 * k + 3] = t3; a[6 * k + 4] = t2; a[6 * k + 5] = t1;
-        b[6 * k + 0] = t1; b[6 * k + 1] = t1; b[6 * k + 2] = t2;
-        b[6 * k + 3] = t1; b[6 * k + 4] = t2; b[6 * k + 5] = t3;
+        const __nv_bfloat16 av[6] = {t1, t2, t1, t3, t2, t1};
+        const __nv_bfloat16 bv[6] = {t1, t1, t2, t1, t2, t3};
+        for (int u = 0; u < 6; ++u) {
+            rows_a[split_at(p, 6 * k + u, kp, nrows)] = av[u];
+            rows_b[split_at(p, 6 * k + u, kp, nrows)] = bv[u];
+        }
     }
     __nv_bfloat16 h1, h2, h3;
     split3(h[p], h1, h2, h3);
     const int o = 6 * dp;
-    a[o] = one; a[o + 1] = one; a[o + 2] = one;
-    b[o] = h1; b[o + 1] = h2; b[o + 2] = h3;
-    for (int k = o + 3; k < kp; ++k) a[k] = b[k] = zero;
+    rows_a[split_at(p, o, kp, nrows)] = one;
+    rows_a[split_at(p, o + 1, kp, nrows)] = one;
+    rows_a[split_at(p, o + 2, kp, nrows)] = one;
+    rows_b[split_at(p, o, kp, nrows)] = h1;
+    rows_b[split_at(p, o + 1, kp, nrows)] = h2;
+    rows_b[split_at(p, o + 2, kp, nrows)] = h3;
 }
 
 static int pack_split_rows(Index* ix) {
     cudaStream_t s = ix->stream;
     const int64_t n = ix->n;
     ix->kp = tc_kp(ix->dp);
+    const int64_t nrows = ((n + 7) & ~int64_t(7)) + kTcPadRows;
+    const size_t elems = (size_t)nrows * ix->kp;
     __nv_bfloat16 *ra = nullptr, *rb = nullptr;
-    SJ_TRY(dev_alloc_t(&ra, (size_t)n * ix->kp, s));
-    SJ_TRY(dev_alloc_t(&rb, (size_t)n * ix->kp, s));
+    SJ_TRY(dev_alloc_t(&ra, elems, s));
+    SJ_TRY(dev_alloc_t(&rb, elems, s));
     ix->rows_a = ra;
     ix->rows_b = rb;
+    SJ_CK(cudaMemsetAsync(ra, 0, elems * sizeof(__nv_bfloat16), s));
+    SJ_CK(cudaMemsetAsync(rb, 0, elems * sizeof(__nv_bfloat16), s));
     k_pack_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(static_cast<const float*>(ix->y),
                                                             static_cast<const float*>(ix->h), n, ix->dp, ix->kp,
-                                                            ra, rb);
+                                                            nrows, ra, rb);
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
@@ -880,7 +913,7 @@ int build_index(Index* ix, const double* pts) {
         ep.stride[i] = ix->stride[i];
     }
     ep.symmetric = ix->opt.symmetric ? 1 : 0;
-    const int qcap = ix->kernel == SJ_KERNEL_FILTER_BF16X3 ? kTcN : kQMax;
+    const int qcap = ix->kernel == SJ_KERNEL_FILTER_BF16X3 ? tc_qmax(tc_kp(ix->dp)) : kQMax;
     ep.qmax = ix->opt.queries_per_item > 0 ? std::min(ix->opt.queries_per_item, qcap) : qcap;
     const int64_t Mc = (int64_t)M;
     // dense key -> cell table when the key space is small (neighbour lookups
@@ -917,8 +950,9 @@ int build_index(Index* ix, const double* pts) {
     SJ_CK(cudaStreamSynchronize(s));
     ix->n_runs = (int64_t)tot.n_runs;
     ix->n_items = (int64_t)tot.n_items;
-    ix->n_evaluated = (int64_t)tot.n_evaluated;
     ix->n_candidates = ep.symmetric ? (int64_t)(2 * tot.n_evaluated - tot.sum_sq) : (int64_t)tot.n_evaluated;
+    // the CUDA-core kernels evaluate only the triangle of each self cell
+    ix->n_evaluated = (int64_t)(tot.n_evaluated - (uses_triangle(ix) ? tot.tri_skip : 0ull));
     if (tot.n_runs >= 0xFFFFFFFFull || tot.n_items >= 0x7FFFFFFFull) {
         set_error("index too large: %llu runs, %llu items", tot.n_runs, tot.n_items);
         dev_free(table, s);
@@ -1116,7 +1150,7 @@ __device__ __forceinline__ EnumParams benum_params(const BEnum& b, const BInst& 
 __global__ void k_benum_count(BEnum b, const BInst* __restrict__ P, const unsigned long long* __restrict__ cell_key,
                               const int32_t* __restrict__ cell_start, int64_t n_cells, uint32_t* run_cnt,
                               uint32_t* item_cnt, unsigned long long* inst_eval, unsigned long long* inst_sq,
-                              EnumTotals* tot) {
+                              unsigned long long* inst_skip, EnumTotals* tot) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     unsigned long long my_runs = 0, my_items = 0;
     if (c < n_cells) {
@@ -1139,6 +1173,7 @@ __global__ void k_benum_count(BEnum b, const BInst* __restrict__ P, const unsign
         item_cnt[c] = ni;
         atomicAdd(&inst_eval[k], ev * (unsigned long long)q);
         atomicAdd(&inst_sq[k], (unsigned long long)q * (unsigned long long)q);
+        if (b.symmetric) atomicAdd(&inst_skip[k], tri_skip(q, e.qmax));
         my_runs = nr;
         my_items = ni;
     }
@@ -1367,19 +1402,19 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     SJ_TRY(dev_alloc_t(&cnt, (size_t)M * 4, s));
     uint32_t *run_cnt = cnt, *item_cnt = cnt + M, *run_off = cnt + 2 * M, *item_off = cnt + 3 * M;
     unsigned long long* ev = nullptr;
-    SJ_TRY(dev_alloc_t(&ev, (size_t)2 * K, s));
-    SJ_CK(cudaMemsetAsync(ev, 0, 2 * K * sizeof(unsigned long long), s));
+    SJ_TRY(dev_alloc_t(&ev, (size_t)3 * K, s));
+    SJ_CK(cudaMemsetAsync(ev, 0, 3 * K * sizeof(unsigned long long), s));
     EnumTotals* dtot = nullptr;
     SJ_TRY(dev_alloc_t(&dtot, 1, s));
     SJ_CK(cudaMemsetAsync(dtot, 0, sizeof(EnumTotals), s));
     k_benum_count<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(be, dP, ix->cell_key, ix->cell_start, M, run_cnt,
-                                                              item_cnt, ev, ev + K, dtot);
+                                                              item_cnt, ev, ev + K, ev + 2 * K, dtot);
     note_launch();
     SJ_CK(cudaGetLastError());
     SJ_TRY(scan_exclusive_u32(run_cnt, run_off, M, s));
     SJ_TRY(scan_exclusive_u32(item_cnt, item_off, M, s));
     EnumTotals tot{};
-    std::vector<unsigned long long> hev((size_t)2 * K);
+    std::vector<unsigned long long> hev((size_t)3 * K);
     SJ_CK(cudaMemcpyAsync(&tot, dtot, sizeof tot, cudaMemcpyDeviceToHost, s));
     SJ_CK(cudaMemcpyAsync(hev.data(), ev, hev.size() * 8, cudaMemcpyDeviceToHost, s));
     SJ_CK(cudaStreamSynchronize(s));
@@ -1390,7 +1425,7 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     ix->n_evaluated = 0;
     ix->n_candidates = 0;
     for (int k = 0; k < K; ++k) {
-        g->eval[k] = (int64_t)hev[k];
+        g->eval[k] = (int64_t)(hev[k] - hev[2 * K + k]);  // (the kernels evaluate self-cell triangles)
         g->cand[k] = ix->opt.symmetric ? (int64_t)(2 * hev[k] - hev[K + k]) : (int64_t)hev[k];
         ix->n_evaluated += g->eval[k];
         ix->n_candidates += g->cand[k];

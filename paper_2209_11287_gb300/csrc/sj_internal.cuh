@@ -16,7 +16,6 @@ namespace sj {
 constexpr int kMaxM = 6;                         // indexed dims (3^(m-1) runs per cell)
 constexpr int kMaxRuns = 243 + 1;                // 3^(kMaxM-1) + the split self run
 constexpr int kQMax = 16;                        // queries per work item (bitmask width)
-constexpr int kTcN = 64;                         // queries per work item of the tensor-core filter
 constexpr int kThreads = 128;                    // CTA size of the distance kernels
 constexpr int kStage = 256;                      // per-warp staging slots for emitted pairs
 constexpr int64_t kDefaultPagePairs = int64_t(1) << 22;
@@ -158,6 +157,15 @@ struct BatchJoin {
 
 int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const int32_t* d_of_host);
 
+// Whether the join evaluates only the triangle of each self cell (symmetric
+// joins on the CUDA-core and tensor-core filter kernels): a work item's
+// self-cell candidates start at its own first query and pairs below the
+// diagonal are skipped.
+inline bool uses_triangle(const Index* ix) {
+    return ix->opt.symmetric && (ix->kernel == SJ_KERNEL_FILTER_F32 || ix->kernel == SJ_KERNEL_FP64_FMA ||
+                                 ix->kernel == SJ_KERNEL_FILTER_BF16X3);
+}
+
 // ---- index build (sj_index.cu) ------------------------------------------------
 int build_index(Index* ix, const double* pts_dev);
 
@@ -177,6 +185,14 @@ int launch_recheck(Index* ix, const JoinOut& out, int emit_dist);
 // Padded K of the tensor-core filter for padded dimension dp: 6 products per
 // dim plus 3 slots for the query term, rounded up to the MMA K of 16.
 constexpr int tc_kp(int dp) { return (6 * dp + 3 + 15) / 16 * 16; }
+// Queries per work item of the tensor-core filter: the MMA N (the query tile,
+// a whole number of 8-row groups from an 8-aligned start) is at most 256
+// (128 when K > 208, for shared memory), so an item holds one group less.
+constexpr int tc_nmax(int kp) { return kp <= 208 ? 256 : 128; }
+constexpr int tc_qmax(int kp) { return tc_nmax(kp) - 8; }
+// Zero rows after the last packed point in the split-row arrays, so 8-row
+// groups and query tiles past the end read zeros.
+constexpr int kTcPadRows = 256;
 // Number of counters of a join (item queue, result cursor, rechecked,
 // recheck-queue fill, error flag, spare).
 constexpr int kCounters = 8;

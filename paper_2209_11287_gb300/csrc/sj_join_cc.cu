@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
         for (uint32_t base = 0; base < C; base += (uint32_t)SLOTS) {
             int32_t j[TC];
             bool valid[TC];
+            uint32_t tri_mask[TC];
             T to[TC], ti[TC];
 #pragma unroll
             for (int t = 0; t < TC; ++t) {
@@ -142,16 +143,19 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                 const uint32_t v = base + (uint32_t)slot;
                 valid[t] = v < C;
                 j[t] = 0;
+                tri_mask[t] = 0xFFFFFFFFu;
                 to[t] = T(INFINITY);  // an empty slot is never maybe-in
                 ti[t] = T(INFINITY);
                 if (valid[t]) {
-                    bool mir;
-                    j[t] = map_candidate<T, DP>(S, nr, v, mir);
+                    uint8_t fl;
+                    j[t] = map_candidate_flag<T, DP>(S, nr, v, fl);
                     to[t] = TO[j[t]];
                     ti[t] = TI[j[t]];
                     W.cj[slot] = j[t];
                     W.cperm[slot] = P.perm[j[t]];
-                    W.cmir[slot] = mir ? 1 : 0;
+                    W.cmir[slot] = fl;
+                    // self-cell triangle: candidate j pairs with queries q0 .. j only
+                    tri_mask[t] = (fl == 2 && j[t] < I.q1) ? (2u << (j[t] - I.q0)) - 1u : 0xFFFFFFFFu;
                 }
             }
             uint32_t bits[TC], cbits[TC];
@@ -198,6 +202,11 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                     cbits[t] = cb;
                 }
             }
+#pragma unroll
+            for (int t = 0; t < TC; ++t) {
+                bits[t] &= tri_mask[t];
+                cbits[t] &= tri_mask[t];
+            }
             // compact the maybe-in pairs with one warp scan
             int cnt = 0;
 #pragma unroll
@@ -228,7 +237,8 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                     const int slot = (ent >> 4) & 0x7FF;
                     q = ent & 15;
                     jj = W.cj[slot];
-                    mir = W.cmir[slot] != 0;
+                    const int fl = W.cmir[slot];
+                    mir = fl == 1 || (fl == 2 && jj != (int64_t)(I.q0 + q));
                     if ((ent >> 15) && !EMIT) {  // certain in
                         nout = mir ? 2 : 1;
                         qid = (int32_t)(S.qid[q] - R.off);
@@ -395,6 +405,7 @@ JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist) {
     p.d = ix->d;
     p.dp = ix->dp;
     p.emit_dist = emit_dist;
+    p.tri = uses_triangle(ix) ? 1 : 0;
     p.band = out.band;
     p.band_cap = out.band_cap;
     p.batch = static_cast<const BatchJoin*>(out.batch);

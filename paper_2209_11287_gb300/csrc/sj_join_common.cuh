@@ -27,6 +27,7 @@ struct JoinParams {
     int d;
     int dp;            // padded dimension (row stride of xs)
     int emit_dist;
+    int tri;           // symmetric join: evaluate only the triangle of each self cell
     // deferred re-decisions: pairs whose certified bound straddles eps (and,
     // when distances are emitted, every maybe-in pair) are queued here and
     // re-decided by k_recheck with whole warps.  Entry: (query sorted
@@ -326,6 +327,9 @@ __device__ __forceinline__ uint32_t load_item(ItemSmem<T, DP>& S, const JoinPara
 // Warp-level variant of load_item: the calling warp alone fills S (its own
 // copy) and the result is visible to the warp after the returned __syncwarp.
 template <typename T, int DP>
+// With P.tri the self-cell run (the one run without the mirror flag in a
+// symmetric join) starts at the item's first query and is flagged 2: its
+// pairs above the diagonal are emitted in both orders, those below skipped.
 __device__ __forceinline__ uint32_t load_item_warp(ItemSmem<T, DP>& S, const JoinParams& P, const Item& I,
                                                    int lane) {
     const T* __restrict__ Y = static_cast<const T*>(P.y);
@@ -343,9 +347,11 @@ __device__ __forceinline__ uint32_t load_item_warp(ItemSmem<T, DP>& S, const Joi
         uint32_t len = 0;
         if (r < nr) {
             const Run R = P.runs[I.r0 + r];
-            S.rstart[r] = R.start;
-            S.rmir[r] = (uint8_t)(R.end_flags >> 31);
-            len = (uint32_t)((int32_t)(R.end_flags & ~kMirrorBit) - R.start);
+            const bool self = P.tri && !(R.end_flags & kMirrorBit);
+            const int32_t start = self ? I.q0 : R.start;
+            S.rstart[r] = start;
+            S.rmir[r] = self ? (uint8_t)2 : (uint8_t)(R.end_flags >> 31);
+            len = (uint32_t)((int32_t)(R.end_flags & ~kMirrorBit) - start);
         }
         uint32_t v = len;
 #pragma unroll
@@ -388,6 +394,21 @@ __device__ __forceinline__ int32_t map_candidate(const ItemSmem<T, DP>& S, int n
             hi = mid - 1;
     }
     mirror = S.rmir[lo] != 0;
+    return S.rstart[lo] + (int32_t)(v - S.rpre[lo]);
+}
+
+// As map_candidate, with the run's flag (0 plain, 1 mirror, 2 self-cell triangle).
+template <typename T, int DP>
+__device__ __forceinline__ int32_t map_candidate_flag(const ItemSmem<T, DP>& S, int nr, uint32_t v, uint8_t& flag) {
+    int lo = 0, hi = nr - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.rpre[mid] <= v)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    flag = S.rmir[lo];
     return S.rstart[lo] + (int32_t)(v - S.rpre[lo]);
 }
 

@@ -23,6 +23,22 @@ __global__ void ffma_k(float* out, float a, float b) {
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3+x4+x5+x6+x7;
 }
+// DFMA with every operand in a register (no constant-bank operand) and 16
+// independent chains.
+__global__ void dfma_reg_k(double* out, double a0, double b0) {
+  const double a = a0 + 1e-17 * threadIdx.x, b = b0 * (1.0 + 1e-17 * threadIdx.x);
+  double x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = threadIdx.x + k;
+  for (int i = 0; i < ITERS / 2; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
 __global__ void dmma884_k(double* out, double av) {
   double a = av + threadIdx.x, b = av - threadIdx.x;
   double c[4][2] = {};
@@ -98,6 +114,9 @@ int main() {
     float ms = timeit([&] { dfma_k<<<blocks, thr>>>(dbuf, 1.0000001, 1e-9); });
     double flops = 2.0 * 8 * ITERS * (double)blocks * thr;
     printf("DFMA  bpsm=%d: %.3f ms  %.3f TFLOP/s  %.2f DFMA/clk/SM(@max)\n", bpsm, ms, flops / ms / 1e9,
+           flops / 2 / (ms * 1e-3) / sms / (clk * 1e3));
+    ms = timeit([&] { dfma_reg_k<<<blocks, thr>>>(dbuf, 1.0000001, 1e-9); });
+    printf("DFMA(reg) bpsm=%d: %.3f ms  %.3f TFLOP/s  %.2f DFMA/clk/SM(@max)\n", bpsm, ms, flops / ms / 1e9,
            flops / 2 / (ms * 1e-3) / sms / (clk * 1e3));
     ms = timeit([&] { ffma_k<<<blocks, thr>>>(fbuf, 1.0000001f, 1e-9f); });
     flops = 2.0 * 8 * ITERS * (double)blocks * thr;

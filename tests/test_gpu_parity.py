@@ -62,6 +62,24 @@ def test_uniform2d_full(kernel, symmetric):
     assert st["count"] == ref.size
 
 
+@pytest.mark.parametrize("kernel", ["fp64_fma", "filter_f32"])
+def test_evaluated_count_triangle(kernel):
+    """Symmetric joins on the CUDA-core kernels evaluate the half
+    neighbourhood with only the triangle of each self cell: item t of a cell
+    (16 queries each) starts its self-cell candidates at its own first query,
+    so the evaluations are (candidates + sum |c|^2) / 2 minus, per cell of q
+    points, the sum over items of 16 t Q_t."""
+    w = workloads.uniform2d()
+    _, _, st = gpu_join(w.points, w.eps, kernel)
+    cells = oracle.grid_cells(w.points, w.eps * (1.0 + 2.0 ** -20))
+    _, cnt = np.unique(cells, axis=0, return_counts=True)
+    skip = 0
+    for q in cnt.tolist():
+        skip += sum(16 * t * min(16, q - 16 * t) for t in range((q + 15) // 16))
+    full = (st["n_candidates"] + int((cnt.astype(np.int64) ** 2).sum())) // 2
+    assert st["n_evaluated"] == full - skip
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_distances_bit_identical(kernel):
     w = workloads.uniform2d(n=6000, seed=3)
