@@ -37,9 +37,12 @@ HEADLINE = "filter_f32"
 VARIANTS = ["filter_f32", "fp64_fma", "fp64_dmma"]
 L2_FLUSH_BYTES = 256 << 20
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
-FP64_DFMA_TFLOPS = 1.009                                  # measured, profiles/fp64_peaks_gb300.txt
-FP64_DMMA_TFLOPS = 1.050                                  # measured, profiles/fp64_peaks_gb300.txt
-KERNEL_NAMES = {"filter_f32": "k_join_cc<float>", "fp64_fma": "k_join_cc<double>", "fp64_dmma": "k_join_dmma"}
+FP64_DFMA_TFLOPS = 1.255                                  # measured, profiles/fp64_peaks_gb300.txt
+FP64_DMMA_TFLOPS = 1.102                                  # measured, profiles/fp64_peaks_gb300.txt
+KERNEL_NAMES = {"filter_f32": "k_join_cc<float>", "fp64_fma": "k_join_cc<double>", "fp64_dmma": "k_join_dmma",
+                "filter_bf16x3": "k_join_tc"}
+DTYPES = {"auto": "bf16x3|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64", "fp64_fma": "f64",
+          "fp64_dmma": "f64"}
 
 
 def parse():
@@ -478,27 +481,37 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
 
     dims = [w.d for w in insts]
+    knames = {v: k for k, v in binding.KERNELS.items()}
 
     def one_step(opt, inputs, host_out=None):
         res = binding.sj_join_batch(inputs, eps, opt, stream)
         cnt = cand = evald = reruns = maxc = 0
-        flops = 0.0
-        tile = 0.0
+        groups = {}  # padded dim -> tile time, kernel, evaluated pairs and 2 d per pair
         for k, r in enumerate(res):
             if host_out is not None:
                 binding.sj_result_copy(r, host_out[: int(r.count)])
             cnt += int(r.count)
             cand += int(r.n_candidates)
             evald += int(r.n_evaluated)
-            flops += 2.0 * dims[k] * int(r.n_evaluated)
             maxc = max(maxc, int(r.count))
             reruns = max(reruns, int(r.reruns))
-            tile = float(r.ms_tile)
+            dp = 2
+            while dp < dims[k]:
+                dp *= 2
+            g = groups.setdefault(dp, {"ms": float(r.ms_tile), "kernel": knames.get(int(r.kernel), "?"),
+                                       "evaluated": 0, "flops_2d": 0.0, "instances": 0, "points": 0})
+            g["evaluated"] += int(r.n_evaluated)
+            g["flops_2d"] += 2.0 * dims[k] * int(r.n_evaluated)
+            g["instances"] += 1
+            g["points"] += len(inputs[k])
         for r in res:
             binding.sj_result_free(r)
-        return cnt, cand, evald, reruns, tile, flops, maxc
+        tile = sum(g["ms"] for g in groups.values())
+        return cnt, cand, evald, reruns, tile, groups, maxc
 
-    variants = [v for v in args.variants.split(",") if v in ("filter_f32", "fp64_fma")] or ["filter_f32"]
+    allowed = ("auto", "filter_f32", "filter_bf16x3", "fp64_fma")
+    asked = args.variants.split(",") if args.variants != ",".join(VARIANTS) else ["auto", "filter_f32", "fp64_fma"]
+    variants = [v for v in asked if v in allowed] or ["auto"]
     sampler = ClockSampler(local)
     results = {}
     for vi, kname in enumerate(variants):
@@ -523,7 +536,7 @@ def run_batched(args):
         times = [a.elapsed_time(b) for a, b in ev]
         results[kname] = {"ms_per_step": statistics.mean(times), "count": info[0], "n_candidates": info[1],
                           "n_evaluated": info[2], "reruns": info[3], "tile_ms": statistics.mean(tiles),
-                          "flops": info[5], "max_count": info[6], "launches": launches, "clocks": clocks}
+                          "groups": info[5], "max_count": info[6], "launches": launches, "clocks": clocks}
     head = results[variants[0]]
     # end to end: host inputs (pinned), every instance's pairs copied back to pinned host memory
     host_pts = [torch.from_numpy(w.points).pin_memory() for w in insts]
@@ -548,11 +561,11 @@ def run_batched(args):
                   "instances_per_s": world * len(insts) / (r["ms_per_step"] * 1e-3),
                   "result_pairs": r["count"], "evaluated_pairs": r["n_evaluated"], "reruns": r["reruns"],
                   "tile_kernel_ms": round(r["tile_ms"], 3), "launches_per_step": r["launches"],
-                  "tile_roofline": batch_roofline(k, insts, r)}
+                  "groups": batch_rooflines(r)}
     line = {"metric": BATCH_METRIC, "value": world * head["n_candidates"] / (head["ms_per_step"] * 1e-3),
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(head["ms_per_step"], 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if variants[0].startswith("filter") else "f64",
+            "vs_baseline": None, "dtype": DTYPES.get(variants[0], "f64"),
             "data": "synthetic",
             "config": batch_config(len(insts), total_n, {"kernel": variants[0], "symmetric": 1,
                                                           "parallelism": f"replicas x{world}",
@@ -563,41 +576,42 @@ def run_batched(args):
             "e2e": {"value": world * head["n_candidates"] / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": sum(w.n * w.d * 8 for w in insts),
                     "d2h_bytes_per_step": head["count"] * 8, "ms_per_step": round(e2e_s * 1e3, 1)},
-            "roofline": batch_roofline(variants[0], insts, head),
+            "roofline": max(batch_rooflines(head).values(), key=lambda g: g["kernel_ms"]),
             "gpu_launches": int(head["launches"]),
             "clocks": results[variants[-1]]["clocks"]}
     print(json.dumps(line), flush=True)
 
 
-def batch_roofline(kname, insts, r):
-    """Roofline of the batch's distance-tile launches (one per dimension
-    group, their event times summed): 2 d flop per evaluated pair of each
-    instance against the FP32 (filter) or FP64 peak; bytes as for one join,
-    summed over instances."""
+def batch_rooflines(r):
+    """Roofline of each dimension group's distance-tile launch (event-timed by
+    the library): the tensor-core filter against the measured sustained bf16
+    peak with 2 K flop per evaluated pair (K the padded split-row length,
+    6 products per dim plus the norm slots); the FP32 filter and the FP64
+    kernel with 2 d flop per evaluated pair against the FP32 peak and the
+    measured DFMA peak."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    elt = 4 if kname.startswith("filter") else 8
-    nbytes = 8 * r["count"]
-    for w in insts:
-        dp = 2
-        while dp < w.d:
-            dp *= 2
-        nbytes += w.n * (elt * (dp + 3) + 4)
-    sec = r["tile_ms"] * 1e-3
-    tfl = r["flops"] / sec / 1e12
-    gbs = nbytes / sec / 1e9
-    fp_peak = FP64_DFMA_TFLOPS if kname == "fp64_fma" else FP32_FMA_PEAK_TFLOPS
-    if tfl / fp_peak >= gbs / hbm_peak:
-        return {"bound": "alu", "achieved": round(tfl, 3), "peak": round(fp_peak, 3), "unit": "TFLOP/s",
-                "frac": round(tfl / fp_peak, 4), "hbm_frac": round(gbs / hbm_peak, 4), "traffic": None,
-                "kernel": KERNEL_NAMES[kname], "kernel_ms": round(r["tile_ms"], 3)}
-    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(gbs / hbm_peak, 4), "alu_frac": round(tfl / fp_peak, 4), "traffic": None,
-            "kernel": KERNEL_NAMES[kname], "kernel_ms": round(r["tile_ms"], 3)}
+    bf16 = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    out = {}
+    for dp, g in sorted(r["groups"].items()):
+        sec = max(g["ms"], 1e-6) * 1e-3
+        if g["kernel"] == "filter_bf16x3":
+            kp = (6 * dp + 3 + 15) // 16 * 16
+            flops, peak, kern = 2.0 * kp * g["evaluated"], bf16, "k_join_tc<bf16x3>"
+            bound = "tensor"
+        else:
+            flops = g["flops_2d"]
+            peak = FP64_DFMA_TFLOPS if g["kernel"] == "fp64_fma" else FP32_FMA_PEAK_TFLOPS
+            kern, bound = KERNEL_NAMES.get(g["kernel"], g["kernel"]), "alu"
+        tfl = flops / sec / 1e12
+        out[f"d{dp}"] = {"bound": bound, "achieved": round(tfl, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                         "frac": round(tfl / peak, 4), "traffic": None, "kernel": kern,
+                         "kernel_ms": round(g["ms"], 3), "instances": g["instances"],
+                         "evaluated_pairs": g["evaluated"]}
+    return out
 
 
 def canonical_candidates_host(w):

@@ -187,15 +187,17 @@ SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj
  * group's index is built by segmented kernels over composite cell keys
  * (instance << S | cell key of the instance's own grid, Sec. III-A) and all
  * of the group's work items run in one persistent distance-tile launch
- * (kernels SJ_KERNEL_FILTER_F32, the AUTO choice, or SJ_KERNEL_FP64_FMA;
- * others give SJ_ERR_UNSUPPORTED).  Pairs carry instance-local indices and
+ * (kernels SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_BF16X3 (padded d <= 64) or
+ * SJ_KERNEL_FP64_FMA; AUTO takes the tensor-core filter for groups of padded
+ * dimension 16 .. 64 and the FP32 filter for the others; SJ_KERNEL_FP64_DMMA
+ * gives SJ_ERR_UNSUPPORTED).  Pairs carry instance-local indices and
  * satisfy the same decision rule as sj_self_join.  The device takes each
  * instance's result pages from one shared pool (opt->page_pairs rounded up
  * to a power of two of at least 64, default 65536 pairs a page); when the
  * pool runs out the joins are rerun with pools sized from the exact counts
  * (reruns in every result).  per_instance_out[k] gets instance k's result (n_candidates and
- * n_evaluated per instance, n_rechecked 0, ms_tile the summed tile-kernel
- * time of all groups); release each with sj_result_free (the pool is freed
+ * n_evaluated per instance, n_rechecked 0, ms_tile the tile-kernel time of
+ * the instance's group, kernel the group's kernel); release each with sj_result_free (the pool is freed
  * with the last of them).  Errors: SJ_ERR_ARG (a bad instance, named in
  * sj_last_error_message), SJ_ERR_OOM, SJ_ERR_CUDA, SJ_ERR_UNSUPPORTED,
  * SJ_ERR_RESULT_OVERFLOW; on error no result needs freeing.

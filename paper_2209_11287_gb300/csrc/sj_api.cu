@@ -489,11 +489,25 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
     sj_options o;
     sj_default_options(&o);
     if (opt) o = *opt;
-    int kernel = o.kernel == SJ_KERNEL_AUTO ? SJ_KERNEL_FILTER_F32 : o.kernel;
-    if (kernel != SJ_KERNEL_FILTER_F32 && kernel != SJ_KERNEL_FP64_FMA) {
-        set_error("batched joins run the FP32 filter or the FP64 CUDA-core kernel (got kernel %d)", kernel);
+    if (o.kernel != SJ_KERNEL_AUTO && o.kernel != SJ_KERNEL_FILTER_F32 && o.kernel != SJ_KERNEL_FP64_FMA &&
+        o.kernel != SJ_KERNEL_FILTER_BF16X3) {
+        set_error("batched joins run the FP32 filter, the tensor-core filter or the FP64 CUDA-core kernel (got "
+                  "kernel %d)", o.kernel);
         return SJ_ERR_UNSUPPORTED;
     }
+    // AUTO: the tensor-core filter for padded dimensions 16 .. 64 (the batched
+    // instances there are near brute force, where its tiles pay), else the
+    // FP32 CUDA-core filter
+    auto group_kernel = [&](int dp) {
+        if (o.kernel != SJ_KERNEL_AUTO) return o.kernel;
+        return (dp >= 16 && dp <= 64) ? SJ_KERNEL_FILTER_BF16X3 : SJ_KERNEL_FILTER_F32;
+    };
+    for (int32_t k = 0; k < count; ++k)
+        if (group_kernel(round_dim(d[k])) == SJ_KERNEL_FILTER_BF16X3 && round_dim(d[k]) > 64) {
+            set_error("the tensor-core filter supports d <= 64 (instance %d has d = %d)", (int)k, (int)d[k]);
+            return SJ_ERR_UNSUPPORTED;
+        }
+    std::vector<int> inst_kernel(count), inst_group(count);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0;
     SJ_CK(cudaGetDevice(&dev));
@@ -527,7 +541,7 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
             g->ix.device = dev;
             g->ix.stream = s;
             g->ix.opt = o;
-            g->ix.kernel = kernel;
+            g->ix.kernel = group_kernel(dp);
             g->ix.d = dp;
             g->ix.dp = dp;
             g->off.push_back(0);
@@ -553,6 +567,8 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
                 src.push_back(p);
                 dof.push_back(d[k]);
                 g->gids.push_back(k);
+                inst_kernel[k] = group_kernel(dp);
+                inst_group[k] = (int)groups.size();
                 g->eps.push_back(eps[k]);
                 g->off.push_back(g->off.back() + n[k]);
             }
@@ -631,7 +647,7 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
     }
     std::vector<unsigned long long> cur(count + 2, 0);
     int reruns = 0;
-    double tile_ms = 0.0;
+    std::vector<double> group_ms;
     for (int attempt = 0; attempt < 3 && st == SJ_OK; ++attempt) {
         pool = std::make_shared<PoolHolder>();
         pool->stream = s;
@@ -645,7 +661,6 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
             st = SJ_ERR_CUDA;
             break;
         }
-        tile_ms = 0.0;
         for (size_t gi = 0; gi < groups.size() && st == SJ_OK; ++gi) {
             BatchGroup& g = *groups[gi];
             BatchJoin bj{};
@@ -687,7 +702,9 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
             }
             if (e == cudaSuccess) e = cudaEventRecord(ix->ev_tile[0], s);
             if (e != cudaSuccess) st = SJ_ERR_CUDA;
-            if (st == SJ_OK) st = launch_join_cc(ix, jo, dist ? 1 : 0);
+            if (st == SJ_OK)
+                st = ix->kernel == SJ_KERNEL_FILTER_BF16X3 ? launch_join_tc(ix, jo, dist ? 1 : 0)
+                                                           : launch_join_cc(ix, jo, dist ? 1 : 0);
             if (st == SJ_OK && cudaEventRecord(ix->ev_tile[1], s) != cudaSuccess) st = SJ_ERR_CUDA;
             if (st == SJ_OK) st = launch_recheck(ix, jo, dist ? 1 : 0);
             dev_free(band, s);
@@ -700,10 +717,24 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
             st = SJ_ERR_CUDA;
             break;
         }
-        for (auto& g : groups) {
+        bool timed_out = false;
+        group_ms.assign(groups.size(), 0.0);
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            auto& g = groups[gi];
             float ms = 0.f;
             if (g->ix.n_items > 0 && cudaEventElapsedTime(&ms, g->ix.ev_tile[0], g->ix.ev_tile[1]) == cudaSuccess)
-                tile_ms += ms;
+                group_ms[gi] = ms;
+            if (g->ix.kernel == SJ_KERNEL_FILTER_BF16X3 && g->ix.n_items > 0) {
+                unsigned long long flag = 0;  // the tensor-core kernel's bounded-wait flag
+                if (cudaMemcpy(&flag, g->ix.counters + 4, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                    flag != 0)
+                    timed_out = true;
+            }
+        }
+        if (timed_out) {
+            set_error("a bounded wait of the tensor-core filter expired");
+            st = SJ_ERR_TIMEOUT;
+            break;
         }
         if (cur[count + 1] != 0) {
             set_error("a wait for a result page claim expired");
@@ -778,8 +809,8 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
         r.n_evaluated = eval[k];
         r.n_rechecked = 0;
         r.reruns = reruns;
-        r.kernel = kernel;
-        r.ms_tile = tile_ms;
+        r.kernel = inst_kernel[k];
+        r.ms_tile = group_ms.empty() ? 0.0 : group_ms[inst_group[k]];
         r.internal = ri;
     }
     free_meta();

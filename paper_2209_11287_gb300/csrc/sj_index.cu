@@ -1299,8 +1299,11 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     std::vector<double> centre((size_t)K * dp, 0.0);
     std::vector<double> e2((size_t)K);
     int shift = 0;
-    const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32;
+    const bool tensor = ix->kernel == SJ_KERNEL_FILTER_BF16X3;
+    const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32 || tensor;
     const double u_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
+    // the tensor-core filter's widened bound (as for a single join)
+    const double c1 = tensor ? 2.0 * gamma_n(ldexp(1.0, -24), dp) + (4.1 * tc_kp(dp) + 2.0) * ldexp(1.0, -22) : -1.0;
     for (int k = 0; k < K; ++k) {
         const unsigned long long* e = hext.data() + (size_t)k * (2 * dp + 1);
         if (e[2 * dp] != 0) {
@@ -1339,7 +1342,7 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
             rmax = std::max(rmax, r);
         }
         PackParams pp{};
-        pack_coefficients(t.eps, pb * (1.0 + ldexp(1.0, -20)), 1.01 * u_t * rmax, u_t, dp, dp, &pp);
+        pack_coefficients(t.eps, pb * (1.0 + ldexp(1.0, -20)), 1.01 * u_t * rmax, u_t, dp, dp, &pp, c1);
         b.a_out = pp.a_out;
         b.b_out = pp.b_out;
         b.a_in = pp.a_in;
@@ -1393,11 +1396,12 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     }
     note_launch();
     SJ_CK(cudaGetLastError());
+    if (tensor) SJ_TRY(pack_split_rows(ix));
     // perm now maps packed points to their place in the group; the join
     // subtracts the instance's first position to get instance-local indices
     // ---- runs and items (one read-back) ----
     const int64_t M = ix->n_cells;
-    BEnum be{shift, ix->opt.symmetric ? 1 : 0, kQMax};
+    BEnum be{shift, ix->opt.symmetric ? 1 : 0, tensor ? tc_qmax(tc_kp(dp)) : kQMax};
     uint32_t* cnt = nullptr;
     SJ_TRY(dev_alloc_t(&cnt, (size_t)M * 4, s));
     uint32_t *run_cnt = cnt, *item_cnt = cnt + M, *run_off = cnt + 2 * M, *item_off = cnt + 3 * M;

@@ -77,7 +77,7 @@ def _check(pts, eps, out, with_dist):
             assert np.array_equal(dists[order], rd), f"instance {k}: distances differ"
 
 
-@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "auto"])
+@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3", "auto"])
 @pytest.mark.parametrize("symmetric", [1, 0])
 def test_mixed_batch(kernel, symmetric):
     pts, eps = _mixed_batch()
@@ -85,18 +85,19 @@ def test_mixed_batch(kernel, symmetric):
     _check(pts, eps, out, with_dist=False)
 
 
-@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma"])
+@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3"])
 def test_mixed_batch_distances_host_input(kernel):
     pts, eps = _mixed_batch(seed=1)
     out = binding.join_batch(pts, eps, kernel=kernel, emit_distances=True)
     _check(pts, eps, out, with_dist=True)
 
 
-def test_pool_regrow():
+@pytest.mark.parametrize("kernel", ["filter_f32", "auto"])
+def test_pool_regrow(kernel):
     """A pool far too small (64-pair pages, a 1-pair hint) is regrown from the
     exact counts and the joins rerun; the result is unchanged."""
     pts, eps = _mixed_batch(seed=2)
-    out = binding.join_batch(pts, eps, kernel="filter_f32", page_pairs=64, max_pairs_hint=1,
+    out = binding.join_batch(pts, eps, kernel=kernel, page_pairs=64, max_pairs_hint=1,
                              emit_distances=True)
     assert max(st["reruns"] for _, _, st in out) >= 1
     _check(pts, eps, out, with_dist=True)
@@ -116,6 +117,8 @@ def test_candidate_counts_per_instance():
 def test_unsupported_kernel_rejected():
     with pytest.raises(RuntimeError):
         binding.join_batch([np.random.default_rng(0).random((10, 4))], [0.1], kernel="fp64_dmma")
+    with pytest.raises(RuntimeError):  # the tensor-core filter stops at d = 64
+        binding.join_batch([np.random.default_rng(0).random((10, 65))], [0.1], kernel="filter_bf16x3")
 
 
 def test_bad_instance_rejected():
