@@ -51,13 +51,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--n", type=int, default=2_000_000)
+    ap.add_argument("--n", type=int, default=0, help="points (0 = the workload's full size)")
     ap.add_argument("--variants", default=",".join(VARIANTS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0 = sized for ~15 s)")
     ap.add_argument("--hint", type=int, default=0, help="expected result pairs (0 = the library's automatic pool)")
-    ap.add_argument("--workload", default="uniform4d", choices=["uniform4d", "batched"],
-                    help="uniform4d: the 2M-point 4-D self-join (the headline); batched: 4096 independent joins")
+    ap.add_argument("--workload", default="uniform4d", choices=["uniform4d", "mixture16d", "expo64d", "batched"],
+                    help="uniform4d: the 2M-point 4-D self-join (the headline); mixture16d: 1M x 16 Gaussian "
+                         "mixture; expo64d: 500k x 64 clipped exponential; batched: 4096 independent joins")
     ap.add_argument("--batch-count", type=int, default=4096)
     return ap.parse_args()
 
@@ -69,13 +70,38 @@ def dist_env():
     return rank, world, local
 
 
+WORKLOAD_TEXT = {
+    "uniform4d": "points i.i.d. uniform in [0,1]^4, eps from the 4-ball volume for a mean of 64 neighbours",
+    "mixture16d": "32 isotropic Gaussians in 16-D (centres uniform in [0,1]^16, sigma 0.04, equal weights), "
+                  "eps calibrated on the oracle for a mean of 100 neighbours",
+    "expo64d": "64-D coordinates i.i.d. exponential(40) clipped to [0,1], eps calibrated on the oracle for a "
+               "mean of 50 neighbours",
+}
+METRICS = {
+    "uniform4d": METRIC,
+    "mixture16d": "self-join candidate pairs/s and join time, n=1M d=16 Gaussian mixture: FP64 plain vs low-prec filter",
+    "expo64d": "self-join candidate pairs/s and join time, n=500k d=64 clipped exponential: FP64 plain vs "
+               "low-prec filter",
+}
+DEFAULT_VARIANTS = {
+    "uniform4d": ["filter_f32", "fp64_fma", "fp64_dmma"],
+    "mixture16d": ["filter_bf16x3", "filter_f32", "fp64_fma"],
+    "expo64d": ["filter_bf16x3", "filter_f32"],
+}
+
+
 def workload_config(w, extra=None):
-    cfg = {"workload": f"uniform4d: n={w.n} points i.i.d. uniform in [0,1]^4 (seed {w.seed}), "
-                       f"eps={w.eps:.7g} (4-ball volume for a mean of 64 neighbours)",
+    cfg = {"workload": f"{w.name}: n={w.n} {WORKLOAD_TEXT.get(w.name, '')} (seed {w.seed}), eps={w.eps:.7g}",
            "n": w.n, "d": w.d, "eps": w.eps}
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def make_workload(args):
+    from paper_2209_11287_gb300 import workloads
+    make = workloads.CONFIGS[args.workload]
+    return make(n=args.n) if args.n > 0 else make()
 
 
 # ---- clocks sampled during the timed region -----------------------------------------
@@ -149,7 +175,7 @@ def run_native(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    w = workloads.uniform4d(n=args.n)
+    w = make_workload(args)
     pts = torch.from_numpy(w.points).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -182,6 +208,8 @@ def run_native(args):
     results = {}
     sampler = ClockSampler(local)
     variants = [v for v in args.variants.split(",") if v]
+    if args.variants == ",".join(VARIANTS):
+        variants = DEFAULT_VARIANTS[args.workload]
     for vi, kname in enumerate(variants):
         opt = binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint)
         for _ in range(args.warmup):
@@ -247,18 +275,19 @@ def kernel_source_sha(kname):
     tile header), to tie committed counters to the code they were taken on."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2209_11287_gb300", "csrc")
-    files = ["sj_join_dmma.cu" if kname == "fp64_dmma" else "sj_join_cc.cu", "sj_join_common.cuh"]
+    main = {"fp64_dmma": "sj_join_dmma.cu", "filter_bf16x3": "sj_join_tc.cu"}.get(kname, "sj_join_cc.cu")
+    files = [main, "sj_join_common.cuh"]
     h = hashlib.sha256()
     for f in files:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def read_traffic(kname):
+def read_traffic(kname, workload="uniform4d"):
     """DRAM bytes per launch of the distance kernel from the committed ncu
     summary (a line 'dram_bytes_per_launch: <int>' and 'kernel_source_sha:
     <sha>'), or None when absent or taken on different kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"join_{kname}_uniform4d.txt")
+    path = os.path.join(ROOT, "profiles", f"join_{kname}_{workload}.txt")
     if not os.path.exists(path):
         return None
     sha = kernel_source_sha(kname)
@@ -278,12 +307,14 @@ def read_traffic(kname):
 def roofline(kname, w, r, kern_ms):
     """Roofline of one distance-tile kernel launch.  Arithmetic: d fused
     multiply-adds (2d flop) per evaluated (query, candidate) pair, in FP32 for
-    the filter (peak from the SM count, FP32 lanes and maximum clock) and in
-    FP64 for the plain kernels (peaks of the committed micro-benchmark,
-    profiles/fp64_peaks_gb300.txt).  Bytes: every packed point read once
-    (coordinates, norm, two thresholds, input index) plus 8 bytes per emitted
-    pair, against the measured HBM copy bandwidth.  The larger fraction is the
-    binding one."""
+    the CUDA-core filter (peak from the SM count, FP32 lanes and maximum
+    clock) and in FP64 for the plain kernels (peaks of the committed
+    micro-benchmark, profiles/fp64_peaks_gb300.txt); for the tensor-core
+    filter 2 K flop per evaluated pair (K the padded split-row length, 6
+    products per dim plus the norm slots) against the measured burst bf16
+    peak.  Bytes: every packed point read once (coordinates, norm, two
+    thresholds, input index) plus 8 bytes per emitted pair, against the
+    measured HBM copy bandwidth.  The larger fraction is the binding one."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -294,16 +325,22 @@ def roofline(kname, w, r, kern_ms):
     dp = 2
     while dp < w.d:
         dp *= 2
-    flops = 2.0 * w.d * r["n_evaluated"]
+    if kname == "filter_bf16x3":
+        kp = (6 * dp + 3 + 15) // 16 * 16
+        flops = 2.0 * kp * r["n_evaluated"]
+        fp_peak, unit_bound = float(peaks.get("bf16_tflops", 1900.0)), "tensor"
+    else:
+        flops = 2.0 * w.d * r["n_evaluated"]
+        fp_peak = {"fp64_fma": FP64_DFMA_TFLOPS, "fp64_dmma": FP64_DMMA_TFLOPS}.get(kname, FP32_FMA_PEAK_TFLOPS)
+        unit_bound = "alu"
     tfl = flops / (kern_ms * 1e-3) / 1e12
     bytes_alg = w.n * (elt * (dp + 3) + 4) + 8 * r["count"]
     gbs = bytes_alg / (kern_ms * 1e-3) / 1e9
-    fp_peak = {"fp64_fma": FP64_DFMA_TFLOPS, "fp64_dmma": FP64_DMMA_TFLOPS}.get(kname, FP32_FMA_PEAK_TFLOPS)
     frac_alu, frac_hbm = tfl / fp_peak, gbs / hbm_peak
-    common = {"traffic": read_traffic(kname), "kernel": KERNEL_NAMES.get(kname, kname),
+    common = {"traffic": read_traffic(kname, w.name), "kernel": KERNEL_NAMES.get(kname, kname),
               "kernel_ms": round(kern_ms, 4), "flop_per_launch": flops, "bytes_per_launch": bytes_alg}
     if frac_alu >= frac_hbm:
-        return {"bound": "alu", "achieved": round(tfl, 3), "peak": round(fp_peak, 3), "unit": "TFLOP/s",
+        return {"bound": unit_bound, "achieved": round(tfl, 3), "peak": round(fp_peak, 3), "unit": "TFLOP/s",
                 "frac": round(frac_alu, 4), "hbm_frac": round(frac_hbm, 4), **common}
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(frac_hbm, 4), "alu_frac": round(frac_alu, 4), **common}
@@ -326,9 +363,10 @@ def make_line(args, w, results, variants, world, kern_ms, e2e_s, head):
                   "tile_roofline": {key: rk[key] for key in ("bound", "achieved", "peak", "unit", "frac")}}
     e2e_val = world * cand / e2e_s
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup,
         "ms_per_step": round(head["ms_per_step"], 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if kname.startswith("filter") else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPES.get(kname, "f64"), "data": "synthetic",
         "config": workload_config(w, {"kernel": kname, "symmetric": 1, "parallelism": f"replicas x{world}",
                                       "l2": "flushed between steps (256 MB write)",
                                       "candidate_pairs": cand, "result_pairs": head["count"]}),
@@ -372,10 +410,14 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    if args.workload != "uniform4d":
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm is defined for the uniform4d "
+                          "headline workload only (its canonical 3^d grid candidate count)"}), flush=True)
+        return
     from paper_2209_11287_gb300 import workloads
     import oracle
     oracle.build()
-    w = workloads.uniform4d(n=args.n)
+    w = make_workload(args)
     cand = canonical_candidates_host(w)
     cores = oracle.threads(0)
     rng = np.random.Generator(np.random.PCG64(99))
@@ -391,7 +433,7 @@ def run_reference(args):
             times.append(dt)
     s = statistics.mean(times)
     value = cand / s
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": workload_config(w, {"kernel": "oracle brute force (CPU)"}),
@@ -429,35 +471,9 @@ def run_batched(args):
     if args.impl == "reference":
         if rank != 0:
             return
-        import oracle
-        oracle.build()
-        cores = oracle.threads(0)
-        rng = np.random.Generator(np.random.PCG64(77))
-        # per step: 64 queries of each of 32 sampled instances, scaled by n / sample per instance
-        cand_total = sum(oracle.grid_candidate_count_fast(w.points, w.eps * (1.0 + 2.0 ** -20)) for w in insts)
-        times = []
-        for k in range(args.warmup + args.steps):
-            pick = rng.choice(len(insts), size=32, replace=False)
-            est = 0.0
-            for i in pick:
-                w = insts[i]
-                q = np.sort(rng.choice(w.n, size=min(64, w.n), replace=False))
-                t0 = time.perf_counter()
-                oracle.rows(w.points, w.eps, q)
-                est += (time.perf_counter() - t0) * w.n / q.size
-            if k >= args.warmup:
-                times.append(est * len(insts) / len(pick))
-        sec = statistics.mean(times)
-        value = cand_total / sec
-        print(json.dumps({"metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
-                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "impl": "reference",
-                          "config": batch_config(len(insts), total_n, {"kernel": "oracle brute force (CPU)"}),
-                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                           "sample": "64 queries of each of 32 instances per step, scaled"},
-                          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                                  "d2h_bytes_per_step": 0}}), flush=True)
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm is defined for the uniform4d "
+                          "headline workload only (its canonical grid candidate count); batched runs report the "
+                          "oracle in cpu_baseline of the native line"}), flush=True)
         return
 
     import torch
@@ -577,9 +593,41 @@ def run_batched(args):
                     "h2d_bytes_per_step": sum(w.n * w.d * 8 for w in insts),
                     "d2h_bytes_per_step": head["count"] * 8, "ms_per_step": round(e2e_s * 1e3, 1)},
             "roofline": max(batch_rooflines(head).values(), key=lambda g: g["kernel_ms"]),
+            "cpu_baseline": None if args.no_cpu_baseline else batch_cpu_baseline(insts, head["n_candidates"]),
             "gpu_launches": int(head["launches"]),
             "clocks": results[variants[-1]]["clocks"]}
     print(json.dumps(line), flush=True)
+
+
+def batch_cpu_baseline(insts, n_candidates):
+    """The oracle (brute force, every sampled query against all points of its
+    instance) on the host cores for sampled queries of sampled instances,
+    scaled by n / sample per instance and by instances / sampled instances."""
+    import oracle
+    oracle.build()
+    cores = oracle.threads(0)
+    rng = np.random.Generator(np.random.PCG64(77))
+    pick = rng.choice(len(insts), size=64, replace=False)
+
+    def run(q_per_inst):
+        est, t_all = 0.0, 0.0
+        for i in pick:
+            w = insts[i]
+            q = np.sort(rng.choice(w.n, size=min(q_per_inst, w.n), replace=False))
+            t0 = time.perf_counter()
+            oracle.rows(w.points, w.eps, q)
+            dt = time.perf_counter() - t0
+            t_all += dt
+            est += dt * w.n / q.size
+        return est * len(insts) / len(pick), t_all
+
+    _, probe = run(16)
+    qpi = int(max(16, min(4096, 16 * 10.0 / max(probe, 1e-3))))  # ~10 s of oracle work
+    full_s, spent = run(qpi)
+    return {"value": n_candidates / full_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{qpi} queries of each of 64 sampled instances (seeded), each against all points of its "
+                      f"instance, scaled by n / sample and 4096 / 64",
+            "sample_seconds": round(spent, 2), "full_batch_seconds_est": round(full_s, 1)}
 
 
 def batch_rooflines(r):

@@ -1,13 +1,15 @@
 """Writes the stored eps of the calibrated workloads (test infrastructure).
 
-For the 16-D Gaussian mixture (mean selectivity 100) and the 64-D clipped
-exponential set (mean selectivity 50) no closed form gives eps, so it is
-calibrated with the oracle: squared distances from 2000 seeded sample queries
-to all points (oracle order), eps^2 = the (target x 2000)-th smallest of the
-pooled values.  The result goes to paper_2209_11287_gb300/workload_eps.json,
-which the workload generators read.
+For the 16-D Gaussian mixture (mean selectivity 100), the 64-D clipped
+exponential set (mean selectivity 50) and the batched instances of dimension
+8 and more (mean 32 neighbours each; in a unit cube the d-ball formula is far
+off there) no closed form gives eps, so it is calibrated with the oracle:
+squared distances from seeded sample queries (2000, or 500 per batched
+instance) to all points (oracle order, the query itself excluded), eps^2 =
+the (target x queries)-th smallest of the pooled values.  The result goes to
+paper_2209_11287_gb300/workload_eps.json, which the workload generators read.
 
-Run: python oracle/calibrate_eps.py
+Run: python oracle/calibrate_eps.py [--batched-only]
 """
 import json
 import os
@@ -46,6 +48,19 @@ def main():
     out = {}
     if os.path.exists(workloads.EPS_TABLE):
         out = json.load(open(workloads.EPS_TABLE))
+    batched = {}
+    for i in range(4096):
+        n, d, _ = workloads.batch_instance_params(i)
+        if d >= 8:
+            w = workloads.batch_instance(i, eps=1.0)
+            batched[str(i)] = calibrate(w.points, 32.0, n_queries=500, seed=1000 + i)
+    out["batched"] = batched
+    print("batched", len(batched), "instances calibrated", flush=True)
+    if "--batched-only" in sys.argv:
+        with open(workloads.EPS_TABLE, "w") as f:
+            json.dump(out, f, indent=1, sort_keys=True)
+            f.write("\n")
+        return
     m = workloads.mixture16d(eps=1.0)
     out["mixture16d"] = calibrate(m.points, 100.0)
     print("mixture16d", out["mixture16d"], flush=True)

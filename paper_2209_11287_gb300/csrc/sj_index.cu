@@ -733,30 +733,45 @@ __device__ __forceinline__ int64_t split_at(int64_t p, int k, int kp, int64_t nr
     return (int64_t)sl * 64 * nrows + (((p >> 3) * (ks >> 3) + (kk >> 3)) * 8 + (p & 7)) * 8 + (kk & 7);
 }
 
+// One thread per 16-byte chunk (8 K slots of one row): consecutive threads
+// write consecutive rows of a chunk, so a warp stores whole 128-byte lines.
 __global__ void k_pack_split(const float* __restrict__ y, const float* __restrict__ h, int64_t n, int dp, int kp,
                              int64_t nrows, __nv_bfloat16* rows_a, __nv_bfloat16* rows_b) {
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
-    for (int k = 0; k < dp; ++k) {
-        __nv_bfloat16 t1, t2, t3;
-        split3(y[p * dp + k], t1, t2, t3);
-        const __nv_bfloat16 av[6] = {t1, t2, t1, t3, t2, t1};
-        const __nv_bfloat16 bv[6] = {t1, t1, t2, t1, t2, t3};
-        for (int u = 0; u < 6; ++u) {
-            rows_a[split_at(p, 6 * k + u, kp, nrows)] = av[u];
-            rows_b[split_at(p, 6 * k + u, kp, nrows)] = bv[u];
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int ch = kp >> 3;
+    const int64_t grp = t / (8 * ch);
+    const int c = (int)((t >> 3) % ch);
+    const int64_t p = grp * 8 + (t & 7);
+    if (p >= n) return;  // padding rows stay zero
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+    __align__(16) __nv_bfloat16 av[8], bv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int k = c * 8 + u;
+        __nv_bfloat16 a = zero, b = zero;
+        if (k < 6 * dp) {
+            __nv_bfloat16 t1, t2, t3;
+            split3(y[p * dp + k / 6], t1, t2, t3);
+            switch (k % 6) {  // candidate (c1, c2, c1, c3, c2, c1), query (q1, q1, q2, q1, q2, q3)
+                case 0: a = t1; b = t1; break;
+                case 1: a = t2; b = t1; break;
+                case 2: a = t1; b = t2; break;
+                case 3: a = t3; b = t1; break;
+                case 4: a = t2; b = t2; break;
+                default: a = t1; b = t3; break;
+            }
+        } else if (k < 6 * dp + 3) {
+            __nv_bfloat16 h1, h2, h3;
+            split3(h[p], h1, h2, h3);
+            a = one;
+            b = k == 6 * dp ? h1 : (k == 6 * dp + 1 ? h2 : h3);
         }
+        av[u] = a;
+        bv[u] = b;
     }
-    __nv_bfloat16 h1, h2, h3;
-    split3(h[p], h1, h2, h3);
-    const int o = 6 * dp;
-    rows_a[split_at(p, o, kp, nrows)] = one;
-    rows_a[split_at(p, o + 1, kp, nrows)] = one;
-    rows_a[split_at(p, o + 2, kp, nrows)] = one;
-    rows_b[split_at(p, o, kp, nrows)] = h1;
-    rows_b[split_at(p, o + 1, kp, nrows)] = h2;
-    rows_b[split_at(p, o + 2, kp, nrows)] = h3;
+    const int64_t o = split_at(p, c * 8, kp, nrows);
+    *reinterpret_cast<uint4*>(rows_a + o) = *reinterpret_cast<const uint4*>(av);
+    *reinterpret_cast<uint4*>(rows_b + o) = *reinterpret_cast<const uint4*>(bv);
 }
 
 static int pack_split_rows(Index* ix) {
@@ -772,7 +787,8 @@ static int pack_split_rows(Index* ix) {
     ix->rows_b = rb;
     SJ_CK(cudaMemsetAsync(ra, 0, elems * sizeof(__nv_bfloat16), s));
     SJ_CK(cudaMemsetAsync(rb, 0, elems * sizeof(__nv_bfloat16), s));
-    k_pack_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(static_cast<const float*>(ix->y),
+    const int64_t threads = ((n + 7) / 8) * 8 * (ix->kp / 8);
+    k_pack_split<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(static_cast<const float*>(ix->y),
                                                             static_cast<const float*>(ix->h), n, ix->dp, ix->kp,
                                                             nrows, ra, rb);
     note_launch();

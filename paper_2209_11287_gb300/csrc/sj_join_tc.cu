@@ -22,10 +22,12 @@
 //   warp 1      MMA issuer (one thread): K/16 MMAs per tile into one of two
 //               TMEM accumulators (128 lanes x N columns), committed to the
 //               stage and accumulator barriers;
-//   warps 2-5   epilogue: each thread owns one candidate row (its TMEM lane)
-//               and compares its N accumulators with the candidate's two
-//               thresholds (a max over 64 columns first; hits are rare), then
-//               runs the warp-aggregated emission of the CUDA-core kernels.
+//   warps 2-9   epilogue: each thread owns one candidate row (its TMEM lane)
+//               and half of its N accumulators (two warps per lane quarter,
+//               alternate 32-column chunks), compares them with the
+//               candidate's two thresholds (a max over 32 columns first; hits
+//               are rare), then runs the warp-aggregated emission of the
+//               CUDA-core kernels.
 // A symmetric join evaluates only the triangle of each self cell: the self
 // run starts at the item's first query and pairs below the diagonal are
 // masked.  Every wait is bounded; on expiry the CTA stops issuing work,
@@ -41,7 +43,8 @@ constexpr int kTcM = 128;             // candidate rows per tile (TMEM lanes)
 constexpr int kTcG = kTcM / 8;        // 8-row groups per tile
 constexpr int kKS = 64;               // K per pipeline slice
 constexpr int kMetaDepth = 4;         // tiles of row metadata in flight
-constexpr int kTcThreads = 192;       // producer, MMA, 4 epilogue warps
+constexpr int kTcEpi = 8;             // epilogue warps: two per TMEM lane quarter, splitting the columns
+constexpr int kTcThreads = 64 + 32 * kTcEpi;  // producer, MMA, epilogue warps
 constexpr long long kTcSpin = 1 << 22;  // bound on barrier polls per wait
 
 struct TcParams {
@@ -79,7 +82,7 @@ struct TcMeta {
 
 template <int KP, bool EMIT>
 struct TcSmem {
-    static constexpr int STAGES = KP > 208 ? 4 : 5;
+    static constexpr int STAGES = (KP > 208 || EMIT) ? 4 : 5;
     uint64_t a_full[STAGES], a_empty[STAGES];
     uint64_t b_full, b_empty;
     uint64_t item_full[2], item_empty[2];
@@ -89,13 +92,14 @@ struct TcSmem {
     uint32_t tmem;
     int abort;
     TcItem items[2];
+    int32_t qperm[2][256];  // input index of each query-tile row of the items in the ring
     TcMeta meta[kMetaDepth];
     int32_t rgp[kMaxRuns];  // producer: per run of the item, its first group's number in the item
     int32_t rlo[kMaxRuns], rhi[kMaxRuns];
     uint8_t rfl[kMaxRuns];
-    int2 stage[4][kStage];
-    double sdist[4][EMIT ? kStage : 1];
-    uint16_t hits[4][64][32];  // per epilogue warp: maybe-in entries of a 64-column chunk, per lane
+    int2 stage[kTcEpi][kStage];
+    double sdist[kTcEpi][EMIT ? kStage : 1];
+    uint16_t hits[kTcEpi][32][32];  // per epilogue warp: maybe-in entries of a 32-column chunk, per lane
 };
 
 template <int KP, bool EMIT>
@@ -199,13 +203,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
         bar_init(&S.b_empty, 1);
         for (int i = 0; i < 2; ++i) {
             bar_init(&S.item_full[i], 1);
-            bar_init(&S.item_empty[i], 5);  // the MMA thread and the 4 epilogue warps
+            bar_init(&S.item_empty[i], 1 + kTcEpi);  // the MMA thread and the epilogue warps
             bar_init(&S.acc_full[i], 1);
-            bar_init(&S.acc_empty[i], 4);
+            bar_init(&S.acc_empty[i], kTcEpi);
         }
         for (int i = 0; i < kMetaDepth; ++i) {
             bar_init(&S.meta_full[i], 1);
-            bar_init(&S.meta_empty[i], 4);
+            bar_init(&S.meta_empty[i], kTcEpi);
         }
         bar_init(&S.drain, 1);
         S.abort = 0;
@@ -269,8 +273,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
             const int ntiles = (ngroups + kTcG - 1) / kTcG;
             const int qa = I.q0 & ~7;
             const int ncol = ((I.q1 - qa) + 15) & ~15;
+            // the ring slot is free once its previous item is done; then its query ids
+            int freed = 1;
+            if (lane == 0) freed = bar_wait(&S.item_empty[it_i], it_ph ^ 1u, abort) ? 1 : 0;
+            freed = __shfl_sync(0xffffffffu, freed, 0);
+            if (freed && it < P.n_items)
+                for (int c = lane; c < ncol; c += 32) {
+                    const int q = qa + c;
+                    S.qperm[it_i][c] = (q >= I.q0 && q < I.q1) ? P.perm[q] : 0;
+                }
+            __syncwarp();
             if (lane == 0) {
-                if (!bar_wait(&S.item_empty[it_i], it_ph ^ 1u, abort)) {
+                if (!freed) {
                     bail = 1;
                 } else if (it >= P.n_items) {
                     S.items[it_i].it = -1;
@@ -285,7 +299,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
                     X.ncol = ncol;
                     X.ntiles = ntiles;
                     bar_arrive(&S.item_full[it_i]);
-                    if (++it_i == 2) it_i = 0, it_ph ^= 1u;
                     // the query tile, one copy per K-slice
                     if (!bar_wait(&S.b_empty, b_ph ^ 1u, abort)) {
                         bail = 1;
@@ -304,6 +317,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
                 }
             }
             bail = __shfl_sync(0xffffffffu, bail, 0);
+            if (freed && it < P.n_items && ++it_i == 2) it_i = 0, it_ph ^= 1u;  // (the whole warp)
             // candidate tiles
             for (int t = 0; t < ntiles && !bail; ++t) {
                 int w = 1;
@@ -435,6 +449,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
         // ------------------------------------------------------------ epilogue
         const int ew = warp - 2;       // stage slot
         const int quarter = warp & 3;  // TMEM lanes 32 quarter .. + 31
+        const int half = ew >> 2;      // 32-column chunks half, half + 2, ...
         const int row = quarter * 32 + lane;
         const float* __restrict__ TO = static_cast<const float*>(P.thr_out);
         const float* __restrict__ TI = static_cast<const float*>(P.thr_in);
@@ -449,10 +464,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
             bool fail = false;
             // this thread's candidate row, read one tile ahead so its
             // threshold loads overlap the previous tile
-            int32_t p = 0;
+            int32_t p = 0, pid = 0;
             bool valid = false;
             int fl = 0;
             float to = INFINITY, ti = INFINITY;
+            const int32_t* qperm = S.qperm[it_i];
             auto read_meta = [&]() -> bool {
                 if (!bar_wait(&S.meta_full[m_i], m_ph, abort)) return false;
                 const TcMeta& M = S.meta[m_i];
@@ -466,12 +482,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
                 if (++m_i == kMetaDepth) m_i = 0, m_ph ^= 1u;
                 to = valid ? TO[p] : INFINITY;
                 ti = valid ? TI[p] : INFINITY;
+                pid = valid ? P.perm[p] : 0;
                 return true;
             };
             if (X.ntiles > 0 && !read_meta()) fail = true;
             const int cq0 = X.q0 - X.qa, cq1 = X.q1 - X.qa;  // the item's query columns
             for (int t = 0; t < X.ntiles && !fail; ++t) {
-                const int32_t cp = p;
+                const int32_t cp = p, cpid = pid;
                 const bool cvalid = valid;
                 const int cfl = fl;
                 const float cto = to, cti = ti;
@@ -484,30 +501,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
                     fail = true;
                     break;
                 }
-                // this lane's maybe-in columns of a 64-column chunk (column | certain << 8),
+                // this lane's maybe-in columns of a 32-column chunk (column | certain << 8),
                 // emitted afterwards a warp-wide round at a time
                 uint16_t(*hits)[32] = S.hits[ew];
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + acc * NMAX;
-                for (int c0 = 0; c0 < X.ncol; c0 += 64) {
-                    // 64 columns per round trip (columns past N are stale and masked)
-                    uint32_t v[64];
+                for (int c0 = 32 * half; c0 < X.ncol; c0 += 64) {
+                    // columns past N are stale and masked
+                    uint32_t v[32];
                     tmem_ld32(taddr + (uint32_t)c0, v);
-                    tmem_ld32(taddr + (uint32_t)c0 + 32u, v + 32);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    // maxima of 8-column groups, then of all 64
-                    float m8[8];
+                    // maxima of 8-column groups, then of all 32
+                    float m8[4];
 #pragma unroll
-                    for (int g8 = 0; g8 < 8; ++g8) {
+                    for (int g8 = 0; g8 < 4; ++g8) {
                         const float* f = reinterpret_cast<const float*>(v + 8 * g8);
                         m8[g8] = fmaxf(fmaxf(fmaxf(f[0], f[1]), fmaxf(f[2], f[3])),
                                        fmaxf(fmaxf(f[4], f[5]), fmaxf(f[6], f[7])));
                     }
-                    const float mall = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])),
-                                             fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
+                    const float mall = fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3]));
                     if (!__any_sync(0xffffffffu, cvalid && mall >= cto)) continue;
                     int hn = 0;
 #pragma unroll
-                    for (int g8 = 0; g8 < 8; ++g8) {
+                    for (int g8 = 0; g8 < 4; ++g8) {
                         const bool h = cvalid && m8[g8] >= cto;
                         if (!__any_sync(0xffffffffu, h)) continue;
 #pragma unroll
@@ -530,8 +545,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
                             mir = cfl == 1 || (cfl == 2 && cp != qs);
                             if ((e >> 8) && !EMIT) {
                                 nout = mir ? 2 : 1;
-                                qid = (int32_t)(P.perm[qs] - R.off);
-                                cid = (int32_t)(P.perm[cp] - R.off);
+                                qid = (int32_t)(qperm[qs - X.qa] - R.off);
+                                cid = (int32_t)(cpid - R.off);
                             } else {
                                 band = true;
                             }
@@ -542,8 +557,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
                             ++rechecked;
                             if (s2 <= R.e2) {
                                 nout = mir ? 2 : 1;
-                                qid = (int32_t)(P.perm[qs] - R.off);
-                                cid = (int32_t)(P.perm[cp] - R.off);
+                                qid = (int32_t)(qperm[qs - X.qa] - R.off);
+                                cid = (int32_t)(cpid - R.off);
                                 if (EMIT) dist = sqrt(s2);
                             }
                         }
