@@ -56,9 +56,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0 = sized for ~15 s)")
     ap.add_argument("--hint", type=int, default=0, help="expected result pairs (0 = the library's automatic pool)")
-    ap.add_argument("--workload", default="uniform4d", choices=["uniform4d", "mixture16d", "expo64d", "batched"],
-                    help="uniform4d: the 2M-point 4-D self-join (the headline); mixture16d: 1M x 16 Gaussian "
-                         "mixture; expo64d: 500k x 64 clipped exponential; batched: 4096 independent joins")
+    ap.add_argument("--workload", default="uniform4d",
+                    choices=["uniform4d", "uniform2d", "mixture16d", "expo64d", "batched"],
+                    help="uniform4d: the 2M-point 4-D self-join (the headline); uniform2d: 16384 x 2; mixture16d: "
+                         "1M x 16 Gaussian mixture; expo64d: 500k x 64 clipped exponential; batched: 4096 "
+                         "independent joins")
     ap.add_argument("--batch-count", type=int, default=4096)
     return ap.parse_args()
 
@@ -72,6 +74,7 @@ def dist_env():
 
 WORKLOAD_TEXT = {
     "uniform4d": "points i.i.d. uniform in [0,1]^4, eps from the 4-ball volume for a mean of 64 neighbours",
+    "uniform2d": "points i.i.d. uniform in [0,1]^2, eps = sqrt(32 / (pi n))",
     "mixture16d": "32 isotropic Gaussians in 16-D (centres uniform in [0,1]^16, sigma 0.04, equal weights), "
                   "eps calibrated on the oracle for a mean of 100 neighbours",
     "expo64d": "64-D coordinates i.i.d. exponential(40) clipped to [0,1], eps calibrated on the oracle for a "
@@ -79,12 +82,14 @@ WORKLOAD_TEXT = {
 }
 METRICS = {
     "uniform4d": METRIC,
+    "uniform2d": "self-join candidate pairs/s and join time, n=16384 d=2: FP64 plain vs low-prec filter",
     "mixture16d": "self-join candidate pairs/s and join time, n=1M d=16 Gaussian mixture: FP64 plain vs low-prec filter",
     "expo64d": "self-join candidate pairs/s and join time, n=500k d=64 clipped exponential: FP64 plain vs "
                "low-prec filter",
 }
 DEFAULT_VARIANTS = {
     "uniform4d": ["filter_f32", "fp64_fma", "fp64_dmma"],
+    "uniform2d": ["filter_f32", "fp64_fma", "fp64_dmma", "filter_bf16x3"],
     "mixture16d": ["filter_bf16x3", "filter_f32", "fp64_fma"],
     "expo64d": ["filter_bf16x3", "filter_f32"],
 }
@@ -445,7 +450,9 @@ def run_reference(args):
 
 # ---- batched workload ------------------------------------------------------------------
 
-BATCH_METRIC = "batched self-joins: candidate pairs/s and join time, 4096 instances, n log-uniform [256, 65536], d in {2,4,8,16,32}"
+BATCH_METRIC = ("batched self-joins: brute-force pair equivalents/s (sum of n_i^2 / step time) and join time, 4096 "
+                "instances, n log-uniform [256, 65536], d in {2,4,8,16,32}")
+BATCH_UNIT = "pair equivalents/s"
 
 
 def batch_config(count, total_n, extra=None):
@@ -573,13 +580,15 @@ def run_batched(args):
     for k in variants:
         r = results[k]
         var[k] = {"ms_per_step": round(r["ms_per_step"], 3),
-                  "candidate_pairs_per_s": world * r["n_candidates"] / (r["ms_per_step"] * 1e-3),
+                  "pair_equivalents_per_s": world * float(sum(w.n * w.n for w in insts)) / (r["ms_per_step"] * 1e-3),
+                  "candidate_pairs": r["n_candidates"],
                   "instances_per_s": world * len(insts) / (r["ms_per_step"] * 1e-3),
                   "result_pairs": r["count"], "evaluated_pairs": r["n_evaluated"], "reruns": r["reruns"],
                   "tile_kernel_ms": round(r["tile_ms"], 3), "launches_per_step": r["launches"],
                   "groups": batch_rooflines(r)}
-    line = {"metric": BATCH_METRIC, "value": world * head["n_candidates"] / (head["ms_per_step"] * 1e-3),
-            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+    nsq = float(sum(w.n * w.n for w in insts))  # the grid-independent unit of work
+    line = {"metric": BATCH_METRIC, "value": world * nsq / (head["ms_per_step"] * 1e-3),
+            "unit": BATCH_UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(head["ms_per_step"], 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPES.get(variants[0], "f64"),
             "data": "synthetic",
@@ -589,17 +598,17 @@ def run_batched(args):
                                                           "candidate_pairs": head["n_candidates"],
                                                           "result_pairs": head["count"]}),
             "variants": var,
-            "e2e": {"value": world * head["n_candidates"] / e2e_s, "unit": UNIT,
+            "e2e": {"value": world * nsq / e2e_s, "unit": BATCH_UNIT,
                     "h2d_bytes_per_step": sum(w.n * w.d * 8 for w in insts),
                     "d2h_bytes_per_step": head["count"] * 8, "ms_per_step": round(e2e_s * 1e3, 1)},
             "roofline": max(batch_rooflines(head).values(), key=lambda g: g["kernel_ms"]),
-            "cpu_baseline": None if args.no_cpu_baseline else batch_cpu_baseline(insts, head["n_candidates"]),
+            "cpu_baseline": None if args.no_cpu_baseline else batch_cpu_baseline(insts, nsq),
             "gpu_launches": int(head["launches"]),
             "clocks": results[variants[-1]]["clocks"]}
     print(json.dumps(line), flush=True)
 
 
-def batch_cpu_baseline(insts, n_candidates):
+def batch_cpu_baseline(insts, nsq):
     """The oracle (brute force, every sampled query against all points of its
     instance) on the host cores for sampled queries of sampled instances,
     scaled by n / sample per instance and by instances / sampled instances."""
@@ -624,7 +633,7 @@ def batch_cpu_baseline(insts, n_candidates):
     _, probe = run(16)
     qpi = int(max(16, min(4096, 16 * 10.0 / max(probe, 1e-3))))  # ~10 s of oracle work
     full_s, spent = run(qpi)
-    return {"value": n_candidates / full_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": nsq / full_s, "unit": BATCH_UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{qpi} queries of each of 64 sampled instances (seeded), each against all points of its "
                       f"instance, scaled by n / sample and 4096 / 64",
             "sample_seconds": round(spent, 2), "full_batch_seconds_est": round(full_s, 1)}

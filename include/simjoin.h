@@ -66,7 +66,9 @@ extern "C" {
 #define SJ_MAX_D 128
 
 /* ---- distance kernels -------------------------------------------------- */
-#define SJ_KERNEL_AUTO 0        /* fastest certified kernel for (d, sizes) */
+#define SJ_KERNEL_AUTO 0        /* single joins: SJ_KERNEL_FILTER_BF16X3 for
+                                   16 <= d <= 64, else SJ_KERNEL_FILTER_F32
+                                   (batched joins: see sj_join_batch) */
 #define SJ_KERNEL_FP64_FMA 1    /* FP64 CUDA-core FMA tiles (expanded form,
                                    Eq. 3) + direct-form recheck of the band */
 #define SJ_KERNEL_FP64_DMMA 2   /* FP64 tensor-core tiles, mma.sync m8n8k4
@@ -189,7 +191,7 @@ SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj
  * of the group's work items run in one persistent distance-tile launch
  * (kernels SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_BF16X3 (padded d <= 64) or
  * SJ_KERNEL_FP64_FMA; AUTO takes the tensor-core filter for groups of padded
- * dimension 16 .. 64 and the FP32 filter for the others; SJ_KERNEL_FP64_DMMA
+ * dimension 8 .. 64 and the FP32 filter for the others; SJ_KERNEL_FP64_DMMA
  * gives SJ_ERR_UNSUPPORTED).  Pairs carry instance-local indices and
  * satisfy the same decision rule as sj_self_join.  The device takes each
  * instance's result pages from one shared pool (opt->page_pairs rounded up

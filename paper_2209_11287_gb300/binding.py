@@ -338,11 +338,11 @@ def self_join(points, eps: float, kernel="auto", emit_distances=False, symmetric
 
 
 def join_batch(points_list, eps_list, kernel="auto", emit_distances=False, symmetric=True, page_pairs=0,
-               max_pairs_hint=0, stream=None):
+               max_pairs_hint=0, indexed_dims=0, stream=None):
     """Batched self-joins in one call: returns one (pairs, distances or None,
     stats) per instance, the results already copied to the host and freed."""
     opt = sj_default_options(kernel=kernel, emit_distances=int(emit_distances), symmetric=int(symmetric),
-                             page_pairs=page_pairs, max_pairs_hint=max_pairs_hint)
+                             page_pairs=page_pairs, max_pairs_hint=max_pairs_hint, indexed_dims=indexed_dims)
     res = sj_join_batch(points_list, eps_list, opt, stream)
     out = []
     try:

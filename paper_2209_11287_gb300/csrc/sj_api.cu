@@ -118,13 +118,13 @@ static void release_index(Index* ix) {
 }
 
 // AUTO: the certified filters always beat the plain FP64 kernels on this part
-// (FP64 runs at ~1/70 of FP32); the tensor-core filter wins once the dot
-// product is long enough to amortise its tiles (measured: d = 64 2.6x faster
-// than the FP32 filter, d = 16 2x slower), the FP32 CUDA-core filter below.
+// (FP64 runs at ~1/60 of FP32); the tensor-core filter wins once the dot
+// product is long enough to amortise its tiles (measured: d = 64 12x and
+// d = 16 1.3x faster than the FP32 filter), the FP32 CUDA-core filter below.
 static int pick_kernel(const Index* ix) {
     int k = ix->opt.kernel;
     if (k != SJ_KERNEL_AUTO) return k;
-    return (ix->d > 16 && ix->d <= 64) ? SJ_KERNEL_FILTER_BF16X3 : SJ_KERNEL_FILTER_F32;
+    return (ix->d >= 16 && ix->d <= 64) ? SJ_KERNEL_FILTER_BF16X3 : SJ_KERNEL_FILTER_F32;
 }
 
 static int round_dim(int d) {
@@ -495,12 +495,12 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
                   "kernel %d)", o.kernel);
         return SJ_ERR_UNSUPPORTED;
     }
-    // AUTO: the tensor-core filter for padded dimensions 16 .. 64 (the batched
-    // instances there are near brute force, where its tiles pay), else the
-    // FP32 CUDA-core filter
+    // AUTO: the tensor-core filter for padded dimensions 8 .. 64 (measured on
+    // uniform instances with the batched grid choice: d 8 1.7x, d 16 4x, d 32
+    // 12x faster than the FP32 filter), else the FP32 CUDA-core filter
     auto group_kernel = [&](int dp) {
         if (o.kernel != SJ_KERNEL_AUTO) return o.kernel;
-        return (dp >= 16 && dp <= 64) ? SJ_KERNEL_FILTER_BF16X3 : SJ_KERNEL_FILTER_F32;
+        return (dp >= 8 && dp <= 64) ? SJ_KERNEL_FILTER_BF16X3 : SJ_KERNEL_FILTER_F32;
     };
     for (int32_t k = 0; k < count; ++k)
         if (group_kernel(round_dim(d[k])) == SJ_KERNEL_FILTER_BF16X3 && round_dim(d[k]) > 64) {

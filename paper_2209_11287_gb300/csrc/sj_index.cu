@@ -664,6 +664,33 @@ static int choose_grid(Index* ix) {
         prod *= (long double)c.ncell;
         take.push_back(c);
     }
+    // Batched instances (uniform data assumed): fewer indexed dims when that
+    // costs less.  The distance kernels run work items of up to qmax queries
+    // against every point of the item's neighbourhood: with M = min(n, cells
+    // of the first m dims) cells of q = n / M points, and a dim of c cells
+    // keeping the fraction (3c - 2) / c^2 of the points within +-1 cell, the
+    // work is about M ceil(q / qmax) qmax n prod_k (3 c_k - 2) / c_k^2.  The
+    // tensor-core filter's large items pay for few big cells.
+    if (ix->trim_dims && ix->opt.indexed_dims <= 0 && !take.empty()) {
+        const int qmax = ix->kernel == SJ_KERNEL_FILTER_BF16X3 ? tc_qmax(tc_kp(ix->dp)) : kQMax;
+        const double nn = (double)ix->n;
+        int best = 0;
+        double best_cost = 0, cells = 1, frac = 1;
+        for (int j = 0; j <= (int)take.size(); ++j) {
+            if (j > 0) {
+                const double c = (double)take[j - 1].ncell;
+                cells *= c;
+                frac *= (3.0 * c - 2.0) / (c * c);
+            }
+            const double M = std::min(nn, cells), q = nn / M;
+            const double cost = M * std::ceil(q / qmax) * qmax * nn * frac;
+            if (j == 0 || cost < best_cost) {
+                best = j;
+                best_cost = cost;
+            }
+        }
+        take.resize(best);
+    }
     // keep the input order of the chosen dims (row-major keys)
     std::sort(take.begin(), take.end(), [](const Cand& a, const Cand& b) { return a.k < b.k; });
     ix->m = (int)take.size();
@@ -1331,6 +1358,9 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
         t.dp = dp;
         t.eps = g->eps[k];
         t.opt = ix->opt;
+        t.kernel = ix->kernel;
+        t.n = g->off[k + 1] - g->off[k];
+        t.trim_dims = true;
         t.key_bits_cap = std::min(62, 64 - inst_bits);
         t.lo.resize(dp);
         t.hi.resize(dp);

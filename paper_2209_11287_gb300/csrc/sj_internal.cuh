@@ -80,6 +80,7 @@ struct Index {
     uint64_t stride[kMaxM] = {};
     int key_bits = 0;
     int key_bits_cap = 62;      // cell keys use at most this many bits
+    bool trim_dims = false;     // batched instances: drop indexed dims by a uniform-density cost model
     std::vector<double> lo, hi;
 
     // device arrays (cell order)

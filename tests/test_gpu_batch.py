@@ -85,6 +85,14 @@ def test_mixed_batch(kernel, symmetric):
     _check(pts, eps, out, with_dist=False)
 
 
+@pytest.mark.parametrize("indexed_dims", [1, 3, 6])
+def test_mixed_batch_indexed_dims(indexed_dims):
+    """Any choice of indexed dims gives the same pairs."""
+    pts, eps = _mixed_batch(seed=3)
+    out = binding.join_batch(pts, eps, kernel="auto", indexed_dims=indexed_dims)
+    _check(pts, eps, out, with_dist=False)
+
+
 @pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3"])
 def test_mixed_batch_distances_host_input(kernel):
     pts, eps = _mixed_batch(seed=1)
@@ -105,11 +113,11 @@ def test_pool_regrow(kernel):
 
 def test_candidate_counts_per_instance():
     """Each instance's canonical candidate count is that of its own grid
-    (cells of side eps (1 + 2^-20) over its own extent)."""
+    (cells of side eps (1 + 2^-20) over its own extent, every dim indexed)."""
     g = np.random.default_rng(5)
-    pts = [g.random((2000, 2)), g.random((3000, 3)), g.random((1000, 2))]
+    pts = [g.random((2000, 2)), g.random((3000, 2)), g.random((1000, 2))]
     eps = [0.02, 0.05, 0.04]
-    out = binding.join_batch(pts, eps, kernel="fp64_fma")
+    out = binding.join_batch(pts, eps, kernel="fp64_fma", indexed_dims=2)
     for x, e, (_, _, st) in zip(pts, eps, out):
         assert st["n_candidates"] == oracle.grid_candidate_count(x, e * (1.0 + 2.0 ** -20))
 
