@@ -40,8 +40,9 @@ FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 f
 FP64_DFMA_TFLOPS = 1.255                                  # measured, profiles/fp64_peaks_gb300.txt
 FP64_DMMA_TFLOPS = 1.102                                  # measured, profiles/fp64_peaks_gb300.txt
 KERNEL_NAMES = {"filter_f32": "k_join_cc<float>", "fp64_fma": "k_join_cc<double>", "fp64_dmma": "k_join_dmma",
-                "filter_bf16x3": "k_join_tc"}
-DTYPES = {"auto": "bf16x3|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64", "fp64_fma": "f64",
+                "filter_bf16x3": "k_join_tc", "filter_bf16x2": "k_join_tc"}
+DTYPES = {"auto": "bf16x2|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64",
+          "filter_bf16x2": "bf16x2+f64", "fp64_fma": "f64",
           "fp64_dmma": "f64"}
 
 
@@ -89,9 +90,9 @@ METRICS = {
 }
 DEFAULT_VARIANTS = {
     "uniform4d": ["filter_f32", "fp64_fma", "fp64_dmma"],
-    "uniform2d": ["filter_f32", "fp64_fma", "fp64_dmma", "filter_bf16x3"],
-    "mixture16d": ["filter_bf16x3", "filter_f32", "fp64_fma"],
-    "expo64d": ["filter_bf16x3", "filter_f32"],
+    "uniform2d": ["filter_f32", "fp64_fma", "fp64_dmma", "filter_bf16x2"],
+    "mixture16d": ["filter_bf16x2", "filter_bf16x3", "filter_f32", "fp64_fma"],
+    "expo64d": ["filter_bf16x2", "filter_bf16x3", "filter_f32"],
 }
 
 
@@ -280,7 +281,8 @@ def kernel_source_sha(kname):
     tile header), to tie committed counters to the code they were taken on."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2209_11287_gb300", "csrc")
-    main = {"fp64_dmma": "sj_join_dmma.cu", "filter_bf16x3": "sj_join_tc.cu"}.get(kname, "sj_join_cc.cu")
+    main = {"fp64_dmma": "sj_join_dmma.cu", "filter_bf16x3": "sj_join_tc.cu",
+            "filter_bf16x2": "sj_join_tc.cu"}.get(kname, "sj_join_cc.cu")
     files = [main, "sj_join_common.cuh"]
     h = hashlib.sha256()
     for f in files:
@@ -317,9 +319,10 @@ def roofline(kname, w, r, kern_ms):
     micro-benchmark, profiles/fp64_peaks_gb300.txt); for the tensor-core
     filter 2 K flop per evaluated pair (K the padded split-row length, 6
     products per dim plus the norm slots) against the measured burst bf16
-    peak.  Bytes: every packed point read once (coordinates, norm, two
-    thresholds, input index) plus 8 bytes per emitted pair, against the
-    measured HBM copy bandwidth.  The larger fraction is the binding one."""
+    peak (K = 6 dp + 3 for BF16x3, 3 dp + 3 for BF16x2, padded to 16).  Bytes:
+    every packed point read once (coordinates, norm, two thresholds, input
+    index) plus 8 bytes per emitted pair, against the measured HBM copy
+    bandwidth.  The larger fraction is the binding one."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -330,8 +333,8 @@ def roofline(kname, w, r, kern_ms):
     dp = 2
     while dp < w.d:
         dp *= 2
-    if kname == "filter_bf16x3":
-        kp = (6 * dp + 3 + 15) // 16 * 16
+    if kname in ("filter_bf16x3", "filter_bf16x2"):
+        kp = ((6 if kname == "filter_bf16x3" else 3) * dp + 3 + 15) // 16 * 16
         flops = 2.0 * kp * r["n_evaluated"]
         fp_peak, unit_bound = float(peaks.get("bf16_tflops", 1900.0)), "tensor"
     else:
@@ -532,7 +535,7 @@ def run_batched(args):
         tile = sum(g["ms"] for g in groups.values())
         return cnt, cand, evald, reruns, tile, groups, maxc
 
-    allowed = ("auto", "filter_f32", "filter_bf16x3", "fp64_fma")
+    allowed = ("auto", "filter_f32", "filter_bf16x3", "filter_bf16x2", "fp64_fma")
     asked = args.variants.split(",") if args.variants != ",".join(VARIANTS) else ["auto", "filter_f32", "fp64_fma"]
     variants = [v for v in asked if v in allowed] or ["auto"]
     sampler = ClockSampler(local)
@@ -655,9 +658,9 @@ def batch_rooflines(r):
     out = {}
     for dp, g in sorted(r["groups"].items()):
         sec = max(g["ms"], 1e-6) * 1e-3
-        if g["kernel"] == "filter_bf16x3":
-            kp = (6 * dp + 3 + 15) // 16 * 16
-            flops, peak, kern = 2.0 * kp * g["evaluated"], bf16, "k_join_tc<bf16x3>"
+        if g["kernel"] in ("filter_bf16x3", "filter_bf16x2"):
+            kp = ((6 if g["kernel"] == "filter_bf16x3" else 3) * dp + 3 + 15) // 16 * 16
+            flops, peak, kern = 2.0 * kp * g["evaluated"], bf16, "k_join_tc<" + g["kernel"][7:] + ">"
             bound = "tensor"
         else:
             flops = g["flops_2d"]

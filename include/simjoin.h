@@ -66,7 +66,7 @@ extern "C" {
 #define SJ_MAX_D 128
 
 /* ---- distance kernels -------------------------------------------------- */
-#define SJ_KERNEL_AUTO 0        /* single joins: SJ_KERNEL_FILTER_BF16X3 for
+#define SJ_KERNEL_AUTO 0        /* single joins: SJ_KERNEL_FILTER_BF16X2 for
                                    16 <= d <= 64, else SJ_KERNEL_FILTER_F32
                                    (batched joins: see sj_join_batch) */
 #define SJ_KERNEL_FP64_FMA 1    /* FP64 CUDA-core FMA tiles (expanded form,
@@ -76,8 +76,12 @@ extern "C" {
 #define SJ_KERNEL_FILTER_F32 3  /* FP32 CUDA-core filter with certified bound,
                                    FP64 direct recheck of the band */
 #define SJ_KERNEL_FILTER_BF16X3 4 /* tcgen05 kind::f16 with 3-term bf16 split
-                                     operands, FP32 accumulation in TMEM,
-                                     certified bound, FP64 recheck */
+                                     operands (6 products per dim), FP32
+                                     accumulation in TMEM, certified bound,
+                                     FP64 recheck; d <= 64 */
+#define SJ_KERNEL_FILTER_BF16X2 5 /* as BF16X3 with a 2-term split (3 products
+                                     per dim: half the K, a slightly wider
+                                     certified band); d <= 64 */
 
 /* ---- options ----------------------------------------------------------- */
 typedef struct sj_options {
@@ -179,6 +183,16 @@ SJ_API void sj_result_free(sj_result* r);
 SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt, void* stream,
             sj_result* out);
 
+/*
+ * Failure-detection self-test (no counterpart in the paper): launches a
+ * kernel whose thread waits on a shared-memory mbarrier that nothing arrives
+ * on, with the same bounded wait the tensor-core filter uses (here 2^16
+ * polls).  The wait must give up, raise the kernel's abort flag and return,
+ * leaving the context usable.  Returns SJ_ERR_TIMEOUT when it did (the
+ * expected outcome), SJ_ERR_CUDA otherwise.  Synchronous on `stream`.
+ */
+SJ_API int sj_selftest_bounded_wait(void* stream);
+
 /* ---- batched joins ----------------------------------------------------- */
 /*
  * Runs `count` independent self-joins (instance k: pts[k], n[k] row-major
@@ -189,9 +203,10 @@ SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj
  * group's index is built by segmented kernels over composite cell keys
  * (instance << S | cell key of the instance's own grid, Sec. III-A) and all
  * of the group's work items run in one persistent distance-tile launch
- * (kernels SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_BF16X3 (padded d <= 64) or
- * SJ_KERNEL_FP64_FMA; AUTO takes the tensor-core filter for groups of padded
- * dimension 8 .. 64 and the FP32 filter for the others; SJ_KERNEL_FP64_DMMA
+ * (kernels SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_BF16X3 / _BF16X2 (padded
+ * d <= 64) or SJ_KERNEL_FP64_FMA; AUTO takes SJ_KERNEL_FILTER_BF16X2 for
+ * groups of padded dimension 8 .. 64 and the FP32 filter for the others;
+ * SJ_KERNEL_FP64_DMMA
  * gives SJ_ERR_UNSUPPORTED).  Pairs carry instance-local indices and
  * satisfy the same decision rule as sj_self_join.  The device takes each
  * instance's result pages from one shared pool (opt->page_pairs rounded up

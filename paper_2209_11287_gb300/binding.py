@@ -32,6 +32,7 @@ SJ_KERNEL_FP64_FMA = 1
 SJ_KERNEL_FP64_DMMA = 2
 SJ_KERNEL_FILTER_F32 = 3
 SJ_KERNEL_FILTER_BF16X3 = 4
+SJ_KERNEL_FILTER_BF16X2 = 5
 
 KERNELS = {
     "auto": SJ_KERNEL_AUTO,
@@ -39,6 +40,7 @@ KERNELS = {
     "fp64_dmma": SJ_KERNEL_FP64_DMMA,
     "filter_f32": SJ_KERNEL_FILTER_F32,
     "filter_bf16x3": SJ_KERNEL_FILTER_BF16X3,
+    "filter_bf16x2": SJ_KERNEL_FILTER_BF16X2,
 }
 
 
@@ -134,6 +136,8 @@ def load():
         lib.sj_kernel_launches.restype = ctypes.c_int64
         lib.sj_self_join_noalloc.argtypes = [_vp, _i64, _i32, ctypes.c_double, _vp, _i64, ctypes.POINTER(_i64), _vp]
         lib.sj_self_join_noalloc.restype = ctypes.c_int
+        lib.sj_selftest_bounded_wait.argtypes = [_vp]
+        lib.sj_selftest_bounded_wait.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -296,6 +300,12 @@ def sj_self_join_noalloc(points, eps: float, pairs_out, stream=None) -> int:
                                        ctypes.byref(cnt), _stream_ptr(stream)))
     del keep
     return int(cnt.value)
+
+
+def sj_selftest_bounded_wait(stream=None) -> int:
+    """Runs the library's bounded-wait self-test; returns its status
+    (SJ_ERR_TIMEOUT when the wait gave up as designed)."""
+    return int(load().sj_selftest_bounded_wait(_stream_ptr(stream)))
 
 
 def sj_error_string(status: int) -> str:

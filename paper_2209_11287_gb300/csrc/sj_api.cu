@@ -124,7 +124,7 @@ static void release_index(Index* ix) {
 static int pick_kernel(const Index* ix) {
     int k = ix->opt.kernel;
     if (k != SJ_KERNEL_AUTO) return k;
-    return (ix->d >= 16 && ix->d <= 64) ? SJ_KERNEL_FILTER_BF16X3 : SJ_KERNEL_FILTER_F32;
+    return (ix->d >= 16 && ix->d <= 64) ? SJ_KERNEL_FILTER_BF16X2 : SJ_KERNEL_FILTER_F32;
 }
 
 static int round_dim(int d) {
@@ -172,6 +172,11 @@ const char* sj_version(void) { return "libsj 0.1 sm_103a"; }
 
 int64_t sj_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
+int sj_selftest_bounded_wait(void* stream) {
+    clear_error();
+    return selftest_bounded_wait(static_cast<cudaStream_t>(stream));
+}
+
 int sj_build_index(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt, void* stream,
                    sj_handle* out) {
     clear_error();
@@ -187,7 +192,7 @@ int sj_build_index(const double* pts, int64_t n, int32_t d, double eps, const sj
     sj_options o;
     sj_default_options(&o);
     if (opt) o = *opt;
-    if (o.kernel < SJ_KERNEL_AUTO || o.kernel > SJ_KERNEL_FILTER_BF16X3 || o.indexed_dims < 0 ||
+    if (o.kernel < SJ_KERNEL_AUTO || o.kernel > SJ_KERNEL_FILTER_BF16X2 || o.indexed_dims < 0 ||
         o.queries_per_item < 0 || o.page_pairs < 0 || o.max_pairs_hint < 0) {
         set_error("invalid options");
         return SJ_ERR_ARG;
@@ -208,7 +213,7 @@ int sj_build_index(const double* pts, int64_t n, int32_t d, double eps, const sj
     ix->eps = eps;
     ix->e2 = eps * eps;
     ix->kernel = pick_kernel(ix);
-    if (ix->kernel == SJ_KERNEL_FILTER_BF16X3 && ix->dp > 64) {
+    if (is_tensor_kernel(ix->kernel) && ix->dp > 64) {
         set_error("the tensor-core filter supports d <= 64 (got d = %d)", (int)d);
         delete ix;
         return SJ_ERR_UNSUPPORTED;
@@ -327,7 +332,7 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
         SJ_CK(cudaEventRecord(ix->ev_tile[0], s));
         if (ix->kernel == SJ_KERNEL_FP64_DMMA)
             st = launch_join_dmma(ix, jo, dist ? 1 : 0);
-        else if (ix->kernel == SJ_KERNEL_FILTER_BF16X3)
+        else if (is_tensor_kernel(ix->kernel))
             st = launch_join_tc(ix, jo, dist ? 1 : 0);
         else
             st = launch_join_cc(ix, jo, dist ? 1 : 0);
@@ -490,7 +495,7 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
     sj_default_options(&o);
     if (opt) o = *opt;
     if (o.kernel != SJ_KERNEL_AUTO && o.kernel != SJ_KERNEL_FILTER_F32 && o.kernel != SJ_KERNEL_FP64_FMA &&
-        o.kernel != SJ_KERNEL_FILTER_BF16X3) {
+        o.kernel != SJ_KERNEL_FILTER_BF16X3 && o.kernel != SJ_KERNEL_FILTER_BF16X2) {
         set_error("batched joins run the FP32 filter, the tensor-core filter or the FP64 CUDA-core kernel (got "
                   "kernel %d)", o.kernel);
         return SJ_ERR_UNSUPPORTED;
@@ -500,10 +505,10 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
     // 12x faster than the FP32 filter), else the FP32 CUDA-core filter
     auto group_kernel = [&](int dp) {
         if (o.kernel != SJ_KERNEL_AUTO) return o.kernel;
-        return (dp >= 8 && dp <= 64) ? SJ_KERNEL_FILTER_BF16X3 : SJ_KERNEL_FILTER_F32;
+        return (dp >= 8 && dp <= 64) ? SJ_KERNEL_FILTER_BF16X2 : SJ_KERNEL_FILTER_F32;
     };
     for (int32_t k = 0; k < count; ++k)
-        if (group_kernel(round_dim(d[k])) == SJ_KERNEL_FILTER_BF16X3 && round_dim(d[k]) > 64) {
+        if (is_tensor_kernel(group_kernel(round_dim(d[k]))) && round_dim(d[k]) > 64) {
             set_error("the tensor-core filter supports d <= 64 (instance %d has d = %d)", (int)k, (int)d[k]);
             return SJ_ERR_UNSUPPORTED;
         }
@@ -703,7 +708,7 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
             if (e == cudaSuccess) e = cudaEventRecord(ix->ev_tile[0], s);
             if (e != cudaSuccess) st = SJ_ERR_CUDA;
             if (st == SJ_OK)
-                st = ix->kernel == SJ_KERNEL_FILTER_BF16X3 ? launch_join_tc(ix, jo, dist ? 1 : 0)
+                st = is_tensor_kernel(ix->kernel) ? launch_join_tc(ix, jo, dist ? 1 : 0)
                                                            : launch_join_cc(ix, jo, dist ? 1 : 0);
             if (st == SJ_OK && cudaEventRecord(ix->ev_tile[1], s) != cudaSuccess) st = SJ_ERR_CUDA;
             if (st == SJ_OK) st = launch_recheck(ix, jo, dist ? 1 : 0);
@@ -724,7 +729,7 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
             float ms = 0.f;
             if (g->ix.n_items > 0 && cudaEventElapsedTime(&ms, g->ix.ev_tile[0], g->ix.ev_tile[1]) == cudaSuccess)
                 group_ms[gi] = ms;
-            if (g->ix.kernel == SJ_KERNEL_FILTER_BF16X3 && g->ix.n_items > 0) {
+            if (is_tensor_kernel(g->ix.kernel) && g->ix.n_items > 0) {
                 unsigned long long flag = 0;  // the tensor-core kernel's bounded-wait flag
                 if (cudaMemcpy(&flag, g->ix.counters + 4, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess ||
                     flag != 0)

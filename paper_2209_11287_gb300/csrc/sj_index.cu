@@ -672,7 +672,7 @@ static int choose_grid(Index* ix) {
     // work is about M ceil(q / qmax) qmax n prod_k (3 c_k - 2) / c_k^2.  The
     // tensor-core filter's large items pay for few big cells.
     if (ix->trim_dims && ix->opt.indexed_dims <= 0 && !take.empty()) {
-        const int qmax = ix->kernel == SJ_KERNEL_FILTER_BF16X3 ? tc_qmax(tc_kp(ix->dp)) : kQMax;
+        const int qmax = is_tensor_kernel(ix->kernel) ? tc_qmax(tc_kp(ix->dp, ix->kernel)) : kQMax;
         const double nn = (double)ix->n;
         int best = 0;
         double best_cost = 0, cells = 1, frac = 1;
@@ -762,8 +762,10 @@ __device__ __forceinline__ int64_t split_at(int64_t p, int k, int kp, int64_t nr
 
 // One thread per 16-byte chunk (8 K slots of one row): consecutive threads
 // write consecutive rows of a chunk, so a warp stores whole 128-byte lines.
+// prod = 6 (BF16x3) or 3 (BF16x2: per dim candidate (c1, c2, c1), query
+// (q1, q1, q2) of the first two split terms, which t1 and t2 of split3 are).
 __global__ void k_pack_split(const float* __restrict__ y, const float* __restrict__ h, int64_t n, int dp, int kp,
-                             int64_t nrows, __nv_bfloat16* rows_a, __nv_bfloat16* rows_b) {
+                             int prod, int64_t nrows, __nv_bfloat16* rows_a, __nv_bfloat16* rows_b) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int ch = kp >> 3;
     const int64_t grp = t / (8 * ch);
@@ -776,22 +778,30 @@ __global__ void k_pack_split(const float* __restrict__ y, const float* __restric
     for (int u = 0; u < 8; ++u) {
         const int k = c * 8 + u;
         __nv_bfloat16 a = zero, b = zero;
-        if (k < 6 * dp) {
+        if (k < prod * dp) {
             __nv_bfloat16 t1, t2, t3;
-            split3(y[p * dp + k / 6], t1, t2, t3);
-            switch (k % 6) {  // candidate (c1, c2, c1, c3, c2, c1), query (q1, q1, q2, q1, q2, q3)
-                case 0: a = t1; b = t1; break;
-                case 1: a = t2; b = t1; break;
-                case 2: a = t1; b = t2; break;
-                case 3: a = t3; b = t1; break;
-                case 4: a = t2; b = t2; break;
-                default: a = t1; b = t3; break;
+            split3(y[p * dp + k / prod], t1, t2, t3);
+            if (prod == 6) {
+                switch (k % 6) {  // candidate (c1, c2, c1, c3, c2, c1), query (q1, q1, q2, q1, q2, q3)
+                    case 0: a = t1; b = t1; break;
+                    case 1: a = t2; b = t1; break;
+                    case 2: a = t1; b = t2; break;
+                    case 3: a = t3; b = t1; break;
+                    case 4: a = t2; b = t2; break;
+                    default: a = t1; b = t3; break;
+                }
+            } else {
+                switch (k % 3) {  // candidate (c1, c2, c1), query (q1, q1, q2)
+                    case 0: a = t1; b = t1; break;
+                    case 1: a = t2; b = t1; break;
+                    default: a = t1; b = t2; break;
+                }
             }
-        } else if (k < 6 * dp + 3) {
+        } else if (k < prod * dp + 3) {
             __nv_bfloat16 h1, h2, h3;
             split3(h[p], h1, h2, h3);
             a = one;
-            b = k == 6 * dp ? h1 : (k == 6 * dp + 1 ? h2 : h3);
+            b = k == prod * dp ? h1 : (k == prod * dp + 1 ? h2 : h3);
         }
         av[u] = a;
         bv[u] = b;
@@ -804,7 +814,7 @@ __global__ void k_pack_split(const float* __restrict__ y, const float* __restric
 static int pack_split_rows(Index* ix) {
     cudaStream_t s = ix->stream;
     const int64_t n = ix->n;
-    ix->kp = tc_kp(ix->dp);
+    ix->kp = tc_kp(ix->dp, ix->kernel);
     const int64_t nrows = ((n + 7) & ~int64_t(7)) + kTcPadRows;
     const size_t elems = (size_t)nrows * ix->kp;
     __nv_bfloat16 *ra = nullptr, *rb = nullptr;
@@ -817,10 +827,29 @@ static int pack_split_rows(Index* ix) {
     const int64_t threads = ((n + 7) / 8) * 8 * (ix->kp / 8);
     k_pack_split<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(static_cast<const float*>(ix->y),
                                                             static_cast<const float*>(ix->h), n, ix->dp, ix->kp,
-                                                            nrows, ra, rb);
+                                                            tc_products(ix->kernel), nrows, ra, rb);
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
+}
+
+// Tensor-core filter: |s_y - (pc - 2a)| <= gamma_32(dp) (Pq + Pc) for the
+// FP32 norms plus twice the dot-product error.  The products of bf16 terms are
+// exact in FP32; the FP32 accumulation of K products is taken to lose up to
+// 2^-22 relative at every addition (truncation): at most 1.02 K 2^-22 (Pq+Pc).
+// The split products left out add, relative to sum_k |yq_k| |yc_k| <=
+// (Pq + Pc) / 2: BF16x3 (y = t1 + t2 + t3 exactly, 8 bits each; the three
+// products whose term indices sum to 5 or 6) below 2^-23 in all, so at most
+// 2^-23 (Pq + Pc); BF16x2 (y = t1 + t2 + r, |t2| <= 2^-8 |y|, |r| <= 2^-16 |y|;
+// t2 t2', r (t1' + t2') and r' (t1 + t2) left out) at most 3.01 2^-16, so
+// 1.51 2^-16 (Pq + Pc).  The sum is doubled (for 2a) and doubled again for
+// safety.
+double tc_c1(int dp, int kernel) {
+    const int kp = tc_kp(dp, kernel);
+    const double norms = 2.0 * gamma_n(ldexp(1.0, -24), dp);
+    const double acc = 4.1 * kp * ldexp(1.0, -22);
+    const double split = kernel == SJ_KERNEL_FILTER_BF16X2 ? 6.1 * ldexp(1.0, -16) : 2.0 * ldexp(1.0, -22);
+    return norms + acc + split;
 }
 
 int build_index(Index* ix, const double* pts) {
@@ -913,18 +942,12 @@ int build_index(Index* ix, const double* pts) {
     const double pbound = pb * (1.0 + ldexp(1.0, -20));
     hp.d = d;
     hp.dp = ix->dp;
-    const bool tensor = ix->kernel == SJ_KERNEL_FILTER_BF16X3;
+    const bool tensor = is_tensor_kernel(ix->kernel);
     const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32 || tensor;
     const double u_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
     const double delta = 1.01 * u_t * rmax;
-    // tensor-core filter: |s_y - (pc - 2a)| <= gamma_32(dp) (Pq + Pc) for the
-    // FP32 norms plus twice the dot-product error, which is at most
-    // (1.02 K 2^-22 + 2^-23) (Pq + Pc): the split products dropped (three per
-    // dim, below 2^-23 relative together) and an FP32 accumulation of K terms
-    // whose every addition is taken to lose up to 2^-22 relative (truncation).
-    // Doubled for safety.
-    double c1 = -1.0;
-    if (tensor) c1 = 2.0 * gamma_n(ldexp(1.0, -24), ix->dp) + (4.1 * tc_kp(ix->dp) + 2.0) * ldexp(1.0, -22);
+    double c1 = -1.0;  // (the tensor-core filter's bound: tc_c1)
+    if (tensor) c1 = tc_c1(ix->dp, ix->kernel);
     pack_coefficients(ix->eps, pbound, delta, u_t, d, ix->dp, &hp, c1);
     if (use_f32)
         SJ_TRY(pack_points<float>(ix, pts, hp));
@@ -956,7 +979,7 @@ int build_index(Index* ix, const double* pts) {
         ep.stride[i] = ix->stride[i];
     }
     ep.symmetric = ix->opt.symmetric ? 1 : 0;
-    const int qcap = ix->kernel == SJ_KERNEL_FILTER_BF16X3 ? tc_qmax(tc_kp(ix->dp)) : kQMax;
+    const int qcap = is_tensor_kernel(ix->kernel) ? tc_qmax(tc_kp(ix->dp, ix->kernel)) : kQMax;
     ep.qmax = ix->opt.queries_per_item > 0 ? std::min(ix->opt.queries_per_item, qcap) : qcap;
     const int64_t Mc = (int64_t)M;
     // dense key -> cell table when the key space is small (neighbour lookups
@@ -1342,11 +1365,11 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     std::vector<double> centre((size_t)K * dp, 0.0);
     std::vector<double> e2((size_t)K);
     int shift = 0;
-    const bool tensor = ix->kernel == SJ_KERNEL_FILTER_BF16X3;
+    const bool tensor = is_tensor_kernel(ix->kernel);
     const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32 || tensor;
     const double u_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
     // the tensor-core filter's widened bound (as for a single join)
-    const double c1 = tensor ? 2.0 * gamma_n(ldexp(1.0, -24), dp) + (4.1 * tc_kp(dp) + 2.0) * ldexp(1.0, -22) : -1.0;
+    const double c1 = tensor ? tc_c1(dp, ix->kernel) : -1.0;
     for (int k = 0; k < K; ++k) {
         const unsigned long long* e = hext.data() + (size_t)k * (2 * dp + 1);
         if (e[2 * dp] != 0) {
@@ -1447,7 +1470,7 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     // subtracts the instance's first position to get instance-local indices
     // ---- runs and items (one read-back) ----
     const int64_t M = ix->n_cells;
-    BEnum be{shift, ix->opt.symmetric ? 1 : 0, tensor ? tc_qmax(tc_kp(dp)) : kQMax};
+    BEnum be{shift, ix->opt.symmetric ? 1 : 0, tensor ? tc_qmax(tc_kp(dp, ix->kernel)) : kQMax};
     uint32_t* cnt = nullptr;
     SJ_TRY(dev_alloc_t(&cnt, (size_t)M * 4, s));
     uint32_t *run_cnt = cnt, *item_cnt = cnt + M, *run_off = cnt + 2 * M, *item_off = cnt + 3 * M;

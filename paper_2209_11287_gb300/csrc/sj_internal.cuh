@@ -162,9 +162,10 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
 // joins on the CUDA-core and tensor-core filter kernels): a work item's
 // self-cell candidates start at its own first query and pairs below the
 // diagonal are skipped.
+inline bool is_tensor_kernel(int k) { return k == SJ_KERNEL_FILTER_BF16X3 || k == SJ_KERNEL_FILTER_BF16X2; }
 inline bool uses_triangle(const Index* ix) {
-    return ix->opt.symmetric && (ix->kernel == SJ_KERNEL_FILTER_F32 || ix->kernel == SJ_KERNEL_FP64_FMA ||
-                                 ix->kernel == SJ_KERNEL_FILTER_BF16X3);
+    return ix->opt.symmetric &&
+           (ix->kernel == SJ_KERNEL_FILTER_F32 || ix->kernel == SJ_KERNEL_FP64_FMA || is_tensor_kernel(ix->kernel));
 }
 
 // ---- index build (sj_index.cu) ------------------------------------------------
@@ -181,11 +182,17 @@ struct JoinOut {
 };
 int launch_join_cc(Index* ix, const JoinOut& out, int emit_dist);
 int launch_join_tc(Index* ix, const JoinOut& out, int emit_dist);
+int selftest_bounded_wait(cudaStream_t s);
 int launch_recheck(Index* ix, const JoinOut& out, int emit_dist);
 
-// Padded K of the tensor-core filter for padded dimension dp: 6 products per
-// dim plus 3 slots for the query term, rounded up to the MMA K of 16.
-constexpr int tc_kp(int dp) { return (6 * dp + 3 + 15) / 16 * 16; }
+// Split products per dim of a tensor-core filter: BF16x3 keeps 6, BF16x2 3.
+constexpr int tc_products(int kernel) { return kernel == SJ_KERNEL_FILTER_BF16X2 ? 3 : 6; }
+// Padded K of the tensor-core filter for padded dimension dp: the products
+// per dim plus 3 slots for the query term, rounded up to the MMA K of 16.
+constexpr int tc_kp(int dp, int kernel) { return (tc_products(kernel) * dp + 3 + 15) / 16 * 16; }
+// Relative coefficient c1 of the tensor-core filter's certified bound
+// E = c1 (P + pc) (sj_index.cu).
+double tc_c1(int dp, int kernel);
 // Queries per work item of the tensor-core filter: the MMA N (the query tile,
 // a whole number of 8-row groups from an 8-aligned start) is at most 256
 // (128 when K > 208, for shared memory), so an item holds one group less.

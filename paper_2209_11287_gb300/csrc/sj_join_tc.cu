@@ -2,10 +2,11 @@
 // (tcgen05.mma kind::f16, bf16 operands, FP32 accumulation in TMEM).
 //
 // The dot products of Eq. 3 (the tensor-core part of Eq. 4) are formed from a
-// 3-term bf16 split of every FP32 kernel coordinate, y = y1 + y2 + y3 exactly
-// (8 significant bits each), keeping the six products whose term indices sum
-// to at most 4: for dim k the candidate row holds (c1, c2, c1, c3, c2, c1)
-// and the query row (q1, q1, q2, q1, q2, q3).  Three more K slots carry the
+// bf16 split of every FP32 kernel coordinate, y = y1 + y2 + y3 exactly (8
+// significant bits each).  BF16x3 keeps the six products whose term indices
+// sum to at most 4: for dim k the candidate row holds (c1, c2, c1, c3, c2, c1)
+// and the query row (q1, q1, q2, q1, q2, q3); BF16x2 keeps three, (c1, c2, c1)
+// against (q1, q1, q2), for half the K.  Three more K slots carry the
 // query's -||y_q||^2 / 2, split the same way, against ones, so the
 // accumulator ends as a = -||y_q||^2/2 + y_q . y_c, the quantity every other
 // kernel computes.  Each value is compared with per-candidate thresholds
@@ -22,9 +23,10 @@
 //   warp 1      MMA issuer (one thread): K/16 MMAs per tile into one of two
 //               TMEM accumulators (128 lanes x N columns), committed to the
 //               stage and accumulator barriers;
-//   warps 2-9   epilogue: each thread owns one candidate row (its TMEM lane)
-//               and half of its N accumulators (two warps per lane quarter,
-//               alternate 32-column chunks), compares them with the
+//   warps 2..   epilogue (8 to 16 warps): each thread owns one candidate row
+//               (its TMEM lane) and a share of its N accumulators (2 to 4
+//               warps per lane quarter, interleaved 32-column chunks),
+//               compares them with the
 //               candidate's two thresholds (a max over 32 columns first; hits
 //               are rare), then runs the warp-aggregated emission of the
 //               CUDA-core kernels.
@@ -43,8 +45,11 @@ constexpr int kTcM = 128;             // candidate rows per tile (TMEM lanes)
 constexpr int kTcG = kTcM / 8;        // 8-row groups per tile
 constexpr int kKS = 64;               // K per pipeline slice
 constexpr int kMetaDepth = 4;         // tiles of row metadata in flight
-constexpr int kTcEpi = 8;             // epilogue warps: two per TMEM lane quarter, splitting the columns
-constexpr int kTcThreads = 64 + 32 * kTcEpi;  // producer, MMA, epilogue warps
+// Epilogue warps: EPI / 4 per TMEM lane quarter, splitting the columns; as
+// many as shared memory allows next to the query tile (the epilogue's
+// latency is what bounds the tile rate when hits are frequent).
+constexpr int tc_epi(int kp, bool emit) { return kp <= 112 ? 16 : (emit ? 8 : 12); }
+constexpr int tc_threads(int kp, bool emit) { return 64 + 32 * tc_epi(kp, emit); }  // producer, MMA, epilogue
 constexpr long long kTcSpin = 1 << 22;  // bound on barrier polls per wait
 
 struct TcParams {
@@ -82,8 +87,10 @@ struct TcMeta {
 
 template <int KP, bool EMIT>
 struct TcSmem {
-    static constexpr int STAGES = (KP > 208 || EMIT) ? 4 : 5;
-    uint64_t a_full[STAGES], a_empty[STAGES];
+    static constexpr int EPI = tc_epi(KP, EMIT);
+    static_assert(EPI % 4 == 0, "epilogue warps come in whole warpgroups");
+    static constexpr int MAX_STAGES = 6;
+    uint64_t a_full[MAX_STAGES], a_empty[MAX_STAGES];
     uint64_t b_full, b_empty;
     uint64_t item_full[2], item_empty[2];
     uint64_t meta_full[kMetaDepth], meta_empty[kMetaDepth];
@@ -97,15 +104,24 @@ struct TcSmem {
     int32_t rgp[kMaxRuns];  // producer: per run of the item, its first group's number in the item
     int32_t rlo[kMaxRuns], rhi[kMaxRuns];
     uint8_t rfl[kMaxRuns];
-    int2 stage[kTcEpi][kStage];
-    double sdist[kTcEpi][EMIT ? kStage : 1];
-    uint16_t hits[kTcEpi][32][32];  // per epilogue warp: maybe-in entries of a 32-column chunk, per lane
+    int2 stage[EPI][kStage];
+    double sdist[EPI][EMIT ? kStage : 1];
+    uint16_t hits[EPI][32][32];  // per epilogue warp: maybe-in entries of a 32-column chunk, per lane
 };
 
+// Operand stages: as many as fit (up to 6) in the 227 KB of shared memory a
+// CTA may use next to the query tile and the rest.
+constexpr size_t kSmemMax = 232448;
+template <int KP, bool EMIT>
+__host__ __device__ constexpr int tc_stages() {
+    const long long left = (long long)kSmemMax - 1024 - TcShape<KP>::B_BYTES - (long long)sizeof(TcSmem<KP, EMIT>);
+    const long long st = left / TcShape<KP>::A_STAGE;
+    return st > TcSmem<KP, EMIT>::MAX_STAGES ? TcSmem<KP, EMIT>::MAX_STAGES : (int)st;
+}
 template <int KP, bool EMIT>
 constexpr size_t tc_smem_bytes() {
     return 1024 /* alignment slack */ + (size_t)TcShape<KP>::B_BYTES +
-           (size_t)TcSmem<KP, EMIT>::STAGES * TcShape<KP>::A_STAGE + sizeof(TcSmem<KP, EMIT>);
+           (size_t)tc_stages<KP, EMIT>() * TcShape<KP>::A_STAGE + sizeof(TcSmem<KP, EMIT>);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -146,14 +162,17 @@ __device__ __forceinline__ bool bar_test(uint64_t* b, uint32_t parity) {
     return done != 0;
 }
 // Waits for the phase of the given parity; false when the CTA aborts or the
-// bound expires (which raises the abort).
-__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
-    for (long long i = 0; i < kTcSpin; ++i) {
+// bound (polls) expires, which raises the abort.
+__device__ __forceinline__ bool bar_wait_n(uint64_t* b, uint32_t parity, volatile int* abort, long long polls) {
+    for (long long i = 0; i < polls; ++i) {
         if (bar_test(b, parity)) return true;
         if (*abort) return false;
     }
     *abort = 1;
     return false;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+    return bar_wait_n(b, parity, abort, kTcSpin);
 }
 // Bulk copy global -> shared completing on an mbarrier.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -165,6 +184,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
+}
+
+// 16 consecutive TMEM columns of this thread's lane (no wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+// Three-input maximum (one instruction on this architecture).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 // 32 consecutive TMEM columns of this thread's lane (no wait).
@@ -181,10 +217,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
 }
 
 template <int KP, bool EMIT>
-__global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParams T) {
+__global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams P, TcParams T) {
     using SH = TcShape<KP>;
     using SM = TcSmem<KP, EMIT>;
-    constexpr int STAGES = SM::STAGES;
+    constexpr int STAGES = tc_stages<KP, EMIT>();
+    static_assert(STAGES >= 2, "at least two operand stages");
     constexpr int NMAX = SH::NMAX;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char* dsm = reinterpret_cast<unsigned char*>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
@@ -203,13 +240,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
         bar_init(&S.b_empty, 1);
         for (int i = 0; i < 2; ++i) {
             bar_init(&S.item_full[i], 1);
-            bar_init(&S.item_empty[i], 1 + kTcEpi);  // the MMA thread and the epilogue warps
+            bar_init(&S.item_empty[i], 1 + SM::EPI);  // the MMA thread and the epilogue warps
             bar_init(&S.acc_full[i], 1);
-            bar_init(&S.acc_empty[i], kTcEpi);
+            bar_init(&S.acc_empty[i], SM::EPI);
         }
         for (int i = 0; i < kMetaDepth; ++i) {
             bar_init(&S.meta_full[i], 1);
-            bar_init(&S.meta_empty[i], kTcEpi);
+            bar_init(&S.meta_empty[i], SM::EPI);
         }
         bar_init(&S.drain, 1);
         S.abort = 0;
@@ -449,7 +486,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
         // ------------------------------------------------------------ epilogue
         const int ew = warp - 2;       // stage slot
         const int quarter = warp & 3;  // TMEM lanes 32 quarter .. + 31
-        const int half = ew >> 2;      // 32-column chunks half, half + 2, ...
+        const int part = ew >> 2;      // 32-column chunks part, part + EPI / 4, ...
         const int row = quarter * 32 + lane;
         const float* __restrict__ TO = static_cast<const float*>(P.thr_out);
         const float* __restrict__ TI = static_cast<const float*>(P.thr_in);
@@ -505,20 +542,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
                 // emitted afterwards a warp-wide round at a time
                 uint16_t(*hits)[32] = S.hits[ew];
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + acc * NMAX;
-                for (int c0 = 32 * half; c0 < X.ncol; c0 += 64) {
-                    // columns past N are stale and masked
+                for (int c0 = 32 * part; c0 < X.ncol; c0 += 32 * (SM::EPI / 4)) {
+                    // only the N accumulated columns are read (a 16-column tail
+                    // leaves the upper half at -inf)
                     uint32_t v[32];
-                    tmem_ld32(taddr + (uint32_t)c0, v);
+                    if (X.ncol - c0 == 16) {
+                        tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+                        for (int k = 16; k < 32; ++k) v[k] = 0xFF800000u;
+                    } else {
+                        tmem_ld32(taddr + (uint32_t)c0, v);
+                    }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    // maxima of 8-column groups, then of all 32
+                    // maxima of 8-column groups, then of all 32 (three-input max)
                     float m8[4];
 #pragma unroll
                     for (int g8 = 0; g8 < 4; ++g8) {
                         const float* f = reinterpret_cast<const float*>(v + 8 * g8);
-                        m8[g8] = fmaxf(fmaxf(fmaxf(f[0], f[1]), fmaxf(f[2], f[3])),
-                                       fmaxf(fmaxf(f[4], f[5]), fmaxf(f[6], f[7])));
+                        m8[g8] = max3f(max3f(f[0], f[1], f[2]), max3f(f[3], f[4], f[5]), fmaxf(f[6], f[7]));
                     }
-                    const float mall = fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3]));
+                    const float mall = max3f(m8[0], m8[1], fmaxf(m8[2], m8[3]));
                     if (!__any_sync(0xffffffffu, cvalid && mall >= cto)) continue;
                     int hn = 0;
 #pragma unroll
@@ -592,17 +635,56 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_join_tc(JoinParams P, TcParam
     }
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier that
+// nothing arrives on; the wait must give up after its bound and raise the
+// abort flag.  out[0] = 1 when the wait gave up, out[1] = the abort flag.
+__global__ void k_wait_selftest(int* out, long long polls) {
+    __shared__ uint64_t bar;
+    __shared__ int abort;
+    if (threadIdx.x == 0) {
+        bar_init(&bar, 1);
+        abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool done = bar_wait_n(&bar, 0, &abort, polls);
+        out[0] = done ? 0 : 1;
+        out[1] = abort;
+    }
+}
+
+int selftest_bounded_wait(cudaStream_t s) {
+    int* d = nullptr;
+    SJ_TRY(dev_alloc_t(&d, 2, s));
+    SJ_CK(cudaMemsetAsync(d, 0, 2 * sizeof(int), s));
+    k_wait_selftest<<<1, 32, 0, s>>>(d, 1 << 16);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    int h[2] = {0, 0};
+    SJ_CK(cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, s));
+    SJ_CK(cudaStreamSynchronize(s));
+    dev_free(d, s);
+    if (h[0] == 1 && h[1] == 1) {
+        set_error("the bounded wait gave up as designed");
+        return SJ_ERR_TIMEOUT;
+    }
+    set_error("the bounded wait did not give up (%d, %d)", h[0], h[1]);
+    return SJ_ERR_CUDA;
+}
+
 template <int KP, bool EMIT>
 static int launch_kp(Index* ix, const JoinParams& p, const TcParams& t) {
     auto kern = k_join_tc<KP, EMIT>;
     const size_t smem = tc_smem_bytes<KP, EMIT>();
-    if (smem > 232448) {
+    if (smem > kSmemMax) {
         set_error("tensor-core tile does not fit in shared memory (K = %d)", KP);
         return SJ_ERR_UNSUPPORTED;
     }
     SJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem));
+    constexpr int threads = tc_threads(KP, EMIT);
+    SJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) {
         set_error("tensor-core tile does not fit on an SM (K = %d)", KP);
         return SJ_ERR_UNSUPPORTED;
@@ -610,7 +692,7 @@ static int launch_kp(Index* ix, const JoinParams& p, const TcParams& t) {
     // one CTA per SM: it holds up to all 512 TMEM columns
     long long blocks = (long long)device_sm_count(ix->device);
     if (blocks > ix->n_items) blocks = ix->n_items > 0 ? ix->n_items : 1;
-    kern<<<(unsigned)blocks, kTcThreads, smem, ix->stream>>>(p, t);
+    kern<<<(unsigned)blocks, threads, smem, ix->stream>>>(p, t);
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;

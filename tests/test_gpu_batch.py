@@ -77,7 +77,7 @@ def _check(pts, eps, out, with_dist):
             assert np.array_equal(dists[order], rd), f"instance {k}: distances differ"
 
 
-@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3", "auto"])
+@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3", "filter_bf16x2", "auto"])
 @pytest.mark.parametrize("symmetric", [1, 0])
 def test_mixed_batch(kernel, symmetric):
     pts, eps = _mixed_batch()
@@ -93,7 +93,7 @@ def test_mixed_batch_indexed_dims(indexed_dims):
     _check(pts, eps, out, with_dist=False)
 
 
-@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3"])
+@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3", "filter_bf16x2"])
 def test_mixed_batch_distances_host_input(kernel):
     pts, eps = _mixed_batch(seed=1)
     out = binding.join_batch(pts, eps, kernel=kernel, emit_distances=True)

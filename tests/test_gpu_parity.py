@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-KERNELS = ["fp64_fma", "fp64_dmma", "filter_f32", "filter_bf16x3"]
+KERNELS = ["fp64_fma", "fp64_dmma", "filter_f32", "filter_bf16x3", "filter_bf16x2"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -253,3 +253,14 @@ def test_uniform4d_full_size_sampled_rows(kernel):
     selfc = int((pairs[:, 0] == pairs[:, 1]).sum())
     assert selfc == w.n
     assert count > 1.0e8
+
+
+def test_bounded_wait_gives_up():
+    """A kernel waiting on an mbarrier that nothing arrives on gives up after
+    its bound and reports it; the context stays usable for the next join."""
+    st = binding.sj_selftest_bounded_wait()
+    assert st == binding.SJ_ERR_TIMEOUT, (st, binding.sj_last_error_message())
+    w = workloads.uniform2d(n=3000, seed=9)
+    ref = oracle.join(w.points, w.eps)
+    got, _, _ = gpu_join(w.points, w.eps, "filter_bf16x3")
+    assert_same_set(w.points, w.eps, ref, got)
