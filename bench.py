@@ -509,31 +509,28 @@ def run_batched(args):
     dims = [w.d for w in insts]
     knames = {v: k for k, v in binding.KERNELS.items()}
 
+    dp_of = np.array([1 << max(1, (dd - 1).bit_length()) for dd in dims])
+    dims_np = np.array(dims, dtype=np.float64)
+    prepared = binding.BatchInputs(pts, eps)  # pointer arrays marshalled once
+
     def one_step(opt, inputs, host_out=None):
-        res = binding.sj_join_batch(inputs, eps, opt, stream)
-        cnt = cand = evald = reruns = maxc = 0
-        groups = {}  # padded dim -> tile time, kernel, evaluated pairs and 2 d per pair
-        for k, r in enumerate(res):
-            if host_out is not None:
+        res = binding.sj_join_batch_raw(inputs, opt, stream)
+        if host_out is not None:
+            for r in res:
                 binding.sj_result_copy(r, host_out[: int(r.count)])
-            cnt += int(r.count)
-            cand += int(r.n_candidates)
-            evald += int(r.n_evaluated)
-            maxc = max(maxc, int(r.count))
-            reruns = max(reruns, int(r.reruns))
-            dp = 2
-            while dp < dims[k]:
-                dp *= 2
-            g = groups.setdefault(dp, {"ms": float(r.ms_tile), "kernel": knames.get(int(r.kernel), "?"),
-                                       "evaluated": 0, "flops_2d": 0.0, "instances": 0, "points": 0})
-            g["evaluated"] += int(r.n_evaluated)
-            g["flops_2d"] += 2.0 * dims[k] * int(r.n_evaluated)
-            g["instances"] += 1
-            g["points"] += len(inputs[k])
-        for r in res:
-            binding.sj_result_free(r)
-        tile = sum(g["ms"] for g in groups.values())
-        return cnt, cand, evald, reruns, tile, groups, maxc
+        t = binding.results_table(res)
+        groups = {}  # padded dim -> tile time, kernel, evaluated pairs and 2 d per pair
+        for dp in np.unique(dp_of):
+            sel = dp_of == dp
+            first = int(np.argmax(sel))
+            ev = t["n_evaluated"][sel]
+            groups[int(dp)] = {"ms": float(t["ms_tile"][first]), "kernel": knames.get(int(t["kernel"][first]), "?"),
+                               "evaluated": int(ev.sum()), "flops_2d": float((2.0 * dims_np[sel] * ev).sum()),
+                               "instances": int(sel.sum()), "points": int(sum(len(pts[i]) for i in np.nonzero(sel)[0]))}
+        out = (int(t["count"].sum()), int(t["n_candidates"].sum()), int(t["n_evaluated"].sum()),
+               int(t["reruns"].max()), sum(g["ms"] for g in groups.values()), groups, int(t["count"].max()))
+        binding.sj_results_free(res)
+        return out
 
     allowed = ("auto", "filter_f32", "filter_bf16x3", "filter_bf16x2", "fp64_fma")
     asked = args.variants.split(",") if args.variants != ",".join(VARIANTS) else ["auto", "filter_f32", "fp64_fma"]
@@ -543,7 +540,7 @@ def run_batched(args):
     for vi, kname in enumerate(variants):
         opt = binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint)
         for _ in range(args.warmup):
-            one_step(opt, pts)
+            one_step(opt, prepared)
         sync_all()
         if vi == 0:
             sampler.start()
@@ -553,7 +550,7 @@ def run_batched(args):
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            info = one_step(opt, pts)
+            info = one_step(opt, prepared)
             ev[k][1].record(stream)
             tiles.append(info[4])
         sync_all()
@@ -565,7 +562,7 @@ def run_batched(args):
                           "groups": info[5], "max_count": info[6], "launches": launches, "clocks": clocks}
     head = results[variants[0]]
     # end to end: host inputs (pinned), every instance's pairs copied back to pinned host memory
-    host_pts = [torch.from_numpy(w.points).pin_memory() for w in insts]
+    host_pts = binding.BatchInputs([torch.from_numpy(w.points).pin_memory() for w in insts], eps)
     host_out = torch.empty((head["max_count"] + 16, 2), dtype=torch.int32).pin_memory()
     opt = binding.sj_default_options(kernel=variants[0], max_pairs_hint=args.hint)
     t_e2e = []

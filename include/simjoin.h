@@ -179,6 +179,9 @@ SJ_API int sj_result_copy(const sj_result* r, int32_t* pairs_out, double* dist_o
 /* Releases a result's pages (NULL-safe, idempotent). */
 SJ_API void sj_result_free(sj_result* r);
 
+/* Releases `count` results in one call (e.g. the results of sj_join_batch). */
+SJ_API void sj_results_free(sj_result* results, int32_t count);
+
 /* Convenience: build + join + destroy in one call. */
 SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt, void* stream,
             sj_result* out);

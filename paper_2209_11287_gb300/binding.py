@@ -136,6 +136,8 @@ def load():
         lib.sj_kernel_launches.restype = ctypes.c_int64
         lib.sj_self_join_noalloc.argtypes = [_vp, _i64, _i32, ctypes.c_double, _vp, _i64, ctypes.POINTER(_i64), _vp]
         lib.sj_self_join_noalloc.restype = ctypes.c_int
+        lib.sj_results_free.argtypes = [ctypes.POINTER(sj_result), _i32]
+        lib.sj_results_free.restype = None
         lib.sj_selftest_bounded_wait.argtypes = [_vp]
         lib.sj_selftest_bounded_wait.restype = ctypes.c_int
         _lib = lib
@@ -269,21 +271,52 @@ def sj_join(points, eps: float, options: sj_options | None = None, stream=None) 
     return r
 
 
+class BatchInputs:
+    """The argument arrays of sj_join_batch (instance pointers, sizes,
+    dimensions, eps), marshalled once for joins repeated on the same inputs."""
+
+    def __init__(self, points_list, eps_list):
+        count = len(points_list)
+        if len(eps_list) != count:
+            raise ValueError("one eps per instance")
+        self.count = count
+        self.ptrs = (_vp * count)()
+        self.ns = (_i64 * count)()
+        self.ds = (_i32 * count)()
+        self.es = (ctypes.c_double * count)()
+        self._keep = []
+        for k, (p, e) in enumerate(zip(points_list, eps_list)):
+            ptr, n, d, kp = _points_ptr(p)
+            self._keep.append(kp)
+            self.ptrs[k], self.ns[k], self.ds[k], self.es[k] = ptr, n, d, float(e)
+
+
+def sj_join_batch_raw(inputs: BatchInputs, options: sj_options | None = None, stream=None):
+    """sj_join_batch on prepared inputs; returns the ctypes array of results
+    (release with sj_results_free)."""
+    res = (sj_result * inputs.count)()
+    _check(load().sj_join_batch(inputs.ptrs, inputs.ns, inputs.ds, inputs.es, inputs.count,
+                                ctypes.byref(options) if options is not None else None, _stream_ptr(stream), res))
+    return res
+
+
+def sj_results_free(results) -> None:
+    load().sj_results_free(results, len(results))
+
+
+def results_table(results) -> np.ndarray:
+    """The scalar fields of an array of sj_result (count, n_candidates,
+    n_evaluated, n_rechecked, reruns, kernel, ms_tile) as a numpy record view."""
+    names = ["count", "n_candidates", "n_evaluated", "n_rechecked", "reruns", "kernel", "ms_tile"]
+    fmts = {"count": "<i8", "n_candidates": "<i8", "n_evaluated": "<i8", "n_rechecked": "<i8", "reruns": "<i4",
+            "kernel": "<i4", "ms_tile": "<f8"}
+    dt = np.dtype({"names": names, "formats": [fmts[n] for n in names],
+                   "offsets": [getattr(sj_result, n).offset for n in names], "itemsize": ctypes.sizeof(sj_result)})
+    return np.frombuffer(results, dtype=dt)
+
+
 def sj_join_batch(points_list, eps_list, options: sj_options | None = None, stream=None) -> list:
-    count = len(points_list)
-    ptrs = (_vp * count)()
-    ns = (_i64 * count)()
-    ds = (_i32 * count)()
-    es = (ctypes.c_double * count)()
-    keep = []
-    for k, (p, e) in enumerate(zip(points_list, eps_list)):
-        ptr, n, d, kp = _points_ptr(p)
-        keep.append(kp)
-        ptrs[k], ns[k], ds[k], es[k] = ptr, n, d, float(e)
-    res = (sj_result * count)()
-    _check(load().sj_join_batch(ptrs, ns, ds, es, count, ctypes.byref(options) if options is not None else None,
-                                _stream_ptr(stream), res))
-    return list(res)
+    return list(sj_join_batch_raw(BatchInputs(points_list, eps_list), options, stream))
 
 
 def sj_self_join_noalloc(points, eps: float, pairs_out, stream=None) -> int:

@@ -466,6 +466,11 @@ void sj_result_free(sj_result* r) {
     memset(r, 0, sizeof *r);
 }
 
+void sj_results_free(sj_result* results, int32_t count) {
+    if (!results) return;
+    for (int32_t k = 0; k < count; ++k) sj_result_free(&results[k]);
+}
+
 int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt, void* stream,
             sj_result* out) {
     sj_handle h = nullptr;

@@ -1107,56 +1107,86 @@ __device__ __forceinline__ int inst_of_position(const long long* __restrict__ of
     return lo;
 }
 
-// Copies the instances' points (device pointers) into one row-major array of
-// padded rows, zero beyond each instance's d, and records each point's instance.
-__global__ void k_bgather(const double* const* __restrict__ src, const int32_t* __restrict__ d_of,
-                          const long long* __restrict__ off, int n_inst, int64_t n, int dp, double* X,
-                          int32_t* inst_of) {
+// Instance of every point of the group (points are numbered instance by
+// instance).
+__global__ void k_binst(const long long* __restrict__ off, int n_inst, int64_t n, int32_t* inst_of) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int k = inst_of_position(off, n_inst, p);
-    const int d = d_of[k];
-    const double* row = src[k] + (p - off[k]) * d;
-    for (int c = 0; c < dp; ++c) X[p * dp + c] = c < d ? row[c] : 0.0;
-    inst_of[p] = k;
+    inst_of[p] = inst_of_position(off, n_inst, p);
 }
 
-// One block per instance: per-dim min / max as order keys and a flag for a
-// non-finite coordinate; ext[k] holds 2 dp + 1 words.
-__global__ void k_bextent(const double* __restrict__ X, const long long* __restrict__ off, int dp,
-                          unsigned long long* ext) {
+// Coordinate c of point p (group numbering) of instance k, read in place from
+// the instance's own n_k x d_k array; zero in the padding dims.
+__device__ __forceinline__ double bcoord(const double* const* __restrict__ src, const int32_t* __restrict__ d_of,
+                                         const long long* __restrict__ off, int k, int64_t p, int c) {
+    const int d = d_of[k];
+    return c < d ? src[k][(p - off[k]) * d + c] : 0.0;
+}
+
+// Extents: block b covers points [blk_start[b], blk_start[b] + kBlkPts) of
+// instance blk_inst[b] (capped at its end); per-dim min / max as order keys
+// merged into ext[k] (2 d + 1 words: mins, maxes, non-finite flag) with
+// atomics, so the result does not depend on the order of the blocks.
+constexpr int kBlkPts = 2048;
+__global__ void k_bextent(const double* const* __restrict__ src, const int32_t* __restrict__ d_of,
+                          const long long* __restrict__ off, const int32_t* __restrict__ blk_inst,
+                          const long long* __restrict__ blk_start, int dp, unsigned long long* ext) {
     extern __shared__ unsigned long long s_ext[];  // [2 * dp + 1]
-    const int k = blockIdx.x;
+    const int k = blk_inst[blockIdx.x];
+    const int d = d_of[k];
     for (int c = threadIdx.x; c < dp; c += blockDim.x) {
         s_ext[c] = ~0ull;
         s_ext[dp + c] = 0ull;
     }
     if (threadIdx.x == 0) s_ext[2 * dp] = 0ull;
     __syncthreads();
-    const int64_t b = off[k] * dp, e = off[k + 1] * dp;
-    unsigned long long mn = ~0ull, mx = 0ull;
-    int bad = 0;
-    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {  // blockDim is a multiple of dp
-        const unsigned long long w = (unsigned long long)__double_as_longlong(X[i]);
-        if (((w >> 52) & 0x7FFull) == 0x7FFull) {
-            bad = 1;
-            continue;
+    const long long p0 = blk_start[blockIdx.x];
+    const long long p1 = p0 + kBlkPts < off[k + 1] ? p0 + kBlkPts : off[k + 1];
+    const double* base = src[k] + (p0 - off[k]) * d;
+    const long long m = (p1 - p0) * d;
+    // a stride that is a multiple of d keeps every thread on one dim
+    const int stride = (int)blockDim.x - (int)blockDim.x % d;
+    if ((int)threadIdx.x < stride) {
+        const int c = (int)threadIdx.x % d;
+        unsigned long long mn = ~0ull, mx = 0ull;
+        int bad = 0;
+        for (long long i = threadIdx.x; i < m; i += stride) {
+            const unsigned long long w = (unsigned long long)__double_as_longlong(base[i]);
+            if (((w >> 52) & 0x7FFull) == 0x7FFull) {
+                bad = 1;
+                continue;
+            }
+            const unsigned long long o = (w >> 63) ? ~w : (w | 0x8000000000000000ull);
+            mn = o < mn ? o : mn;
+            mx = o > mx ? o : mx;
         }
-        const unsigned long long o = (w >> 63) ? ~w : (w | 0x8000000000000000ull);
-        mn = o < mn ? o : mn;
-        mx = o > mx ? o : mx;
+        if (mn <= mx) {
+            atomicMin(&s_ext[c], mn);
+            atomicMax(&s_ext[dp + c], mx);
+        }
+        if (bad) atomicOr(&s_ext[2 * dp], 1ull);
     }
-    const int c = threadIdx.x % dp;
-    if (mn <= mx) {
-        atomicMin(&s_ext[c], mn);
-        atomicMax(&s_ext[dp + c], mx);
-    }
-    if (bad) atomicOr(&s_ext[2 * dp], 1ull);
     __syncthreads();
-    for (int c2 = threadIdx.x; c2 < 2 * dp + 1; c2 += blockDim.x) ext[(int64_t)k * (2 * dp + 1) + c2] = s_ext[c2];
+    unsigned long long* e = ext + (int64_t)k * (2 * dp + 1);
+    for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+        // padding dims hold zeros (key of +0)
+        const unsigned long long zero = 0x8000000000000000ull;
+        atomicMin(&e[c], c < d ? s_ext[c] : zero);
+        atomicMax(&e[dp + c], c < d ? s_ext[dp + c] : zero);
+    }
+    if (threadIdx.x == 0 && s_ext[2 * dp]) atomicOr(&e[2 * dp], 1ull);
 }
 
-__global__ void k_bkeys(const double* __restrict__ X, int64_t n, int dp, const int32_t* __restrict__ inst_of,
+__global__ void k_bextent_init(unsigned long long* ext, int n_inst, int dp) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t w = 2 * dp + 1;
+    if (i >= (int64_t)n_inst * w) return;
+    const int64_t c = i % w;
+    ext[i] = c < dp ? ~0ull : 0ull;
+}
+
+__global__ void k_bkeys(const double* const* __restrict__ src, const int32_t* __restrict__ d_of,
+                        const long long* __restrict__ off, int64_t n, const int32_t* __restrict__ inst_of,
                         const BInst* __restrict__ P, int shift, unsigned long long* keys, int32_t* ids) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -1164,7 +1194,7 @@ __global__ void k_bkeys(const double* __restrict__ X, int64_t n, int dp, const i
     const BInst& g = P[k];
     unsigned long long key = 0;
     for (int t = 0; t < g.m; ++t) {
-        const int64_t c = cell_coord(X[i * dp + g.dims[t]], g.lo[t], g.inv_w, g.ncell[t]);
+        const int64_t c = cell_coord(bcoord(src, d_of, off, k, i, g.dims[t]), g.lo[t], g.inv_w, g.ncell[t]);
         key += (unsigned long long)c * g.stride[t];
     }
     keys[i] = ((unsigned long long)k << shift) | key;
@@ -1172,7 +1202,8 @@ __global__ void k_bkeys(const double* __restrict__ X, int64_t n, int dp, const i
 }
 
 template <typename T>
-__global__ void k_bpack(const double* __restrict__ X, const int32_t* __restrict__ perm,
+__global__ void k_bpack(const double* const* __restrict__ srcp, const int32_t* __restrict__ d_of,
+                        const long long* __restrict__ off, const int32_t* __restrict__ perm,
                         const int32_t* __restrict__ inst_of, const BInst* __restrict__ P,
                         const double* __restrict__ centre, int64_t n, int dp, double* xs, T* y, T* h, T* thr_out,
                         T* thr_in, int32_t* inst_of_sorted) {
@@ -1183,7 +1214,7 @@ __global__ void k_bpack(const double* __restrict__ X, const int32_t* __restrict_
     const BInst& g = P[k];
     T nrm = T(0);
     for (int c = 0; c < dp; ++c) {
-        const double v = X[src * dp + c];
+        const double v = bcoord(srcp, d_of, off, k, src, c);
         xs[p * dp + c] = v;
         const T yc = T(v - centre[(int64_t)k * dp + c]);
         y[p * dp + c] = yc;
@@ -1331,30 +1362,47 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     // ---- per-instance offsets, dims, source pointers ----
     SJ_TRY(dev_alloc_t(&g->d_off, (size_t)K + 1, s));
     SJ_CK(cudaMemcpyAsync(g->d_off, g->off.data(), (K + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
-    double* X = nullptr;
-    SJ_TRY(dev_alloc_t(&X, (size_t)n * dp, s));
     int32_t* inst_of = nullptr;
     SJ_TRY(dev_alloc_t(&inst_of, (size_t)n, s));
-    {
-        const double** dsrc = nullptr;
-        int32_t* dd = nullptr;
-        SJ_TRY(dev_alloc_t(&dsrc, (size_t)K, s));
-        SJ_TRY(dev_alloc_t(&dd, (size_t)K, s));
-        SJ_CK(cudaMemcpyAsync(dsrc, src_dev_ptrs, K * sizeof(double*), cudaMemcpyHostToDevice, s));
-        SJ_CK(cudaMemcpyAsync(dd, d_of_host, K * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        k_bgather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, K, n, dp, X, inst_of);
-        note_launch();
-        SJ_CK(cudaGetLastError());
-        dev_free(dsrc, s);
-        dev_free(dd, s);
-    }
-    // ---- extents (one read-back) and per-instance grids ----
-    unsigned long long* ext = nullptr;
-    SJ_TRY(dev_alloc_t(&ext, (size_t)K * (2 * dp + 1), s));
-    const int eb = 256 - (256 % dp);
-    k_bextent<<<K, eb, (2 * dp + 1) * sizeof(unsigned long long), s>>>(X, g->d_off, dp, ext);
+    // the instances' arrays are read in place
+    const double** dsrc = nullptr;
+    int32_t* dd = nullptr;
+    SJ_TRY(dev_alloc_t(&dsrc, (size_t)K, s));
+    SJ_TRY(dev_alloc_t(&dd, (size_t)K, s));
+    SJ_CK(cudaMemcpyAsync(dsrc, src_dev_ptrs, K * sizeof(double*), cudaMemcpyHostToDevice, s));
+    SJ_CK(cudaMemcpyAsync(dd, d_of_host, K * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    k_binst<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->d_off, K, n, inst_of);
     note_launch();
     SJ_CK(cudaGetLastError());
+    // ---- extents (blocks of up to kBlkPts points; one read-back) and per-instance grids ----
+    std::vector<int32_t> hblk_inst;
+    std::vector<long long> hblk_start;
+    for (int k = 0; k < K; ++k)
+        for (long long p = g->off[k]; p < g->off[k + 1]; p += kBlkPts) {
+            hblk_inst.push_back(k);
+            hblk_start.push_back(p);
+        }
+    const int nblk = (int)hblk_inst.size();
+    int32_t* dblk_inst = nullptr;
+    long long* dblk_start = nullptr;
+    unsigned long long* ext = nullptr;
+    SJ_TRY(dev_alloc_t(&dblk_inst, (size_t)nblk, s));
+    SJ_TRY(dev_alloc_t(&dblk_start, (size_t)nblk, s));
+    SJ_TRY(dev_alloc_t(&ext, (size_t)K * (2 * dp + 1), s));
+    SJ_CK(cudaMemcpyAsync(dblk_inst, hblk_inst.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    SJ_CK(cudaMemcpyAsync(dblk_start, hblk_start.data(), nblk * sizeof(long long), cudaMemcpyHostToDevice, s));
+    {
+        const int64_t w = (int64_t)K * (2 * dp + 1);
+        k_bextent_init<<<(unsigned)((w + 255) / 256), 256, 0, s>>>(ext, K, dp);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+    }
+    k_bextent<<<nblk, 256, (2 * dp + 1) * sizeof(unsigned long long), s>>>(dsrc, dd, g->d_off, dblk_inst, dblk_start,
+                                                                         dp, ext);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    dev_free(dblk_inst, s);
+    dev_free(dblk_start, s);
     std::vector<unsigned long long> hext((size_t)K * (2 * dp + 1));
     SJ_CK(cudaMemcpyAsync(hext.data(), ext, hext.size() * 8, cudaMemcpyDeviceToHost, s));
     SJ_CK(cudaStreamSynchronize(s));
@@ -1435,7 +1483,7 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     unsigned long long* keys = nullptr;
     SJ_TRY(dev_alloc_t(&keys, (size_t)n, s));
     SJ_TRY(dev_alloc_t(&ix->perm, (size_t)n, s));
-    k_bkeys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, n, dp, inst_of, dP, shift, keys, ix->perm);
+    k_bkeys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, n, inst_of, dP, shift, keys, ix->perm);
     note_launch();
     SJ_CK(cudaGetLastError());
     SJ_TRY(radix_sort_pairs(reinterpret_cast<uint64_t*>(keys), ix->perm, n, shift + inst_bits, s));
@@ -1451,7 +1499,8 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
         SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
         SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
         ix->y = y, ix->h = h, ix->thr_out = to, ix->thr_in = ti;
-        k_bpack<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, ix->perm, inst_of, dP, dcentre, n, dp, ix->xs,
+        k_bpack<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, ix->perm, inst_of, dP, dcentre,
+                                                                   n, dp, ix->xs,
                                                                    y, h, to, ti, g->d_inst_of_sorted);
     } else {
         double *y, *h, *to, *ti;
@@ -1460,7 +1509,8 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
         SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
         SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
         ix->y = y, ix->h = h, ix->thr_out = to, ix->thr_in = ti;
-        k_bpack<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, ix->perm, inst_of, dP, dcentre, n, dp,
+        k_bpack<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, ix->perm, inst_of, dP, dcentre,
+                                                                    n, dp,
                                                                     ix->xs, y, h, to, ti, g->d_inst_of_sorted);
     }
     note_launch();
@@ -1519,7 +1569,8 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     dev_free(dtot, s);
     dev_free(dP, s);
     dev_free(dcentre, s);
-    dev_free(X, s);
+    dev_free(dsrc, s);
+    dev_free(dd, s);
     dev_free(inst_of, s);
     SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
     return SJ_OK;
