@@ -1443,6 +1443,7 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
         BInst& b = hp[k];
         memset(&b, 0, sizeof b);
         b.m = t.m;
+        ix->m = std::max(ix->m, t.m);  // the group's kernels size their run arrays by the largest m
         for (int i = 0; i < t.m; ++i) {
             b.dims[i] = t.dims[i];
             b.lo[i] = t.lo[t.dims[i]];

@@ -40,21 +40,22 @@ constexpr int cc_warps() {
     return sizeof(WS) * 4 <= 46 * 1024 ? 4 : sizeof(WS) * 2 <= 46 * 1024 ? 2 : 1;
 }
 
-template <typename T, int DP, int TC, bool EMIT>
+template <typename T, int DP, int TC, bool EMIT, int RUNS>
 struct CcWarpSmem {
-    ItemSmem<T, DP> it;
+    ItemSmem<T, DP, RUNS> it;
     int32_t cj[32 * TC];               // sorted position of each candidate slot
     int32_t cperm[32 * TC];            // its input index
     uint8_t cmir[32 * TC];             // its mirror flag
-    uint16_t list[32 * TC * kQMax];    // maybe-in entries: certain << 15 | slot << 4 | query
+    uint16_t list[32 * TC * (kQMax / 2)];  // maybe-in entries of one half of the queries:
+                                           // certain << 15 | slot << 4 | query
     int2 stage[kStage];
     double sdist[EMIT ? kStage : 1];
 };
 
 // Maybe-in bitmasks of TC candidates against all queries of the item, d <= 8:
 // the threshold test follows each query's fma chain.
-template <typename T, int DP, int TC>
-__device__ __forceinline__ void tile_fused(const ItemSmem<T, DP>& S, int Q, const T (&c)[TC][DP], const T (&to)[TC],
+template <typename T, int DP, int TC, int RUNS>
+__device__ __forceinline__ void tile_fused(const ItemSmem<T, DP, RUNS>& S, int Q, const T (&c)[TC][DP], const T (&to)[TC],
                                            const T (&ti)[TC], uint32_t (&bits)[TC], uint32_t (&cbits)[TC]) {
 #pragma unroll
     for (int t = 0; t < TC; ++t) bits[t] = cbits[t] = 0;
@@ -101,20 +102,20 @@ constexpr int cc_min_blocks() {
     return std::is_same<T, float>::value && DP <= 8 ? 8 : 1;
 }
 
-template <typename T, int DP, int TC, bool EMIT, int NW>
+template <typename T, int DP, int TC, bool EMIT, int NW, int RUNS>
 __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(JoinParams P) {
     constexpr bool FUSED = DP <= 8;
     constexpr int KC = DP < 8 ? DP : 8;  // dims per register chunk (unfused path)
     constexpr int SLOTS = 32 * TC;
     static_assert(SLOTS <= 2048, "slot index must fit in 11 bits");
-    __shared__ CcWarpSmem<T, DP, TC, EMIT> smem[NW];
+    __shared__ CcWarpSmem<T, DP, TC, EMIT, RUNS> smem[NW];
 
     const T* __restrict__ Y = static_cast<const T*>(P.y);
     const T* __restrict__ TO = static_cast<const T*>(P.thr_out);
     const T* __restrict__ TI = static_cast<const T*>(P.thr_in);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    CcWarpSmem<T, DP, TC, EMIT>& W = smem[wid];
-    ItemSmem<T, DP>& S = W.it;
+    CcWarpSmem<T, DP, TC, EMIT, RUNS>& W = smem[wid];
+    ItemSmem<T, DP, RUNS>& S = W.it;
     WarpStage st{W.stage, EMIT ? W.sdist : nullptr, 0, 0};
     unsigned long long rechecked = 0;
 
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                 for (int t = 0; t < TC; ++t)
 #pragma unroll
                     for (int k = 0; k < DP; ++k) c[t][k] = valid[t] ? Y[(int64_t)j[t] * DP + k] : T(0);
-                tile_fused<T, DP, TC>(S, Q, c, to, ti, bits, cbits);
+                tile_fused<T, DP, TC, RUNS>(S, Q, c, to, ti, bits, cbits);
             } else {
                 T acc[TC][kQMax];
 #pragma unroll
@@ -207,15 +208,19 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                 bits[t] &= tri_mask[t];
                 cbits[t] &= tri_mask[t];
             }
-            // compact the maybe-in pairs with one warp scan
+            // compact the maybe-in pairs with one warp scan per half of the queries
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+            const uint32_t hm = half ? 0xFF00u : 0x00FFu;
             int cnt = 0;
 #pragma unroll
-            for (int t = 0; t < TC; ++t) cnt += __popc(bits[t]);
+            for (int t = 0; t < TC; ++t) cnt += __popc(bits[t] & hm);
             int total;
             int off = warp_excl_scan(cnt, lane, &total);
+            if (total == 0) continue;
 #pragma unroll
             for (int t = 0; t < TC; ++t) {
-                uint32_t b = bits[t];
+                uint32_t b = bits[t] & hm;
                 while (b) {
                     const int q = __ffs(b) - 1;
                     b &= b - 1u;
@@ -264,6 +269,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                     stage_emit_pairs(st, P, lane, nout, qid, cid);
             }
             __syncwarp();
+            }
         }
         __syncwarp();
     }
@@ -320,11 +326,11 @@ __global__ void __launch_bounds__(128) k_recheck(JoinParams P) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && count) atomicAdd(&P.counters[2], count);
 }
 
-template <typename T, int DP, bool EMIT>
-static int launch_dpe(Index* ix, const JoinParams& p) {
+template <typename T, int DP, bool EMIT, int RUNS>
+static int launch_dper(Index* ix, const JoinParams& p) {
     constexpr int TC = DP <= 8 ? 4 : 2;
-    constexpr int NW = cc_warps<CcWarpSmem<T, DP, TC, EMIT>>();
-    auto kern = k_join_cc<T, DP, TC, EMIT, NW>;
+    constexpr int NW = cc_warps<CcWarpSmem<T, DP, TC, EMIT, RUNS>>();
+    auto kern = k_join_cc<T, DP, TC, EMIT, NW, RUNS>;
     int per_sm = 0;
     SJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, 0));
     if (per_sm < 1) per_sm = 1;
@@ -335,6 +341,14 @@ static int launch_dpe(Index* ix, const JoinParams& p) {
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
+}
+
+// Run capacity of the item image: 3^(m-1) + 1 runs for m indexed dims; a
+// grid of at most 4 dims needs 28, which keeps the per-warp shared memory
+// small enough for 8 CTAs per SM.
+template <typename T, int DP, bool EMIT>
+static int launch_dpe(Index* ix, const JoinParams& p) {
+    return ix->m <= 4 ? launch_dper<T, DP, EMIT, 28>(ix, p) : launch_dper<T, DP, EMIT, kMaxRuns>(ix, p);
 }
 
 template <typename T, int DP>

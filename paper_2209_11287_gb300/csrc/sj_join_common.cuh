@@ -271,21 +271,22 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total) {
     return x - v;
 }
 
-// Shared-memory image of one work item.
-template <typename T, int DP>
+// Shared-memory image of one work item (RUNS: run capacity, 3^(m-1) + 1 for
+// a grid of m indexed dims).
+template <typename T, int DP, int RUNS = kMaxRuns>
 struct ItemSmem {
     __align__(16) T qy[kQMax][DP];
     T qh[kQMax];
     int32_t qid[kQMax];
-    int32_t rstart[kMaxRuns];
-    uint32_t rpre[kMaxRuns + 1];  // prefix of run lengths
-    uint8_t rmir[kMaxRuns];
+    int32_t rstart[RUNS];
+    uint32_t rpre[RUNS + 1];  // prefix of run lengths
+    uint8_t rmir[RUNS];
 };
 
 // Loads item I into shared memory (all threads of the CTA); query rows past
 // Q are zero.  Returns the candidate count C after a barrier.
-template <typename T, int DP>
-__device__ __forceinline__ uint32_t load_item(ItemSmem<T, DP>& S, const JoinParams& P, const Item& I) {
+template <typename T, int DP, int RUNS>
+__device__ __forceinline__ uint32_t load_item(ItemSmem<T, DP, RUNS>& S, const JoinParams& P, const Item& I) {
     const T* __restrict__ Y = static_cast<const T*>(P.y);
     const T* __restrict__ H = static_cast<const T*>(P.h);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -326,11 +327,11 @@ __device__ __forceinline__ uint32_t load_item(ItemSmem<T, DP>& S, const JoinPara
 
 // Warp-level variant of load_item: the calling warp alone fills S (its own
 // copy) and the result is visible to the warp after the returned __syncwarp.
-template <typename T, int DP>
+template <typename T, int DP, int RUNS>
 // With P.tri the self-cell run (the one run without the mirror flag in a
 // symmetric join) starts at the item's first query and is flagged 2: its
 // pairs above the diagonal are emitted in both orders, those below skipped.
-__device__ __forceinline__ uint32_t load_item_warp(ItemSmem<T, DP>& S, const JoinParams& P, const Item& I,
+__device__ __forceinline__ uint32_t load_item_warp(ItemSmem<T, DP, RUNS>& S, const JoinParams& P, const Item& I,
                                                    int lane) {
     const T* __restrict__ Y = static_cast<const T*>(P.y);
     const T* __restrict__ H = static_cast<const T*>(P.h);
@@ -383,8 +384,8 @@ __device__ __forceinline__ int32_t map_candidate_tc(const int32_t* rstart, const
 }
 
 // Candidate v (0 <= v < C) of the item: its sorted position and mirror flag.
-template <typename T, int DP>
-__device__ __forceinline__ int32_t map_candidate(const ItemSmem<T, DP>& S, int nr, uint32_t v, bool& mirror) {
+template <typename T, int DP, int RUNS>
+__device__ __forceinline__ int32_t map_candidate(const ItemSmem<T, DP, RUNS>& S, int nr, uint32_t v, bool& mirror) {
     int lo = 0, hi = nr - 1;  // last r with rpre[r] <= v
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -398,8 +399,9 @@ __device__ __forceinline__ int32_t map_candidate(const ItemSmem<T, DP>& S, int n
 }
 
 // As map_candidate, with the run's flag (0 plain, 1 mirror, 2 self-cell triangle).
-template <typename T, int DP>
-__device__ __forceinline__ int32_t map_candidate_flag(const ItemSmem<T, DP>& S, int nr, uint32_t v, uint8_t& flag) {
+template <typename T, int DP, int RUNS>
+__device__ __forceinline__ int32_t map_candidate_flag(const ItemSmem<T, DP, RUNS>& S, int nr, uint32_t v,
+                                                      uint8_t& flag) {
     int lo = 0, hi = nr - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
