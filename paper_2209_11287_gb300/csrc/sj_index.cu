@@ -1226,6 +1226,40 @@ __global__ void k_bpack(const double* const* __restrict__ srcp, const int32_t* _
     inst_of_sorted[p] = k;
 }
 
+// As k_bpack with dp threads per point (dp <= 32, a power of two): the row
+// is read and written coalesced and the norm is summed by a shuffle tree over
+// the point's dp lanes (the norm bound holds for any order of the sum).
+template <typename T>
+__global__ void k_bpack_lanes(const double* const* __restrict__ srcp, const int32_t* __restrict__ d_of,
+                              const long long* __restrict__ off, const int32_t* __restrict__ perm,
+                              const int32_t* __restrict__ inst_of, const BInst* __restrict__ P,
+                              const double* __restrict__ centre, int64_t n, int dp, double* xs, T* y, T* h,
+                              T* thr_out, T* thr_in, int32_t* inst_of_sorted) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = t / dp;
+    const int c = (int)(t % dp);
+    const bool live = p < n;
+    int k = 0;
+    T sq = T(0);
+    if (live) {
+        const int64_t src = perm[p];
+        k = inst_of[src];
+        const double v = bcoord(srcp, d_of, off, k, src, c);
+        xs[p * dp + c] = v;
+        const T yc = T(v - centre[(int64_t)k * dp + c]);
+        y[p * dp + c] = yc;
+        sq = yc * yc;
+    }
+    for (int o = dp >> 1; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o, dp);
+    if (live && c == 0) {
+        const BInst& g = P[k];
+        h[p] = -sq * T(0.5);
+        thr_out[p] = thr_down(g.a_out, sq, g.b_out);
+        thr_in[p] = g.has_in ? thr_up(g.a_in, sq, g.b_in) : T(INFINITY);
+        inst_of_sorted[p] = k;
+    }
+}
+
 struct BEnum {
     int shift, symmetric, qmax;
 };
@@ -1500,9 +1534,13 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
         SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
         SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
         ix->y = y, ix->h = h, ix->thr_out = to, ix->thr_in = ti;
-        k_bpack<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, ix->perm, inst_of, dP, dcentre,
-                                                                   n, dp, ix->xs,
-                                                                   y, h, to, ti, g->d_inst_of_sorted);
+        if (dp <= 32)
+            k_bpack_lanes<float><<<(unsigned)((n * dp + 255) / 256), 256, 0, s>>>(
+                dsrc, dd, g->d_off, ix->perm, inst_of, dP, dcentre, n, dp, ix->xs, y, h, to, ti, g->d_inst_of_sorted);
+        else
+            k_bpack<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, ix->perm, inst_of, dP,
+                                                                       dcentre, n, dp, ix->xs, y, h, to, ti,
+                                                                       g->d_inst_of_sorted);
     } else {
         double *y, *h, *to, *ti;
         SJ_TRY(dev_alloc_t(&y, (size_t)n * dp, s));
@@ -1510,9 +1548,13 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
         SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
         SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
         ix->y = y, ix->h = h, ix->thr_out = to, ix->thr_in = ti;
-        k_bpack<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, ix->perm, inst_of, dP, dcentre,
-                                                                    n, dp,
-                                                                    ix->xs, y, h, to, ti, g->d_inst_of_sorted);
+        if (dp <= 32)
+            k_bpack_lanes<double><<<(unsigned)((n * dp + 255) / 256), 256, 0, s>>>(
+                dsrc, dd, g->d_off, ix->perm, inst_of, dP, dcentre, n, dp, ix->xs, y, h, to, ti, g->d_inst_of_sorted);
+        else
+            k_bpack<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, ix->perm, inst_of, dP,
+                                                                        dcentre, n, dp, ix->xs, y, h, to, ti,
+                                                                        g->d_inst_of_sorted);
     }
     note_launch();
     SJ_CK(cudaGetLastError());
