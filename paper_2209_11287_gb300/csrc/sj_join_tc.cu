@@ -529,6 +529,12 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                 const bool cvalid = valid;
                 const int cfl = fl;
                 const float cto = to, cti = ti;
+                // this row's valid query columns: the item's, and in a self-cell
+                // triangle those at or below the candidate (one unsigned compare)
+                const int col_lo = cq0;
+                const int col_hi = cfl == 2 ? min(cq1 - 1, cp - X.qa) : cq1 - 1;
+                const bool has_cols = col_hi >= col_lo;
+                const uint32_t col_span = has_cols ? (uint32_t)(col_hi - col_lo) : 0u;
                 if (!bar_wait(&S.acc_full[acc], acc_ph, abort)) {
                     fail = true;
                     break;
@@ -572,8 +578,7 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                         for (int k = 0; k < 8; ++k) {
                             const int col = c0 + 8 * g8 + k;
                             const float a = __uint_as_float(v[8 * g8 + k]);
-                            const bool ok =
-                                h && a >= cto && col >= cq0 && col < cq1 && (cfl != 2 || X.qa + col <= cp);
+                            const bool ok = h && has_cols && a >= cto && (uint32_t)(col - col_lo) <= col_span;
                             if (ok) hits[hn++][lane] = (uint16_t)((uint32_t)col | (a >= cti ? 256u : 0u));
                         }
                     }
