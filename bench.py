@@ -21,6 +21,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import threading
 import time
@@ -43,7 +44,8 @@ KERNEL_NAMES = {"filter_f32": "k_join_cc<float>", "fp64_fma": "k_join_cc<double>
                 "filter_bf16x3": "k_join_tc", "filter_bf16x2": "k_join_tc"}
 DTYPES = {"auto": "bf16x2|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64",
           "filter_bf16x2": "bf16x2+f64", "fp64_fma": "f64",
-          "fp64_dmma": "f64"}
+          "fp64_dmma": "f64", "tuned": "bf16x2|bf16x3|f32+f64", "tuned_graph": "bf16x2|bf16x3|f32+f64",
+          "auto_graph": "bf16x2|f32+f64"}
 
 
 def parse():
@@ -89,9 +91,9 @@ METRICS = {
                "low-prec filter",
 }
 DEFAULT_VARIANTS = {
-    "uniform4d": ["filter_f32", "fp64_fma", "fp64_dmma"],
+    "uniform4d": ["filter_f32", "tuned", "fp64_fma", "fp64_dmma"],
     "uniform2d": ["filter_f32", "fp64_fma", "fp64_dmma", "filter_bf16x2"],
-    "mixture16d": ["filter_bf16x2", "filter_bf16x3", "filter_f32", "fp64_fma"],
+    "mixture16d": ["filter_bf16x2", "tuned", "filter_bf16x3", "filter_f32", "fp64_fma"],
     "expo64d": ["filter_bf16x2", "filter_bf16x3", "filter_f32"],
 }
 
@@ -206,10 +208,25 @@ def run_native(args):
         if host_out is not None:
             binding.sj_result_copy(r, host_out)
         info = (int(r.count), int(r.n_candidates), int(r.n_evaluated), int(r.n_rechecked), int(r.reruns),
-                float(r.ms_tile))
+                float(r.ms_tile), int(r.kernel))
         binding.sj_result_free(r)
         binding.sj_destroy(h)
         return info
+
+    knames = {v: k for k, v in binding.KERNELS.items()}
+    tuned = {}
+
+    def make_opt(kname):
+        """Options of a variant: a kernel name, or "tuned" (the autotuner's
+        pick for this workload, tuned once before the variant's warm-up)."""
+        if kname != "tuned":
+            return binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint)
+        if not tuned:
+            t0 = time.perf_counter()
+            best, ms = binding.sj_autotune(pts, w.eps, binding.sj_default_options(max_pairs_hint=args.hint), stream,
+                                           reps=3)
+            tuned.update(opt=best, ms=ms, seconds=round(time.perf_counter() - t0, 1))
+        return tuned["opt"]
 
     results = {}
     sampler = ClockSampler(local)
@@ -217,7 +234,7 @@ def run_native(args):
     if args.variants == ",".join(VARIANTS):
         variants = DEFAULT_VARIANTS[args.workload]
     for vi, kname in enumerate(variants):
-        opt = binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint)
+        opt = make_opt(kname)
         for _ in range(args.warmup):
             one_step(opt)
         barrier()
@@ -238,8 +255,9 @@ def run_native(args):
         clocks = sampler.stop() if vi == len(variants) - 1 else None
         times = [a.elapsed_time(b) for a, b in ev]
         ms = max_over_ranks(sum(times) / len(times))
-        count, cand, evald, rech, reruns, _ = info
-        results[kname] = {"ms_per_step": ms, "count": count, "n_candidates": cand, "n_evaluated": evald,
+        count, cand, evald, rech, reruns, _, kused = info
+        results[kname] = {"kernel": knames.get(kused, kname), "ms_per_step": ms, "count": count,
+                          "n_candidates": cand, "n_evaluated": evald,
                           "n_rechecked": rech, "reruns": reruns, "launches": launches, "clocks": clocks,
                           "ms_min": min(times), "ms_max": max(times),
                           "tile_ms": max_over_ranks(statistics.mean(tile_ms))}
@@ -252,7 +270,7 @@ def run_native(args):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     host_pts = torch.from_numpy(w.points).pin_memory()
     host_out = torch.empty((head["count"] + 16, 2), dtype=torch.int32).pin_memory()
-    opt = binding.sj_default_options(kernel=variants[0], max_pairs_hint=args.hint)
+    opt = make_opt(variants[0])
     one_step(opt, host_pts, host_out)
     barrier()
     t_e2e = []
@@ -267,6 +285,11 @@ def run_native(args):
 
     if rank == 0:
         line = make_line(args, w, results, variants, world, kern_ms, e2e_s, head)
+        if tuned:
+            o = tuned["opt"]
+            line["autotune"] = {"kernel": knames.get(o.kernel, "?"), "queries_per_item": o.queries_per_item,
+                                "indexed_dims": o.indexed_dims, "tuned_ms": round(tuned["ms"], 4),
+                                "seconds": tuned["seconds"]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, head["n_candidates"], args.cpu_queries)
         print(json.dumps(line), flush=True)
@@ -358,16 +381,16 @@ def make_line(args, w, results, variants, world, kern_ms, e2e_s, head):
     kname = variants[0]
     cand = head["n_candidates"]
     value = world * cand / (head["ms_per_step"] * 1e-3)
-    roof = roofline(kname, w, head, kern_ms)
+    roof = roofline(head.get("kernel", kname), w, head, kern_ms)
     var = {}
     for k in variants:
         r = results[k]
-        rk = roofline(k, w, r, r["tile_ms"])
+        rk = roofline(r.get("kernel", k), w, r, r["tile_ms"])
         var[k] = {"ms_per_step": round(r["ms_per_step"], 4),
                   "candidate_pairs_per_s": world * r["n_candidates"] / (r["ms_per_step"] * 1e-3),
                   "result_pairs_per_s": world * r["count"] / (r["ms_per_step"] * 1e-3), "result_pairs": r["count"],
                   "evaluated_pairs": r["n_evaluated"], "rechecked_pairs": r["n_rechecked"], "reruns": r["reruns"],
-                  "tile_kernel_ms": round(r["tile_ms"], 4),
+                  "tile_kernel_ms": round(r["tile_ms"], 4), "kernel": r.get("kernel", k),
                   "tile_roofline": {key: rk[key] for key in ("bound", "achieved", "peak", "unit", "frac")}}
     e2e_val = world * cand / e2e_s
     line = {
@@ -532,13 +555,33 @@ def run_batched(args):
         binding.sj_results_free(res)
         return out
 
-    allowed = ("auto", "filter_f32", "filter_bf16x3", "filter_bf16x2", "fp64_fma")
-    asked = args.variants.split(",") if args.variants != ",".join(VARIANTS) else ["auto", "filter_f32", "fp64_fma"]
+    # variants: a kernel name; "tuned" = AUTO with the tuning cache the
+    # autotuner writes before the variant's warm-up (untimed); "*_graph" = the
+    # join phase as one CUDA graph
+    allowed = ("tuned_graph", "tuned", "auto_graph", "auto", "filter_f32", "filter_bf16x3", "filter_bf16x2",
+               "fp64_fma")
+    asked = (args.variants.split(",") if args.variants != ",".join(VARIANTS)
+             else ["tuned_graph", "tuned", "auto", "filter_f32", "fp64_fma"])
     variants = [v for v in asked if v in allowed] or ["auto"]
+    tune_dir = tempfile.mkdtemp(prefix="sj_tune_")
+    tune_path = os.path.join(tune_dir, "batch.txt")
+    tuned = {}
+
+    def make_opt(kname):
+        cache = tune_path if kname.startswith("tuned") else None
+        if cache and not tuned:
+            t0 = time.perf_counter()
+            tuned["groups"] = binding.sj_autotune_batch(
+                prepared, binding.sj_default_options(max_pairs_hint=args.hint), stream, reps=1, cache_path=cache)
+            tuned["seconds"] = round(time.perf_counter() - t0, 1)
+        base = kname.replace("tuned", "auto").replace("_graph", "")
+        return binding.sj_default_options(kernel=base, max_pairs_hint=args.hint, graph=int(kname.endswith("_graph")),
+                                          tune_cache=cache)
+
     sampler = ClockSampler(local)
     results = {}
     for vi, kname in enumerate(variants):
-        opt = binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint)
+        opt = make_opt(kname)
         for _ in range(args.warmup):
             one_step(opt, prepared)
         sync_all()
@@ -564,7 +607,7 @@ def run_batched(args):
     # end to end: host inputs (pinned), every instance's pairs copied back to pinned host memory
     host_pts = binding.BatchInputs([torch.from_numpy(w.points).pin_memory() for w in insts], eps)
     host_out = torch.empty((head["max_count"] + 16, 2), dtype=torch.int32).pin_memory()
-    opt = binding.sj_default_options(kernel=variants[0], max_pairs_hint=args.hint)
+    opt = make_opt(variants[0])
     t_e2e = []
     for k in range(max(2, min(args.steps, 4))):
         flush.fill_(float(k))
@@ -598,6 +641,10 @@ def run_batched(args):
                                                           "candidate_pairs": head["n_candidates"],
                                                           "result_pairs": head["count"]}),
             "variants": var,
+            "autotune": None if not tuned else {
+                "seconds": tuned["seconds"],
+                "groups": {str(g["dp"]): {"kernel": knames.get(g["kernel"], "?"), "queries_per_item": g["qpi"],
+                                          "tile_ms": round(g["ms"], 3)} for g in tuned["groups"]}},
             "e2e": {"value": world * nsq / e2e_s, "unit": BATCH_UNIT,
                     "h2d_bytes_per_step": sum(w.n * w.d * 8 for w in insts),
                     "d2h_bytes_per_step": head["count"] * 8, "ms_per_step": round(e2e_s * 1e3, 1)},

@@ -97,15 +97,35 @@ typedef struct sj_options {
                                  distance work); 0: every query cell scans its
                                  full 3^m neighbourhood as in Sec. III-B */
     int32_t queries_per_item; /* queries per work item (a cell's queries are
-                                 split into items of at most this many);
-                                 0 = automatic */
-    int32_t reserved0;
+                                 split into items of at most this many; the
+                                 query tile of the tensor-core filter);
+                                 0 = automatic (the kernel's maximum: 16 for
+                                 the CUDA-core kernels, 248 or 120 for the
+                                 tensor-core filter) */
+    int32_t graph;            /* batched joins: 1 = the join phase (every
+                                 group's tile and recheck launches) runs as one
+                                 CUDA graph, captured per call on a private
+                                 stream with the tensor-core groups and the
+                                 CUDA-core groups on two parallel branches, and
+                                 launched on the caller's stream; 0 = plain
+                                 launches on the stream, group after group.
+                                 Ignored by single joins. */
     int64_t page_pairs;       /* pairs per result page; 0 = 1 << 22 */
     int64_t max_pairs_hint;   /* expected result size; 0 = automatic */
+    const char* tune_cache;   /* NULL, or the path of a tuning cache written by
+                                 sj_autotune / sj_autotune_batch.  With kernel
+                                 AUTO, a matching entry supplies the kernel and
+                                 (where the options leave them 0) the queries
+                                 per item and the indexed dims: for a single
+                                 join the entry of the same d whose
+                                 round(log2 n) is nearest, within 1; for a
+                                 batched join, per group, the entry of the
+                                 group's padded dimension.  A missing file is
+                                 an empty cache. */
 } sj_options;
 
 /* Fills *opt with the defaults (kernel AUTO, no distances, automatic m,
- * symmetric, automatic item size and pool). */
+ * symmetric, automatic item size and pool, no graph, no tuning cache). */
 SJ_API void sj_default_options(sj_options* opt);
 
 /* ---- index ------------------------------------------------------------- */
@@ -224,6 +244,76 @@ SJ_API int sj_selftest_bounded_wait(void* stream);
  */
 SJ_API int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps,
                   int32_t count, const sj_options* opt, void* stream, sj_result* per_instance_out);
+
+/* ---- autotuner --------------------------------------------------------- */
+/*
+ * No counterpart in the paper, which fixes one kernel design for its GPU.
+ * The tunable choices of a join here are the distance kernel (which also
+ * fixes the split count of the tensor-core operands: none for the FP32
+ * filter, 2 terms for BF16X2, 3 for BF16X3), the queries per work item (the
+ * query tile of a work item, Sec. III-B's shared candidate set) and the
+ * number of indexed dims (Sec. II-D).  The autotuner times each candidate
+ * configuration on the caller's data with CUDA events on `stream` and keeps
+ * the fastest.
+ *
+ * Tuning cache file: plain text, one entry per line, '#' starts a comment,
+ * later lines override earlier ones with the same key:
+ *   single d=<d> nlog2=<round(log2 n)> kernel=<k> qpi=<q> m=<m> ms=<t>
+ *   batch dp=<padded d> kernel=<k> qpi=<q> ms=<t>
+ * (kernel: an SJ_KERNEL_* number; qpi, m: 0 = automatic; ms: the time the
+ * entry was tuned at).  Entries are appended to the file.
+ */
+
+/*
+ * Tunes a single join of (pts, n, d, eps) (pts host or device, as for
+ * sj_build_index).  Candidates: kernel in {FILTER_F32, FILTER_BF16X2 and
+ * FILTER_BF16X3 when d <= 64} x queries per item in {the kernel's maximum,
+ * half of it, a quarter} (at least 4) x indexed dims in {automatic, one less
+ * than the automatic choice}; the FP64 kernels are never candidates (FP64 runs
+ * at a small fraction of the FP32 and tensor rates on this part).  Each
+ * candidate's time is the whole path, sj_build_index to the count of
+ * sj_self_join, on `stream`: one untimed warm-up run, then the median of
+ * `reps` timed runs (reps < 1 means 3); a candidate whose warm-up takes more
+ * than twice the best median so far is not timed further.  `base` (may be
+ * NULL) supplies every other option; its kernel, queries_per_item and
+ * indexed_dims are ignored.  On success *best is `base` with the winning
+ * kernel, queries_per_item and indexed_dims (tune_cache untouched) and
+ * *best_ms (may be NULL) its median time; when `cache_path` is not NULL the
+ * winner is appended to that file.  Errors: those of sj_build_index /
+ * sj_self_join for the first candidate, SJ_ERR_ARG for a NULL `best` or a
+ * cache file that cannot be written.
+ */
+SJ_API int sj_autotune(const double* pts, int64_t n, int32_t d, double eps, const sj_options* base, void* stream,
+                       int32_t reps, const char* cache_path, sj_options* best, double* best_ms);
+
+/*
+ * Tunes a batched join (arguments as for sj_join_batch) per group of padded
+ * dimension.  Candidates, each applied to every group it supports: FILTER_F32
+ * with 16 and 8 queries per item; FILTER_BF16X2 with its maximum, half and a
+ * quarter; FILTER_BF16X3 with its maximum (tensor-core candidates only for
+ * padded d <= 64).  Each candidate runs the whole batch once untimed and
+ * `reps` times timed (reps < 1 means 2); a group's time for a candidate is the
+ * median of its distance-tile kernel time (sj_result.ms_tile).  Per group the
+ * fastest candidate is written to group_dp[g], group_kernel[g], group_qpi[g]
+ * and group_ms[g] (g < *n_groups <= max_groups; any of these arrays may be
+ * NULL) and appended to `cache_path` when not NULL.  Errors: those of
+ * sj_join_batch, SJ_ERR_ARG for an unwritable cache file.
+ */
+SJ_API int sj_autotune_batch(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps,
+                             int32_t count, const sj_options* base, void* stream, int32_t reps,
+                             const char* cache_path, int32_t max_groups, int32_t* n_groups, int32_t* group_dp,
+                             int32_t* group_kernel, int32_t* group_qpi, double* group_ms);
+
+/*
+ * Looks up the tuning cache at `path` without touching a GPU: for batch = 0
+ * the entry a single join of n points in d dims would use, for batch = 1 the
+ * entry of a batched group of padded dimension d (n ignored).  Returns 1 and
+ * fills kernel / qpi / m (any may be NULL; m is 0 for batched entries) when
+ * an entry matches, 0 when none does, SJ_ERR_ARG for a NULL path or a
+ * malformed line (named in sj_last_error_message).
+ */
+SJ_API int sj_tune_lookup(const char* path, int32_t batch, int32_t d, int64_t n, int32_t* kernel, int32_t* qpi,
+                          int32_t* m);
 
 /* ---- self-join without allocation -------------------------------------- */
 /*

@@ -57,9 +57,10 @@ class sj_options(ctypes.Structure):
         ("indexed_dims", ctypes.c_int32),
         ("symmetric", ctypes.c_int32),
         ("queries_per_item", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("graph", ctypes.c_int32),
         ("page_pairs", ctypes.c_int64),
         ("max_pairs_hint", ctypes.c_int64),
+        ("tune_cache", ctypes.c_char_p),
     ]
 
 
@@ -140,6 +141,18 @@ def load():
         lib.sj_results_free.restype = None
         lib.sj_selftest_bounded_wait.argtypes = [_vp]
         lib.sj_selftest_bounded_wait.restype = ctypes.c_int
+        lib.sj_autotune.argtypes = [_vp, _i64, _i32, ctypes.c_double, ctypes.POINTER(sj_options), _vp, _i32,
+                                    ctypes.c_char_p, ctypes.POINTER(sj_options), ctypes.POINTER(ctypes.c_double)]
+        lib.sj_autotune.restype = ctypes.c_int
+        lib.sj_autotune_batch.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
+                                          ctypes.POINTER(ctypes.c_double), _i32, ctypes.POINTER(sj_options), _vp,
+                                          _i32, ctypes.c_char_p, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                          ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                          ctypes.POINTER(ctypes.c_double)]
+        lib.sj_autotune_batch.restype = ctypes.c_int
+        lib.sj_tune_lookup.argtypes = [ctypes.c_char_p, _i32, _i32, _i64, ctypes.POINTER(_i32),
+                                       ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+        lib.sj_tune_lookup.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -196,6 +209,9 @@ def sj_default_options(**overrides) -> sj_options:
     o = sj_options()
     load().sj_default_options(ctypes.byref(o))
     for k, v in overrides.items():
+        if k == "tune_cache":
+            o.tune_cache = None if v is None else os.fsencode(v)
+            continue
         if k == "kernel" and isinstance(v, str):
             v = KERNELS[v]
         setattr(o, k, int(v))
@@ -335,6 +351,48 @@ def sj_self_join_noalloc(points, eps: float, pairs_out, stream=None) -> int:
     return int(cnt.value)
 
 
+def sj_autotune(points, eps: float, base: sj_options | None = None, stream=None, reps: int = 0,
+                cache_path=None):
+    """Times the candidate configurations of a single join on ``points``
+    and returns (best options, median ms of the whole path); the winner is
+    appended to ``cache_path`` when given."""
+    ptr, n, d, keep = _points_ptr(points)
+    best = sj_options()
+    ms = ctypes.c_double(0.0)
+    _check(load().sj_autotune(ptr, n, d, float(eps), ctypes.byref(base) if base is not None else None,
+                              _stream_ptr(stream), int(reps), None if cache_path is None else os.fsencode(cache_path),
+                              ctypes.byref(best), ctypes.byref(ms)))
+    del keep
+    return best, float(ms.value)
+
+
+def sj_autotune_batch(inputs: "BatchInputs", base: sj_options | None = None, stream=None, reps: int = 0,
+                      cache_path=None) -> list:
+    """Tunes a batched join per group of padded dimension; returns one dict
+    per group (dp, kernel, qpi, ms), the winners also appended to
+    ``cache_path`` when given."""
+    mg = 64
+    ng = _i32(0)
+    gdp, gk, gq = (_i32 * mg)(), (_i32 * mg)(), (_i32 * mg)()
+    gms = (ctypes.c_double * mg)()
+    _check(load().sj_autotune_batch(inputs.ptrs, inputs.ns, inputs.ds, inputs.es, inputs.count,
+                                    ctypes.byref(base) if base is not None else None, _stream_ptr(stream), int(reps),
+                                    None if cache_path is None else os.fsencode(cache_path), mg, ctypes.byref(ng),
+                                    gdp, gk, gq, gms))
+    return [{"dp": gdp[i], "kernel": gk[i], "qpi": gq[i], "ms": gms[i]} for i in range(ng.value)]
+
+
+def sj_tune_lookup(path, batch: int, d: int, n: int = 0):
+    """The tuning-cache entry a join would use (no GPU needed): a dict with
+    kernel, qpi and m, or None when no entry matches."""
+    k, q, m = _i32(0), _i32(0), _i32(0)
+    r = load().sj_tune_lookup(os.fsencode(path), int(batch), int(d), int(n), ctypes.byref(k), ctypes.byref(q),
+                              ctypes.byref(m))
+    if r < 0:
+        _check(r)
+    return {"kernel": k.value, "qpi": q.value, "m": m.value} if r == 1 else None
+
+
 def sj_selftest_bounded_wait(stream=None) -> int:
     """Runs the library's bounded-wait self-test; returns its status
     (SJ_ERR_TIMEOUT when the wait gave up as designed)."""
@@ -360,11 +418,12 @@ def sj_kernel_launches() -> int:
 # ---- convenience ------------------------------------------------------------------
 
 def self_join(points, eps: float, kernel="auto", emit_distances=False, symmetric=True, indexed_dims=0,
-              max_pairs_hint=0, stream=None):
+              max_pairs_hint=0, queries_per_item=0, tune_cache=None, stream=None):
     """Build, join and copy out in one call: returns (pairs int32 n x 2 numpy,
     distances or None, stats dict)."""
     opt = sj_default_options(kernel=kernel, emit_distances=int(emit_distances), symmetric=int(symmetric),
-                             indexed_dims=indexed_dims, max_pairs_hint=max_pairs_hint)
+                             indexed_dims=indexed_dims, max_pairs_hint=max_pairs_hint,
+                             queries_per_item=queries_per_item, tune_cache=tune_cache)
     h = sj_build_index(points, eps, opt, stream)
     try:
         info = sj_index_info(h)
@@ -381,11 +440,12 @@ def self_join(points, eps: float, kernel="auto", emit_distances=False, symmetric
 
 
 def join_batch(points_list, eps_list, kernel="auto", emit_distances=False, symmetric=True, page_pairs=0,
-               max_pairs_hint=0, indexed_dims=0, stream=None):
+               max_pairs_hint=0, indexed_dims=0, queries_per_item=0, graph=0, tune_cache=None, stream=None):
     """Batched self-joins in one call: returns one (pairs, distances or None,
     stats) per instance, the results already copied to the host and freed."""
     opt = sj_default_options(kernel=kernel, emit_distances=int(emit_distances), symmetric=int(symmetric),
-                             page_pairs=page_pairs, max_pairs_hint=max_pairs_hint, indexed_dims=indexed_dims)
+                             page_pairs=page_pairs, max_pairs_hint=max_pairs_hint, indexed_dims=indexed_dims,
+                             queries_per_item=queries_per_item, graph=int(graph), tune_cache=tune_cache)
     res = sj_join_batch(points_list, eps_list, opt, stream)
     out = []
     try:

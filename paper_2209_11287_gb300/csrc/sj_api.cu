@@ -127,7 +127,7 @@ static int pick_kernel(const Index* ix) {
     return (ix->d >= 16 && ix->d <= 64) ? SJ_KERNEL_FILTER_BF16X2 : SJ_KERNEL_FILTER_F32;
 }
 
-static int round_dim(int d) {
+int round_dim(int d) {
     int p = 2;
     while (p < d) p <<= 1;
     return p;
@@ -196,6 +196,18 @@ int sj_build_index(const double* pts, int64_t n, int32_t d, double eps, const sj
         o.queries_per_item < 0 || o.page_pairs < 0 || o.max_pairs_hint < 0) {
         set_error("invalid options");
         return SJ_ERR_ARG;
+    }
+    // AUTO with a tuning cache: a tuned entry for this d and size supplies the
+    // kernel and whichever of items / indexed dims the caller left automatic
+    if (o.kernel == SJ_KERNEL_AUTO && o.tune_cache && o.tune_cache[0]) {
+        std::vector<TuneEntry> table;
+        int ts = tune_load(o.tune_cache, &table);
+        if (ts != SJ_OK) return ts;
+        if (const TuneEntry* te = tune_find_single(table, d, n)) {
+            o.kernel = te->kernel;
+            if (o.queries_per_item == 0) o.queries_per_item = te->qpi;
+            if (o.indexed_dims == 0) o.indexed_dims = te->m;
+        }
     }
     sj_index* ix = new (std::nothrow) sj_index();
     if (!ix) return SJ_ERR_OOM;
@@ -484,6 +496,124 @@ int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj_option
 int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps, int32_t count,
                   const sj_options* opt, void* stream, sj_result* per_instance_out) {
     clear_error();
+    return join_batch_impl(pts, n, d, eps, count, opt, stream, per_instance_out, nullptr);
+}
+
+}  // extern "C"
+
+namespace sj {
+
+// The join phase of a batched join: per group the counter reset, the
+// distance-tile launch between its two timing events and the recheck launch.
+// With `graph`, the phase is captured on a private stream into one CUDA graph
+// (the tensor-core groups on one branch, the CUDA-core groups on another, so
+// a group's tail overlaps the other branch) and launched on `s`; otherwise the
+// launches go to `s` in group order.
+static int batch_join_phase(std::vector<std::unique_ptr<BatchGroup>>& groups, const std::vector<JoinOut>& jos,
+                            int32_t* table, long long table_slots, unsigned long long* cursor, int count, bool dist,
+                            bool graph, cudaStream_t s) {
+    auto launch_group = [&](size_t gi, cudaStream_t gs) -> int {
+        BatchGroup& g = *groups[gi];
+        Index* ix = &g.ix;
+        if (ix->n_items == 0) return SJ_OK;
+        const cudaStream_t keep = ix->stream;
+        ix->stream = gs;
+        int st = SJ_OK;
+        // inside a capture, only an external record becomes a timing node of the graph
+        const unsigned rec = graph ? cudaEventRecordExternal : cudaEventRecordDefault;
+        cudaError_t e = cudaMemsetAsync(ix->counters, 0, kCounters * sizeof(unsigned long long), gs);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ix->ev_tile[0], gs, rec);
+        if (e != cudaSuccess) {
+            set_error("batch group launch: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+        }
+        if (st == SJ_OK)
+            st = is_tensor_kernel(ix->kernel) ? launch_join_tc(ix, jos[gi], dist ? 1 : 0)
+                                              : launch_join_cc(ix, jos[gi], dist ? 1 : 0);
+        if (st == SJ_OK && cudaEventRecordWithFlags(ix->ev_tile[1], gs, rec) != cudaSuccess) st = SJ_ERR_CUDA;
+        if (st == SJ_OK) st = launch_recheck(ix, jos[gi], dist ? 1 : 0);
+        ix->stream = keep;
+        return st;
+    };
+    auto reset = [&](cudaStream_t rs) -> int {
+        SJ_CK(cudaMemsetAsync(table, 0xFF, table_slots * sizeof(int32_t), rs));
+        SJ_CK(cudaMemsetAsync(cursor, 0, (count + 2) * sizeof(unsigned long long), rs));
+        return SJ_OK;
+    };
+    if (!graph) {
+        SJ_TRY(reset(s));
+        for (size_t gi = 0; gi < groups.size(); ++gi) SJ_TRY(launch_group(gi, s));
+        return SJ_OK;
+    }
+    cudaStream_t cs = nullptr, br[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    int st = SJ_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        set_error("batch graph set-up: %s", cudaGetErrorString(e));
+        st = SJ_ERR_CUDA;
+    }
+    bool capturing = false;
+    if (st == SJ_OK) {
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            set_error("batch graph capture: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+        } else {
+            capturing = true;
+        }
+    }
+    if (st == SJ_OK) st = reset(cs);
+    if (st == SJ_OK) {
+        e = cudaEventRecord(fork, cs);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(br[b], fork, 0);
+        if (e != cudaSuccess) st = SJ_ERR_CUDA;
+    }
+    for (size_t gi = 0; gi < groups.size() && st == SJ_OK; ++gi)
+        st = launch_group(gi, br[is_tensor_kernel(groups[gi]->ix.kernel) ? 0 : 1]);
+    if (st == SJ_OK) {
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventRecord(join[b], br[b]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, join[b], 0);
+        }
+        if (e != cudaSuccess) st = SJ_ERR_CUDA;
+    }
+    if (capturing) {
+        e = cudaStreamEndCapture(cs, &gr);
+        if (st == SJ_OK && e != cudaSuccess) {
+            set_error("batch graph capture: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+        }
+    }
+    if (st == SJ_OK) {
+        e = cudaGraphInstantiate(&ex, gr, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ex, s);
+        if (e != cudaSuccess) {
+            set_error("batch graph launch: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+        }
+    }
+    if (st != SJ_OK) cudaGetLastError();
+    // the executable graph may be destroyed while its launch is in flight
+    if (ex) cudaGraphExecDestroy(ex);
+    if (gr) cudaGraphDestroy(gr);
+    for (int b = 0; b < 2; ++b) {
+        if (join[b]) cudaEventDestroy(join[b]);
+        if (br[b]) cudaStreamDestroy(br[b]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cs) cudaStreamDestroy(cs);
+    return st;
+}
+
+int join_batch_impl(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps, int32_t count,
+                    const sj_options* opt, void* stream, sj_result* per_instance_out,
+                    const std::vector<TuneEntry>* forced) {
     if (!pts || !n || !d || !eps || !per_instance_out || count < 1) {
         set_error("invalid batch arguments");
         return SJ_ERR_ARG;
@@ -508,7 +638,22 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
     // AUTO: the tensor-core filter for padded dimensions 8 .. 64 (measured on
     // uniform instances with the batched grid choice: d 8 1.7x, d 16 4x, d 32
     // 12x faster than the FP32 filter), else the FP32 CUDA-core filter
+    std::vector<TuneEntry> tuned;
+    if (o.kernel == SJ_KERNEL_AUTO && o.tune_cache && o.tune_cache[0]) {
+        const int ts = tune_load(o.tune_cache, &tuned);
+        if (ts != SJ_OK) return ts;
+    }
+    // a group's configuration: a forced entry (tuning runs), else a tuned
+    // entry of the cache (AUTO), else the options
+    auto group_entry = [&](int dp) -> const TuneEntry* {
+        const TuneEntry* e = forced ? tune_find_group(*forced, dp) : nullptr;
+        if (!e && !tuned.empty()) e = tune_find_group(tuned, dp);
+        if (!e || e->kernel == SJ_KERNEL_AUTO || e->kernel == SJ_KERNEL_FP64_DMMA) return nullptr;
+        if (is_tensor_kernel(e->kernel) && dp > 64) return nullptr;
+        return e;
+    };
     auto group_kernel = [&](int dp) {
+        if (const TuneEntry* e = group_entry(dp)) return e->kernel;
         if (o.kernel != SJ_KERNEL_AUTO) return o.kernel;
         return (dp >= 8 && dp <= 64) ? SJ_KERNEL_FILTER_BF16X2 : SJ_KERNEL_FILTER_F32;
     };
@@ -551,6 +696,7 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
             g->ix.device = dev;
             g->ix.stream = s;
             g->ix.opt = o;
+            if (const TuneEntry* te = group_entry(dp)) g->ix.opt.queries_per_item = te->qpi;
             g->ix.kernel = group_kernel(dp);
             g->ix.d = dp;
             g->ix.dp = dp;
@@ -664,13 +810,10 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
         st = dev_alloc_t(&pool->block, (size_t)n_pages * page_pairs * 2, s);
         if (st == SJ_OK && dist) st = dev_alloc_t(&pool->dblock, (size_t)n_pages * page_pairs, s);
         if (st != SJ_OK) break;
-        cudaError_t e = cudaMemsetAsync(table, 0xFF, std::max<long long>(toff[count], 1) * sizeof(int32_t), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, (count + 2) * sizeof(unsigned long long), s);
-        if (e != cudaSuccess) {
-            set_error("batch reset: %s", cudaGetErrorString(e));
-            st = SJ_ERR_CUDA;
-            break;
-        }
+        cudaError_t e = cudaSuccess;
+        std::vector<BatchJoin> hbj(groups.size());
+        std::vector<JoinOut> jos(groups.size());
+        std::vector<int2*> bands(groups.size(), nullptr);
         for (size_t gi = 0; gi < groups.size() && st == SJ_OK; ++gi) {
             BatchGroup& g = *groups[gi];
             BatchJoin bj{};
@@ -689,36 +832,36 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
             bj.max_pages = dmaxp;
             bj.cursor = cursor;
             bj.error = cursor + count + 1;
-            e = cudaMemcpyAsync(dbj + gi, &bj, sizeof bj, cudaMemcpyHostToDevice, s);
-            if (e != cudaSuccess) {
-                st = SJ_ERR_CUDA;
-                break;
-            }
+            hbj[gi] = bj;
             Index* ix = &g.ix;
             if (ix->n_items == 0) continue;
             const unsigned long long ev = (unsigned long long)std::max<int64_t>(ix->n_evaluated, 1);
             unsigned long long band_cap =
                 std::min<unsigned long long>(ev, std::max<unsigned long long>(1ull << 20, dist ? ev / 8 : ev / 64));
-            int2* band = nullptr;
-            if ((st = dev_alloc_t(&band, (size_t)band_cap, s)) != SJ_OK) break;
-            JoinOut jo;
-            jo.band = band;
-            jo.band_cap = band_cap;
-            jo.batch = dbj + gi;
-            e = cudaMemsetAsync(ix->counters, 0, kCounters * sizeof(unsigned long long), s);
-            if (e == cudaSuccess && !ix->ev_tile[0]) {
+            if ((st = dev_alloc_t(&bands[gi], (size_t)band_cap, s)) != SJ_OK) break;
+            jos[gi].band = bands[gi];
+            jos[gi].band_cap = band_cap;
+            jos[gi].batch = dbj + gi;
+            if (!ix->ev_tile[0]) {
                 e = cudaEventCreate(&ix->ev_tile[0]);
                 if (e == cudaSuccess) e = cudaEventCreate(&ix->ev_tile[1]);
+                if (e != cudaSuccess) {
+                    set_error("batch events: %s", cudaGetErrorString(e));
+                    st = SJ_ERR_CUDA;
+                }
             }
-            if (e == cudaSuccess) e = cudaEventRecord(ix->ev_tile[0], s);
-            if (e != cudaSuccess) st = SJ_ERR_CUDA;
-            if (st == SJ_OK)
-                st = is_tensor_kernel(ix->kernel) ? launch_join_tc(ix, jo, dist ? 1 : 0)
-                                                           : launch_join_cc(ix, jo, dist ? 1 : 0);
-            if (st == SJ_OK && cudaEventRecord(ix->ev_tile[1], s) != cudaSuccess) st = SJ_ERR_CUDA;
-            if (st == SJ_OK) st = launch_recheck(ix, jo, dist ? 1 : 0);
-            dev_free(band, s);
         }
+        if (st == SJ_OK) {
+            e = cudaMemcpyAsync(dbj, hbj.data(), hbj.size() * sizeof(BatchJoin), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                set_error("batch routing copy: %s", cudaGetErrorString(e));
+                st = SJ_ERR_CUDA;
+            }
+        }
+        if (st == SJ_OK)
+            st = batch_join_phase(groups, jos, table, std::max<long long>(toff[count], 1), cursor, count, dist,
+                                  o.graph != 0, s);
+        for (int2* b : bands) dev_free(b, s);
         if (st != SJ_OK) break;
         e = cudaMemcpyAsync(cur.data(), cursor, (count + 2) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -732,8 +875,12 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
         for (size_t gi = 0; gi < groups.size(); ++gi) {
             auto& g = groups[gi];
             float ms = 0.f;
-            if (g->ix.n_items > 0 && cudaEventElapsedTime(&ms, g->ix.ev_tile[0], g->ix.ev_tile[1]) == cudaSuccess)
-                group_ms[gi] = ms;
+            if (g->ix.n_items > 0) {
+                if (cudaEventElapsedTime(&ms, g->ix.ev_tile[0], g->ix.ev_tile[1]) == cudaSuccess)
+                    group_ms[gi] = ms;
+                else
+                    cudaGetLastError();  // no timing: not an error of the join
+            }
             if (is_tensor_kernel(g->ix.kernel) && g->ix.n_items > 0) {
                 unsigned long long flag = 0;  // the tensor-core kernel's bounded-wait flag
                 if (cudaMemcpy(&flag, g->ix.counters + 4, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -829,4 +976,4 @@ int sj_join_batch(const double* const* pts, const int64_t* n, const int32_t* d, 
     return st;
 }
 
-}  // extern "C"
+}  // namespace sj

@@ -672,7 +672,7 @@ static int choose_grid(Index* ix) {
     // work is about M ceil(q / qmax) qmax n prod_k (3 c_k - 2) / c_k^2.  The
     // tensor-core filter's large items pay for few big cells.
     if (ix->trim_dims && ix->opt.indexed_dims <= 0 && !take.empty()) {
-        const int qmax = is_tensor_kernel(ix->kernel) ? tc_qmax(tc_kp(ix->dp, ix->kernel)) : kQMax;
+        const int qmax = item_qmax(ix);
         const double nn = (double)ix->n;
         int best = 0;
         double best_cost = 0, cells = 1, frac = 1;
@@ -979,8 +979,7 @@ int build_index(Index* ix, const double* pts) {
         ep.stride[i] = ix->stride[i];
     }
     ep.symmetric = ix->opt.symmetric ? 1 : 0;
-    const int qcap = is_tensor_kernel(ix->kernel) ? tc_qmax(tc_kp(ix->dp, ix->kernel)) : kQMax;
-    ep.qmax = ix->opt.queries_per_item > 0 ? std::min(ix->opt.queries_per_item, qcap) : qcap;
+    ep.qmax = item_qmax(ix);
     const int64_t Mc = (int64_t)M;
     // dense key -> cell table when the key space is small (neighbour lookups
     // become O(1) instead of binary searches over the cell keys)
@@ -1563,7 +1562,7 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     // subtracts the instance's first position to get instance-local indices
     // ---- runs and items (one read-back) ----
     const int64_t M = ix->n_cells;
-    BEnum be{shift, ix->opt.symmetric ? 1 : 0, tensor ? tc_qmax(tc_kp(dp, ix->kernel)) : kQMax};
+    BEnum be{shift, ix->opt.symmetric ? 1 : 0, item_qmax(ix)};
     uint32_t* cnt = nullptr;
     SJ_TRY(dev_alloc_t(&cnt, (size_t)M * 4, s));
     uint32_t *run_cnt = cnt, *item_cnt = cnt + M, *run_off = cnt + 2 * M, *item_off = cnt + 3 * M;

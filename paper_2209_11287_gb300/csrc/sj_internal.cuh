@@ -206,6 +206,40 @@ constexpr int kTcPadRows = 256;
 constexpr int kCounters = 8;
 int launch_join_dmma(Index* ix, const JoinOut& out, int emit_dist);
 
+// Queries per work item of an index: the caller's queries_per_item when set
+// (clamped to the kernel's capacity), else the capacity: the query bitmask
+// width of the CUDA-core kernels, the query tile of the tensor-core filter.
+inline int item_qmax(const Index* ix) {
+    const int cap = is_tensor_kernel(ix->kernel) ? tc_qmax(tc_kp(ix->dp, ix->kernel)) : kQMax;
+    return ix->opt.queries_per_item > 0 ? (ix->opt.queries_per_item < cap ? ix->opt.queries_per_item : cap) : cap;
+}
+
+// ---- tuning cache (sj_tune.cu) -------------------------------------------------
+// One tuned configuration: for single joins keyed by (d, round(log2 n)), for
+// the groups of batched joins by the padded dimension.
+struct TuneEntry {
+    int batch = 0;       // 0 single join, 1 batched group
+    int d = 0;           // d (single) or padded d (batched group)
+    int nlog2 = 0;       // single joins: round(log2 n)
+    int kernel = SJ_KERNEL_AUTO;
+    int qpi = 0;         // queries per item, 0 = the kernel's capacity
+    int m = 0;           // indexed dims, 0 = automatic (single joins only)
+    double ms = 0;       // the time it was tuned at
+};
+// Reads a tuning cache (a missing file is an empty cache); later lines win.
+int tune_load(const char* path, std::vector<TuneEntry>* out);
+// The entry for a single join of n points in d dims: same d, nearest
+// round(log2 n) within 1; null if none.
+const TuneEntry* tune_find_single(const std::vector<TuneEntry>& t, int d, int64_t n);
+// The entry for a batched group of padded dimension dp; null if none.
+const TuneEntry* tune_find_group(const std::vector<TuneEntry>& t, int dp);
+// A batched join with per-group overrides: `forced` (tuning runs; kernel
+// AUTO in an entry means no override) and the options' tuning cache.
+int join_batch_impl(const double* const* pts, const int64_t* n, const int32_t* d, const double* eps, int32_t count,
+                    const sj_options* opt, void* stream, sj_result* per_instance_out,
+                    const std::vector<TuneEntry>* forced);
+int round_dim(int d);
+
 // ---- radix sort / scan (sj_index.cu) ------------------------------------------
 int radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cudaStream_t s);
 int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);

@@ -74,3 +74,45 @@ def test_invalid_options_rejected(lib):
     o.kernel = 99
     h = ctypes.c_void_p()
     assert lib.sj_build_index(x.ctypes.data, 4, 2, 0.1, ctypes.byref(o), None, ctypes.byref(h)) == binding.SJ_ERR_ARG
+
+
+def test_tune_cache_lookup(lib, tmp_path):
+    """The tuning cache is host logic: nearest round(log2 n) within 1 for
+    single joins, exact padded dimension for batched groups, later lines
+    win, a missing file is empty, a malformed line is an error."""
+    p = tmp_path / "tune.txt"
+    assert binding.sj_tune_lookup(str(p), 0, 4, 1 << 20) is None  # no file
+    p.write_text(
+        "# comment line\n"
+        "single d=4 nlog2=20 kernel=3 qpi=8 m=3 ms=1.5\n"
+        "single d=4 nlog2=21 kernel=5 qpi=0 m=0 ms=2.0   # trailing comment\n"
+        "\n"
+        "batch dp=16 kernel=5 qpi=62 ms=3.0\n"
+        "batch dp=16 kernel=4 qpi=0 ms=2.5\n"
+    )
+    assert binding.sj_tune_lookup(str(p), 0, 4, 1 << 20) == {"kernel": 3, "qpi": 8, "m": 3}
+    assert binding.sj_tune_lookup(str(p), 0, 4, 1 << 21) == {"kernel": 5, "qpi": 0, "m": 0}
+    assert binding.sj_tune_lookup(str(p), 0, 4, 1 << 19) == {"kernel": 3, "qpi": 8, "m": 3}  # gap 1
+    assert binding.sj_tune_lookup(str(p), 0, 4, 1 << 23) is None                             # gap 2
+    assert binding.sj_tune_lookup(str(p), 0, 8, 1 << 20) is None                             # other d
+    assert binding.sj_tune_lookup(str(p), 1, 16) == {"kernel": 4, "qpi": 0, "m": 0}          # later wins
+    assert binding.sj_tune_lookup(str(p), 1, 32) is None
+    with open(p, "a") as f:  # a later single entry for the same key overrides
+        f.write("single d=4 nlog2=20 kernel=4 qpi=16 m=2 ms=1.0\n")
+    assert binding.sj_tune_lookup(str(p), 0, 4, 1 << 20) == {"kernel": 4, "qpi": 16, "m": 2}
+    for bad in ("single d=4 kernel=3\n", "batch dp=16 kernel=9\n", "single d=0 nlog2=3 kernel=3\n",
+                "tile d=4\n", "batch dp=16 kernel=3 qpi=x\n"):
+        q = tmp_path / "bad.txt"
+        q.write_text(bad)
+        with pytest.raises(binding.SimJoinError) as ei:
+            binding.sj_tune_lookup(str(q), 0, 4, 16)
+        assert ei.value.status == binding.SJ_ERR_ARG
+    assert "malformed line 1" in binding.sj_last_error_message()
+
+
+def test_options_layout(lib):
+    """The binding's options mirror the header: defaults come back from C."""
+    o = binding.sj_default_options()
+    assert o.kernel == binding.SJ_KERNEL_AUTO and o.symmetric == 1 and o.graph == 0 and o.tune_cache is None
+    o = binding.sj_default_options(graph=1, tune_cache="/tmp/x", queries_per_item=8)
+    assert o.graph == 1 and o.tune_cache == b"/tmp/x" and o.queries_per_item == 8
