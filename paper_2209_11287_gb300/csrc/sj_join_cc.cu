@@ -43,11 +43,11 @@ constexpr int cc_warps() {
 template <typename T, int DP, int TC, bool EMIT, int RUNS>
 struct CcWarpSmem {
     ItemSmem<T, DP, RUNS> it;
-    int32_t cj[32 * TC];               // sorted position of each candidate slot
+    int32_t cj[EMIT ? 32 * TC : 1];    // sorted position of each candidate slot (with distances)
     int32_t cperm[32 * TC];            // its input index
     uint8_t cmir[32 * TC];             // its mirror flag
-    uint16_t list[32 * TC * (kQMax / 2)];  // maybe-in entries of one half of the queries:
-                                           // certain << 15 | slot << 4 | query
+    uint16_t list[EMIT ? 32 * TC * (kQMax / 2) : 1];  // with distances: maybe-in entries of one half
+                                                      // of the queries, slot << 4 | query
     int2 stage[kStage];
     double sdist[EMIT ? kStage : 1];
 };
@@ -92,6 +92,104 @@ __device__ __forceinline__ void tile_fused(const ItemSmem<T, DP, RUNS>& S, int Q
                 if (ge_threshold(a, ti[t])) cbits[t] |= 1u << q;
             }
         }
+    }
+}
+
+// Emission of one chunk without distances.  Certain pairs (maybe-in and
+// certain-in bits) go straight into the warp's stage: one warp scan of each
+// lane's output count (two outputs for a mirrored pair, one for a self pair)
+// gives every lane its slots, and each lane writes its pairs in query order.
+// A chunk larger than the stage is written in stage-sized windows, each
+// flushed when full.  Uncertain pairs (maybe-in, not certain-in: the
+// certified bound straddles eps) are queued for the binary64 recheck, one
+// per lane per round, or re-decided here when the queue is full.
+template <int TC>
+__device__ __forceinline__ void emit_direct(WarpStage& st, const JoinParams& P, const int32_t* cperm,
+                                            const uint8_t* cmir, const int32_t* qids, const ItemRoute& R,
+                                            const Item& I, int lane, const int32_t (&j)[TC],
+                                            const uint32_t (&bits)[TC], const uint32_t (&cbits)[TC],
+                                            unsigned long long& rechecked) {
+    int nout = 0;
+    uint32_t any_unc = 0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t) {
+        const uint32_t cin = bits[t] & cbits[t];
+        any_unc |= bits[t] & ~cbits[t];
+        if (cin) {
+            const int fl = cmir[t * 32 + lane];
+            const int c = __popc(cin);
+            nout += fl ? 2 * c : c;
+            const int qd = j[t] - I.q0;  // the diagonal of a self-cell candidate
+            if (fl == 2 && qd >= 0 && qd < kQMax && ((cin >> qd) & 1u)) nout -= 1;
+        }
+    }
+    int total;
+    const int off = warp_excl_scan(nout, lane, &total);
+    if (total > 0) {
+        if (st.cnt + total > kStage) stage_flush(st, P, lane);
+        for (int w0 = 0; w0 < total;) {  // warp-uniform
+            const int w1 = min(total, w0 + (kStage - st.cnt));
+            if (off < w1 && off + nout > w0) {
+                int idx = off;
+#pragma unroll
+                for (int t = 0; t < TC; ++t) {
+                    uint32_t b = bits[t] & cbits[t];
+                    if (!b) continue;
+                    const int slot = t * 32 + lane;
+                    const int fl = cmir[slot];
+                    const int32_t cid = (int32_t)(cperm[slot] - R.off);
+                    const int qd = fl == 2 ? j[t] - I.q0 : -1;
+                    while (b) {
+                        const int q = __ffs(b) - 1;
+                        b &= b - 1u;
+                        const int32_t qid = (int32_t)(qids[q] - R.off);
+                        if (idx >= w0 && idx < w1) st.pairs[st.cnt + idx - w0] = make_int2(qid, cid);
+                        ++idx;
+                        if (fl == 1 || (fl == 2 && q != qd)) {
+                            if (idx >= w0 && idx < w1) st.pairs[st.cnt + idx - w0] = make_int2(cid, qid);
+                            ++idx;
+                        }
+                    }
+                }
+            }
+            st.cnt += w1 - w0;
+            w0 = w1;
+            if (st.cnt == kStage) stage_flush(st, P, lane);
+        }
+    }
+    if (!__any_sync(0xffffffffu, any_unc != 0u)) return;
+    uint32_t unc[TC];
+#pragma unroll
+    for (int t = 0; t < TC; ++t) unc[t] = bits[t] & ~cbits[t];
+    for (;;) {
+        bool want = false;
+        int q = 0, slot = 0;
+        int32_t jj = 0;
+#pragma unroll
+        for (int t = 0; t < TC; ++t)
+            if (!want && unc[t]) {
+                q = __ffs(unc[t]) - 1;
+                unc[t] &= unc[t] - 1u;
+                want = true;
+                jj = j[t];
+                slot = t * 32 + lane;
+            }
+        if (!__any_sync(0xffffffffu, want)) break;
+        const int fl = want ? cmir[slot] : 0;
+        const bool mir = fl == 1 || (fl == 2 && jj != I.q0 + q);
+        const bool queued = band_push(P, lane, want, I.q0 + q, jj, mir);
+        int no = 0;
+        int32_t qid = 0, cid = 0;
+        if (want && !queued) {  // queue full: decide here
+            const double s = direct_sq(P.xs + (int64_t)(I.q0 + q) * P.dp, P.xs + (int64_t)jj * P.dp, P.d);
+            ++rechecked;
+            if (s <= R.e2) {
+                no = mir ? 2 : 1;
+                qid = (int32_t)(qids[q] - R.off);
+                cid = (int32_t)(cperm[slot] - R.off);
+            }
+        }
+        stage_emit_pairs(st, P, lane, no, qid, cid);
     }
 }
 
@@ -152,7 +250,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                     j[t] = map_candidate_flag<T, DP>(S, nr, v, fl);
                     to[t] = TO[j[t]];
                     ti[t] = TI[j[t]];
-                    W.cj[slot] = j[t];
+                    if constexpr (EMIT) W.cj[slot] = j[t];
                     W.cperm[slot] = P.perm[j[t]];
                     W.cmir[slot] = fl;
                     // self-cell triangle: candidate j pairs with queries q0 .. j only
@@ -208,7 +306,12 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                 bits[t] &= tri_mask[t];
                 cbits[t] &= tri_mask[t];
             }
-            // compact the maybe-in pairs with one warp scan per half of the queries
+            if constexpr (!EMIT) {
+                emit_direct<TC>(st, P, W.cperm, W.cmir, S.qid, R, I, lane, j, bits, cbits, rechecked);
+            } else {
+            // with distances every maybe-in pair is re-decided in binary64: the
+            // pairs are compacted with one warp scan per half of the queries and
+            // queued 32 at a time
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
             const uint32_t hm = half ? 0xFF00u : 0x00FFu;
@@ -224,8 +327,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                 while (b) {
                     const int q = __ffs(b) - 1;
                     b &= b - 1u;
-                    const int certain = (cbits[t] >> q) & 1u;
-                    W.list[off++] = (uint16_t)((certain << 15) | ((t * 32 + lane) << 4) | q);
+                    W.list[off++] = (uint16_t)(((t * 32 + lane) << 4) | q);
                 }
             }
             __syncwarp();
@@ -244,13 +346,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                     jj = W.cj[slot];
                     const int fl = W.cmir[slot];
                     mir = fl == 1 || (fl == 2 && jj != (int64_t)(I.q0 + q));
-                    if ((ent >> 15) && !EMIT) {  // certain in
-                        nout = mir ? 2 : 1;
-                        qid = (int32_t)(S.qid[q] - R.off);
-                        cid = (int32_t)(W.cperm[slot] - R.off);
-                    } else {
-                        band = true;  // re-decided (and measured) in binary64
-                    }
+                    band = true;
                 }
                 const bool queued = band_push(P, lane, band, I.q0 + q, (int32_t)jj, mir);
                 if (band && !queued) {  // queue full: decide here
@@ -260,15 +356,13 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                         nout = mir ? 2 : 1;
                         qid = (int32_t)(S.qid[q] - R.off);
                         cid = (int32_t)(W.cperm[(W.list[e] >> 4) & 0x7FF] - R.off);
-                        if (EMIT) dist = sqrt(s);
+                        dist = sqrt(s);
                     }
                 }
-                if (EMIT)
-                    stage_emit(st, P, lane, nout, qid, cid, dist);
-                else
-                    stage_emit_pairs(st, P, lane, nout, qid, cid);
+                stage_emit(st, P, lane, nout, qid, cid, dist);
             }
             __syncwarp();
+            }
             }
         }
         __syncwarp();
