@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0 = sized for ~15 s)")
     ap.add_argument("--hint", type=int, default=0, help="expected result pairs (0 = the library's automatic pool)")
     ap.add_argument("--workload", default="uniform4d",
-                    choices=["uniform4d", "uniform2d", "mixture16d", "expo64d", "batched"],
+                    choices=["uniform4d", "uniform2d", "mixture16d", "expo64d", "brute16d", "batched"],
                     help="uniform4d: the 2M-point 4-D self-join (the headline); uniform2d: 16384 x 2; mixture16d: "
                          "1M x 16 Gaussian mixture; expo64d: 500k x 64 clipped exponential; batched: 4096 "
                          "independent joins")
@@ -82,11 +82,15 @@ WORKLOAD_TEXT = {
                   "eps calibrated on the oracle for a mean of 100 neighbours",
     "expo64d": "64-D coordinates i.i.d. exponential(40) clipped to [0,1], eps calibrated on the oracle for a "
                "mean of 50 neighbours",
+    "brute16d": "16-D coordinates i.i.d. exponential(40) clipped to [0,1], eps calibrated on the oracle for a "
+                "mean of 50 neighbours, joined without an index (brute force: every pair evaluated)",
 }
 METRICS = {
     "uniform4d": METRIC,
     "uniform2d": "self-join candidate pairs/s and join time, n=16384 d=2: FP64 plain vs low-prec filter",
     "mixture16d": "self-join candidate pairs/s and join time, n=1M d=16 Gaussian mixture: FP64 plain vs low-prec filter",
+    "brute16d": "brute-force self-join (no index) pairs/s and join time, n=2^17 d=16 clipped exponential: FP64 "
+                "CUDA cores vs FP64 tensor cores vs low-prec filter",
     "expo64d": "self-join candidate pairs/s and join time, n=500k d=64 clipped exponential: FP64 plain vs "
                "low-prec filter",
 }
@@ -95,6 +99,7 @@ DEFAULT_VARIANTS = {
     "uniform2d": ["filter_f32", "fp64_fma", "fp64_dmma", "filter_bf16x2"],
     "mixture16d": ["filter_bf16x2", "tuned", "filter_bf16x3", "filter_f32", "fp64_fma"],
     "expo64d": ["filter_bf16x2", "filter_bf16x3", "filter_f32"],
+    "brute16d": ["filter_bf16x2", "filter_bf16x3", "filter_f32", "fp64_fma", "fp64_dmma"],
 }
 
 
@@ -220,7 +225,8 @@ def run_native(args):
         """Options of a variant: a kernel name, or "tuned" (the autotuner's
         pick for this workload, tuned once before the variant's warm-up)."""
         if kname != "tuned":
-            return binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint)
+            return binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint,
+                                              indexed_dims=binding.SJ_NO_INDEX if w.name == "brute16d" else 0)
         if not tuned:
             t0 = time.perf_counter()
             best, ms = binding.sj_autotune(pts, w.eps, binding.sj_default_options(max_pairs_hint=args.hint), stream,

@@ -84,6 +84,7 @@ extern "C" {
                                      certified band); d <= 64 */
 
 /* ---- options ----------------------------------------------------------- */
+#define SJ_NO_INDEX (-1)        /* sj_options.indexed_dims: brute force */
 typedef struct sj_options {
     int32_t kernel;           /* SJ_KERNEL_* */
     int32_t emit_distances;   /* 1: also return the FP64 distance of every
@@ -91,7 +92,10 @@ typedef struct sj_options {
                                  decision rule's sqrt(s)) */
     int32_t indexed_dims;     /* m, the number of dims the grid indexes
                                  (Sec. II-D: an index on fewer dims than d);
-                                 0 = automatic */
+                                 0 = automatic; SJ_NO_INDEX = no index: all
+                                 points form one cell and every pair is
+                                 evaluated by the same tile kernels (the
+                                 brute-force comparison of Sec. IV, Fig. 3) */
     int32_t symmetric;        /* 1: evaluate each unordered pair of adjacent
                                  cells once and emit both orders (halves the
                                  distance work); 0: every query cell scans its

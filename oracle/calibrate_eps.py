@@ -1,7 +1,8 @@
 """Writes the stored eps of the calibrated workloads (test infrastructure).
 
 For the 16-D Gaussian mixture (mean selectivity 100), the 64-D clipped
-exponential set (mean selectivity 50) and the batched instances of dimension
+exponential set (mean selectivity 50), the 16-D clipped exponential set of the
+brute-force workload (mean selectivity 50) and the batched instances of dimension
 8 and more (mean 32 neighbours each; in a unit cube the d-ball formula is far
 off there) no closed form gives eps, so it is calibrated with the oracle:
 squared distances from seeded sample queries (2000, or 500 per batched
@@ -9,7 +10,7 @@ instance) to all points (oracle order, the query itself excluded), eps^2 =
 the (target x queries)-th smallest of the pooled values.  The result goes to
 paper_2209_11287_gb300/workload_eps.json, which the workload generators read.
 
-Run: python oracle/calibrate_eps.py [--batched-only]
+Run: python oracle/calibrate_eps.py [--batched-only | --brute16d-only]
 """
 import json
 import os
@@ -48,6 +49,14 @@ def main():
     out = {}
     if os.path.exists(workloads.EPS_TABLE):
         out = json.load(open(workloads.EPS_TABLE))
+    if "--brute16d-only" in sys.argv:
+        b = workloads.brute16d(eps=1.0)
+        out["brute16d"] = calibrate(b.points, 50.0)
+        print("brute16d", out["brute16d"], flush=True)
+        with open(workloads.EPS_TABLE, "w") as f:
+            json.dump(out, f, indent=1, sort_keys=True)
+            f.write("\n")
+        return
     batched = {}
     for i in range(4096):
         n, d, _ = workloads.batch_instance_params(i)
@@ -67,6 +76,9 @@ def main():
     e = workloads.expo64d(eps=1.0)
     out["expo64d"] = calibrate(e.points, 50.0)
     print("expo64d", out["expo64d"], flush=True)
+    b = workloads.brute16d(eps=1.0)
+    out["brute16d"] = calibrate(b.points, 50.0)
+    print("brute16d", out["brute16d"], flush=True)
     with open(workloads.EPS_TABLE, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
         f.write("\n")

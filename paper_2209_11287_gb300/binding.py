@@ -27,6 +27,8 @@ SJ_ERR_TIMEOUT = -4
 SJ_ERR_CUDA = -5
 SJ_ERR_UNSUPPORTED = -6
 
+SJ_NO_INDEX = -1  # sj_options.indexed_dims: no index, every pair evaluated
+
 SJ_KERNEL_AUTO = 0
 SJ_KERNEL_FP64_FMA = 1
 SJ_KERNEL_FP64_DMMA = 2

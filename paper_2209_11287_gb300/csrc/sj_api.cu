@@ -192,7 +192,7 @@ int sj_build_index(const double* pts, int64_t n, int32_t d, double eps, const sj
     sj_options o;
     sj_default_options(&o);
     if (opt) o = *opt;
-    if (o.kernel < SJ_KERNEL_AUTO || o.kernel > SJ_KERNEL_FILTER_BF16X2 || o.indexed_dims < 0 ||
+    if (o.kernel < SJ_KERNEL_AUTO || o.kernel > SJ_KERNEL_FILTER_BF16X2 || o.indexed_dims < SJ_NO_INDEX ||
         o.queries_per_item < 0 || o.page_pairs < 0 || o.max_pairs_hint < 0) {
         set_error("invalid options");
         return SJ_ERR_ARG;

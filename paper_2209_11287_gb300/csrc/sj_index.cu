@@ -97,6 +97,75 @@ __global__ void k_cell_keys(const double* __restrict__ x, int64_t n, int d, Grid
 }
 
 // ---------------------------------------------------------------------------
+// counting sort by cell key, for key spaces of at most a few times n keys
+// ---------------------------------------------------------------------------
+// One count per key, a scan of the counts, a scatter, then the non-empty
+// keys compacted into the cell table.  Lanes of a warp with the same key
+// share one atomic (match_any), so a crowded cell costs one atomic per warp.
+// Inside a cell the points follow the order in which warps reach it, not the
+// input order: every result of the join is a set and does not depend on it.
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;  // keys of the dense path are below 2^31
+
+__global__ void k_key_count(const double* __restrict__ x, int64_t n, int d, GridParams g, uint32_t* key32,
+                            uint32_t* cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    uint32_t key = kNoKey;
+    if (valid) {
+        unsigned long long k64 = 0;
+        for (int k = 0; k < g.m; ++k)
+            k64 += (unsigned long long)cell_coord(x[i * d + g.dims[k]], g.lo[k], g.inv_w, g.ncell[k]) * g.stride[k];
+        key = (uint32_t)k64;
+        key32[i] = key;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], (uint32_t)__popc(peers));
+}
+
+__global__ void k_key_scatter(const uint32_t* __restrict__ key32, int64_t n, const uint32_t* __restrict__ start,
+                              uint32_t* fill, int32_t* perm) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t key = valid ? key32[i] : kNoKey;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t b = 0;
+    if (valid && lane == leader) b = atomicAdd(&fill[key], (uint32_t)__popc(peers));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    if (valid) perm[start[key] + b + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
+__global__ void k_nonempty(const uint32_t* __restrict__ cnt, int64_t K, uint32_t* flags) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < K) flags[k] = cnt[k] != 0u ? 1u : 0u;
+}
+
+// Non-empty key k becomes cell cidx[k]: its key, its first sorted position,
+// and the dense key -> cell table (-1 for empty keys); the last thread writes
+// the cell count M and cell_start[M] = n.
+__global__ void k_bins_to_cells(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ start,
+                                const uint32_t* __restrict__ cidx, int64_t K, int64_t n,
+                                unsigned long long* cell_key, int32_t* cell_start, int32_t* table,
+                                unsigned long long* n_cells) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const bool ne = cnt[k] != 0u;
+    const uint32_t c = cidx[k];
+    table[k] = ne ? (int32_t)c : -1;
+    if (ne) {
+        cell_key[c] = (unsigned long long)k;
+        cell_start[c] = (int32_t)start[k];
+    }
+    if (k == K - 1) {
+        const uint32_t M = c + (ne ? 1u : 0u);
+        *n_cells = M;
+        cell_start[M] = (int32_t)n;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // exclusive scan of uint32 (reduce-then-scan over tiles of 4096)
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
@@ -555,11 +624,6 @@ __device__ __forceinline__ unsigned long long tri_skip(int64_t q, int qmax) {
     return m * m * (T * (T - (T > 0 ? 1ull : 0ull)) / 2) + T * m * r;
 }
 
-__global__ void k_table(const unsigned long long* __restrict__ cell_key, int64_t n_cells, int32_t* table) {
-    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c < n_cells) table[cell_key[c]] = (int32_t)c;
-}
-
 // Per cell: its run count, its item count, and the pair evaluations of its
 // queries.  The canonical candidate count (full neighbourhoods, ordered) is
 // the evaluations when not symmetric, else 2 * evaluations - sum_c |c|^2
@@ -654,7 +718,10 @@ static int choose_grid(Index* ix) {
     }
     // most selective dims first (most cells); ties keep the input order
     std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.ncell > b.ncell; });
-    int want = ix->opt.indexed_dims > 0 ? std::min(ix->opt.indexed_dims, kMaxM) : std::min(d, kMaxM);
+    // SJ_NO_INDEX: no indexed dims, one cell, every pair evaluated (brute force)
+    int want = ix->opt.indexed_dims > 0   ? std::min(ix->opt.indexed_dims, kMaxM)
+               : ix->opt.indexed_dims < 0 ? 0
+                                          : std::min(d, kMaxM);
     std::vector<Cand> take;
     long double prod = 1;
     for (const Cand& c : cand) {
@@ -904,28 +971,66 @@ int build_index(Index* ix, const double* pts) {
         gp.ncell[i] = ix->ncell[i];
         gp.stride[i] = ix->stride[i];
     }
-    k_cell_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, n, d, gp, keys, ix->perm);
-    note_launch();
-    SJ_CK(cudaGetLastError());
-    SJ_TRY(radix_sort_pairs(reinterpret_cast<uint64_t*>(keys), ix->perm, n, ix->key_bits, s));
-
-    // ---- cell table (one sync for the cell count) ----
-    uint32_t *flags = nullptr, *idx = nullptr;
-    SJ_TRY(dev_alloc_t(&flags, (size_t)n, s));
-    SJ_TRY(dev_alloc_t(&idx, (size_t)n, s));
+    // the key space: small enough (at most max(4 n, 2^22) keys) for a
+    // counting sort and a dense key -> cell table
+    long double kspace = 1;
+    for (int i = 0; i < ix->m; ++i) kspace *= (long double)ix->ncell[i];
+    const bool dense = kspace <= (long double)std::max<int64_t>(4 * n, int64_t(1) << 22) &&
+                       kspace < (long double)0x7FFFFFFF;
     unsigned long long* dcount = nullptr;
     SJ_TRY(dev_alloc_t(&dcount, 1, s));
-    k_heads<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, flags);
-    note_launch();
-    SJ_CK(cudaGetLastError());
-    SJ_TRY(scan_exclusive_u32(flags, idx, n, s));
+    uint32_t *flags = nullptr, *idx = nullptr, *bins = nullptr, *key32 = nullptr;
     unsigned long long* ckey_tmp = nullptr;
     int32_t* cstart_tmp = nullptr;
-    SJ_TRY(dev_alloc_t(&ckey_tmp, (size_t)n, s));
-    SJ_TRY(dev_alloc_t(&cstart_tmp, (size_t)n + 1, s));
-    k_cells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, flags, idx, n, ckey_tmp, cstart_tmp, dcount);
-    note_launch();
-    SJ_CK(cudaGetLastError());
+    int32_t* table = nullptr;
+    if (dense) {
+        // ---- counting sort and cell table ----
+        const int64_t K = (int64_t)kspace;
+        const int64_t cap = std::min<int64_t>(n, K);  // non-empty cells at most
+        SJ_TRY(dev_alloc_t(&key32, (size_t)n, s));
+        SJ_TRY(dev_alloc_t(&bins, (size_t)K * 4, s));
+        uint32_t *cnt = bins, *fill = bins + K, *start = bins + 2 * K, *cidx = bins + 3 * K;
+        SJ_CK(cudaMemsetAsync(bins, 0, (size_t)K * 2 * sizeof(uint32_t), s));  // cnt and fill
+        k_key_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, n, d, gp, key32, cnt);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        SJ_TRY(scan_exclusive_u32(cnt, start, K, s));
+        k_key_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(key32, n, start, fill, ix->perm);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        k_nonempty<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(cnt, K, fill);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        SJ_TRY(scan_exclusive_u32(fill, cidx, K, s));
+        SJ_TRY(dev_alloc_t(&ix->cell_key, (size_t)cap, s));
+        SJ_TRY(dev_alloc_t(&ix->cell_start, (size_t)cap + 1, s));
+        SJ_TRY(dev_alloc_t(&table, (size_t)K, s));
+        k_bins_to_cells<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(cnt, start, cidx, K, n, ix->cell_key,
+                                                                    ix->cell_start, table, dcount);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        dev_free(key32, s);
+        dev_free(bins, s);
+        dev_free(keys, s);
+        keys = nullptr;
+    } else {
+        // ---- radix sort and cell table ----
+        k_cell_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, n, d, gp, keys, ix->perm);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        SJ_TRY(radix_sort_pairs(reinterpret_cast<uint64_t*>(keys), ix->perm, n, ix->key_bits, s));
+        SJ_TRY(dev_alloc_t(&flags, (size_t)n, s));
+        SJ_TRY(dev_alloc_t(&idx, (size_t)n, s));
+        k_heads<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, flags);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        SJ_TRY(scan_exclusive_u32(flags, idx, n, s));
+        SJ_TRY(dev_alloc_t(&ckey_tmp, (size_t)n, s));
+        SJ_TRY(dev_alloc_t(&cstart_tmp, (size_t)n + 1, s));
+        k_cells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, flags, idx, n, ckey_tmp, cstart_tmp, dcount);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+    }
 
     // ---- packing (independent of the cell count) ----
     SJ_TRY(dev_alloc_t(&ix->xs, (size_t)n * ix->dp, s));
@@ -960,10 +1065,12 @@ int build_index(Index* ix, const double* pts) {
     SJ_CK(cudaMemcpyAsync(&M, dcount, 8, cudaMemcpyDeviceToHost, s));
     SJ_CK(cudaStreamSynchronize(s));
     ix->n_cells = (int64_t)M;
-    SJ_TRY(dev_alloc_t(&ix->cell_key, (size_t)M, s));
-    SJ_TRY(dev_alloc_t(&ix->cell_start, (size_t)M + 1, s));
-    SJ_CK(cudaMemcpyAsync(ix->cell_key, ckey_tmp, M * 8, cudaMemcpyDeviceToDevice, s));
-    SJ_CK(cudaMemcpyAsync(ix->cell_start, cstart_tmp, (M + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    if (!dense) {
+        SJ_TRY(dev_alloc_t(&ix->cell_key, (size_t)M, s));
+        SJ_TRY(dev_alloc_t(&ix->cell_start, (size_t)M + 1, s));
+        SJ_CK(cudaMemcpyAsync(ix->cell_key, ckey_tmp, M * 8, cudaMemcpyDeviceToDevice, s));
+        SJ_CK(cudaMemcpyAsync(ix->cell_start, cstart_tmp, (M + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    }
     dev_free(ckey_tmp, s);
     dev_free(cstart_tmp, s);
     dev_free(keys, s);
@@ -981,18 +1088,12 @@ int build_index(Index* ix, const double* pts) {
     ep.symmetric = ix->opt.symmetric ? 1 : 0;
     ep.qmax = item_qmax(ix);
     const int64_t Mc = (int64_t)M;
-    // dense key -> cell table when the key space is small (neighbour lookups
-    // become O(1) instead of binary searches over the cell keys)
-    int32_t* table = nullptr;
-    long double kspace = 1;
-    for (int i = 0; i < ix->m; ++i) kspace *= (long double)ix->ncell[i];
-    if (ix->m > 0 && kspace <= (long double)std::max<int64_t>(4 * ix->n, int64_t(1) << 22)) {
-        const size_t K = (size_t)kspace;
-        SJ_TRY(dev_alloc_t(&table, K, s));
-        SJ_CK(cudaMemsetAsync(table, 0xFF, K * sizeof(int32_t), s));
-        k_table<<<(unsigned)((Mc + 255) / 256), 256, 0, s>>>(ix->cell_key, Mc, table);
-        note_launch();
-        SJ_CK(cudaGetLastError());
+    // the dense key -> cell table (from the counting sort) makes neighbour
+    // lookups O(1); otherwise they binary-search the cell keys.  A grid of no
+    // indexed dims has one cell and needs no lookups.
+    if (ix->m == 0 && table) {
+        dev_free(table, s);
+        table = nullptr;
     }
     ep.table = table;
     ep.local_mask = ~0ull;

@@ -193,11 +193,22 @@ __device__ __forceinline__ void emit_direct(WarpStage& st, const JoinParams& P, 
     }
 }
 
-// Minimum resident CTAs per SM requested from the register allocator: the
-// FP32 small-d tile is latency-bound, so it is held to 64 registers.
+// Minimum resident CTAs per SM requested from the register allocator, and
+// candidates per lane, of the FP32 small-d tile (d <= 8): it is
+// latency-bound, so it runs with 2 candidates per lane and 9 CTAs of 4
+// warps per SM (at most 56 registers).  Measured on the uniform 4-D
+// workload (2M points), tile-kernel time: 2 candidates x 9 CTAs 1.196 ms,
+// 2 x 10 1.218, 2 x 8 1.235, 2 x 12 1.521, 2 x 16 1.781, 4 x 8 1.323,
+// 4 x 7 1.372, 4 x 6 1.428.  Compile-time tuning constants.
+#ifndef SJ_CC_F32_MIN_BLOCKS
+#define SJ_CC_F32_MIN_BLOCKS 9
+#endif
+#ifndef SJ_CC_TC_SMALL_D
+#define SJ_CC_TC_SMALL_D 2
+#endif
 template <typename T, int DP>
 constexpr int cc_min_blocks() {
-    return std::is_same<T, float>::value && DP <= 8 ? 8 : 1;
+    return std::is_same<T, float>::value && DP <= 8 ? SJ_CC_F32_MIN_BLOCKS : 1;
 }
 
 template <typename T, int DP, int TC, bool EMIT, int NW, int RUNS>
@@ -422,7 +433,7 @@ __global__ void __launch_bounds__(128) k_recheck(JoinParams P) {
 
 template <typename T, int DP, bool EMIT, int RUNS>
 static int launch_dper(Index* ix, const JoinParams& p) {
-    constexpr int TC = DP <= 8 ? 4 : 2;
+    constexpr int TC = DP > 8 ? 2 : std::is_same<T, float>::value ? SJ_CC_TC_SMALL_D : 4;
     constexpr int NW = cc_warps<CcWarpSmem<T, DP, TC, EMIT, RUNS>>();
     auto kern = k_join_cc<T, DP, TC, EMIT, NW, RUNS>;
     int per_sm = 0;

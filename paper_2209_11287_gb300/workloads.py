@@ -19,6 +19,10 @@ and 2); the workloads below are synthetic stand-ins of the same kinds:
 * ``expo64d``     n=500,000 in d=64, coordinates exponential(lambda=40)
                   clipped to [0,1], eps for a mean selectivity of 50 (stored;
                   calibrated with the oracle).
+* ``brute16d``    n=2^17 in d=16, coordinates exponential(lambda=40) clipped
+                  to [0,1], eps for a mean selectivity of 50 (stored;
+                  calibrated with the oracle): the brute-force comparison of
+                  Sec. IV (Fig. 3), joined without an index.
 * ``batched``     4096 independent uniform instances: n log-uniform in
                   [256, 65536], d from {2,4,8,16,32}, eps per instance for a
                   mean of 32 neighbours.
@@ -97,6 +101,11 @@ def expo64d(n: int = 500_000, seed: int = 0, eps: float | None = None) -> Worklo
     return Workload("expo64d", x, _eps_for("expo64d", n, 64, 500_000, eps), seed)
 
 
+def brute16d(n: int = 1 << 17, seed: int = 0, eps: float | None = None) -> Workload:
+    x = np.minimum(_rng(seed).exponential(1.0 / 40.0, size=(n, 16)), 1.0)
+    return Workload("brute16d", x, _eps_for("brute16d", n, 16, 1 << 17, eps), seed)
+
+
 def _eps_for(name: str, n: int, d: int, n_full: int, eps):
     if eps is not None:
         return float(eps)
@@ -144,4 +153,5 @@ CONFIGS = {
     "uniform4d": uniform4d,
     "mixture16d": mixture16d,
     "expo64d": expo64d,
+    "brute16d": brute16d,
 }

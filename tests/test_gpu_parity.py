@@ -264,3 +264,32 @@ def test_bounded_wait_gives_up():
     ref = oracle.join(w.points, w.eps)
     got, _, _ = gpu_join(w.points, w.eps, "filter_bf16x3")
     assert_same_set(w.points, w.eps, ref, got)
+
+
+@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x2"])
+@pytest.mark.parametrize("eps", [2e-4, 0.02], ids=["sparse_keys_radix_sort", "dense_keys_counting_sort"])
+def test_key_space_paths(kernel, eps):
+    """The index sorts by cell key with an LSD radix sort when the key space
+    is large (2e-4: 5000^2 keys for 3000 points) and with a counting sort
+    plus a dense key table when it is small (0.02: 51^2 keys); both give the
+    oracle's set."""
+    x = np.random.Generator(np.random.PCG64(123)).random((3000, 2))
+    ref = oracle.join(x, eps)
+    got, _, st = gpu_join(x, eps, kernel)
+    assert_same_set(x, eps, ref, got)
+    assert st["n_candidates"] == oracle.grid_candidate_count(x, eps * (1.0 + 2.0 ** -20))
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_no_index_brute_force(kernel):
+    """indexed_dims = SJ_NO_INDEX: one cell, every pair evaluated (the
+    brute-force comparison of Sec. IV); the set is the oracle's, the
+    candidate count n^2 and the evaluations those of one triangle (or all
+    n^2 where a kernel evaluates the full self cell)."""
+    w = workloads.brute16d(n=3000, seed=4)
+    ref = oracle.join(w.points, w.eps)
+    got, _, st = gpu_join(w.points, w.eps, kernel, indexed_dims=binding.SJ_NO_INDEX)
+    assert_same_set(w.points, w.eps, ref, got)
+    assert st["m"] == 0 and st["n_cells"] == 1
+    assert st["n_candidates"] == w.n * w.n
+    assert w.n * (w.n + 1) // 2 <= st["n_evaluated"] <= w.n * w.n
