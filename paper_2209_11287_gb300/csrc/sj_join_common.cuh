@@ -259,6 +259,75 @@ __device__ __forceinline__ bool band_push(const JoinParams& P, int lane, bool wa
     return true;
 }
 
+// Per-warp staging of recheck-queue entries: lanes append (query sorted
+// position, candidate sorted position | mirror) to a shared-memory list, and
+// the list goes to the global queue with one atomic per flush (when full and
+// at the end of every work item), so no tile waits on a queue atomic per
+// entry.  Entries past the queue's capacity are re-decided in the flush with
+// the decision rule and emitted (route R: the item's instance offset and
+// eps^2).
+constexpr int kBandStage = 64;
+struct BandStage {
+    int2* e;  // kBandStage slots of this warp
+    int cnt;  // warp-uniform fill
+};
+
+template <bool EMIT>
+__device__ __forceinline__ void band_stage_flush(BandStage& bs, WarpStage& st, const JoinParams& P,
+                                                 const ItemRoute& R, int lane, unsigned long long& rechecked) {
+    __syncwarp();
+    if (bs.cnt == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&P.counters[3], (unsigned long long)bs.cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i0 = 0; i0 < bs.cnt; i0 += 32) {
+        const int i = i0 + lane;
+        int nout = 0;
+        int32_t qid = 0, cid = 0;
+        double dist = 0.0;
+        if (i < bs.cnt) {
+            const int2 e = bs.e[i];
+            const unsigned long long pos = base + (unsigned long long)i;
+            if (pos < P.band_cap) {
+                P.band[pos] = e;
+            } else {  // queue full: decide here
+                const int32_t cs = (int32_t)((uint32_t)e.y & ~kMirrorBit);
+                const bool mir = ((uint32_t)e.y & kMirrorBit) != 0;
+                const double s = direct_sq(P.xs + (int64_t)e.x * P.dp, P.xs + (int64_t)cs * P.dp, P.d);
+                ++rechecked;
+                if (s <= R.e2) {
+                    nout = mir ? 2 : 1;
+                    qid = (int32_t)(P.perm[e.x] - R.off);
+                    cid = (int32_t)(P.perm[cs] - R.off);
+                    dist = sqrt(s);
+                }
+            }
+        }
+        if constexpr (EMIT)
+            stage_emit(st, P, lane, nout, qid, cid, dist);
+        else
+            stage_emit_pairs(st, P, lane, nout, qid, cid);
+    }
+    __syncwarp();
+    bs.cnt = 0;
+}
+
+// Warp-collective: lanes with `want` append their entry to the warp's band
+// stage (flushed first when it could overflow).
+template <bool EMIT>
+__device__ __forceinline__ void band_stage_push(BandStage& bs, WarpStage& st, const JoinParams& P,
+                                                const ItemRoute& R, int lane, bool want, int32_t qs, int32_t cs,
+                                                bool mirror, unsigned long long& rechecked) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (m == 0) return;
+    const int n = __popc(m);
+    if (bs.cnt + n > kBandStage) band_stage_flush<EMIT>(bs, st, P, R, lane, rechecked);
+    if (want)
+        bs.e[bs.cnt + __popc(m & ((1u << lane) - 1u))] =
+            make_int2(qs, (int32_t)((uint32_t)cs | (mirror ? kMirrorBit : 0u)));
+    bs.cnt += n;
+}
+
 // Warp-wide exclusive prefix sum of v; *total gets the sum.
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total) {
     int x = v;

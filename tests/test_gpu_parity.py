@@ -293,3 +293,21 @@ def test_no_index_brute_force(kernel):
     assert st["m"] == 0 and st["n_cells"] == 1
     assert st["n_candidates"] == w.n * w.n
     assert w.n * (w.n + 1) // 2 <= st["n_evaluated"] <= w.n * w.n
+
+
+@pytest.mark.parametrize("kernel", ["filter_f32", "filter_bf16x2"])
+@pytest.mark.parametrize("emit", [False, True], ids=["pairs", "distances"])
+def test_recheck_queue_overflow(kernel, emit):
+    """One point far from the rest makes the kernel coordinates' norms huge,
+    so the certified bound covers every evaluated pair: all of them go to the
+    recheck queue, more than it holds (2^20 entries or 1/64 of the
+    evaluations), and the overflow is re-decided inside the tile kernel."""
+    g = np.random.Generator(np.random.PCG64(31))
+    x = np.concatenate([g.random((20000, 2)), [[1.0e4, 1.0e4]]])
+    eps = 0.04
+    ref, rd = oracle.join(x, eps, with_dist=True)
+    got, dists, st = gpu_join(x, eps, kernel, emit_distances=emit)
+    assert_same_set(x, eps, ref, got)
+    assert st["n_rechecked"] > (1 << 20)
+    if emit:
+        assert np.array_equal(dists, rd)
