@@ -50,7 +50,6 @@ struct CcWarpSmem {
                                                       // of the queries, slot << 4 | query
     int2 stage[kStage];
     double sdist[EMIT ? kStage : 1];
-    int2 bstage[kBandStage];  // recheck-queue entries awaiting a flush
 };
 
 // Maybe-in bitmasks of TC candidates against all queries of the item, d <= 8:
@@ -105,7 +104,7 @@ __device__ __forceinline__ void tile_fused(const ItemSmem<T, DP, RUNS>& S, int Q
 // certified bound straddles eps) are queued for the binary64 recheck, one
 // per lane per round, or re-decided here when the queue is full.
 template <int TC>
-__device__ __forceinline__ void emit_direct(WarpStage& st, BandStage& bs, const JoinParams& P, const int32_t* cperm,
+__device__ __forceinline__ void emit_direct(WarpStage& st, const JoinParams& P, const int32_t* cperm,
                                             const uint8_t* cmir, const int32_t* qids, const ItemRoute& R,
                                             const Item& I, int lane, const int32_t (&j)[TC],
                                             const uint32_t (&bits)[TC], const uint32_t (&cbits)[TC],
@@ -178,7 +177,19 @@ __device__ __forceinline__ void emit_direct(WarpStage& st, BandStage& bs, const 
         if (!__any_sync(0xffffffffu, want)) break;
         const int fl = want ? cmir[slot] : 0;
         const bool mir = fl == 1 || (fl == 2 && jj != I.q0 + q);
-        band_stage_push<false>(bs, st, P, R, lane, want, I.q0 + q, jj, mir, rechecked);
+        const bool queued = band_push(P, lane, want, I.q0 + q, jj, mir);  // rare: no reservation
+        int no = 0;
+        int32_t qid = 0, cid = 0;
+        if (want && !queued) {  // queue full: decide here
+            const double s = direct_sq(P.xs + (int64_t)(I.q0 + q) * P.dp, P.xs + (int64_t)jj * P.dp, P.d);
+            ++rechecked;
+            if (s <= R.e2) {
+                no = mir ? 2 : 1;
+                qid = (int32_t)(qids[q] - R.off);
+                cid = (int32_t)(cperm[slot] - R.off);
+            }
+        }
+        stage_emit_pairs(st, P, lane, no, qid, cid);
     }
 }
 
@@ -215,7 +226,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
     CcWarpSmem<T, DP, TC, EMIT, RUNS>& W = smem[wid];
     ItemSmem<T, DP, RUNS>& S = W.it;
     WarpStage st{W.stage, EMIT ? W.sdist : nullptr, 0, 0};
-    BandStage bs{W.bstage, 0};
+    BandQ bq{0, 0};
     unsigned long long rechecked = 0;
 
     long long next = 0;
@@ -308,7 +319,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                 cbits[t] &= tri_mask[t];
             }
             if constexpr (!EMIT) {
-                emit_direct<TC>(st, bs, P, W.cperm, W.cmir, S.qid, R, I, lane, j, bits, cbits, rechecked);
+                emit_direct<TC>(st, P, W.cperm, W.cmir, S.qid, R, I, lane, j, bits, cbits, rechecked);
             } else {
             // with distances every maybe-in pair is re-decided in binary64: the
             // pairs are compacted with one warp scan per half of the queries and
@@ -334,27 +345,41 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
             __syncwarp();
             for (int e0 = 0; e0 < total; e0 += 32) {
                 const int e = e0 + lane;
+                int nout = 0;
+                int32_t qid = 0, cid = 0;
+                double dist = 0.0;
                 bool band = false, mir = false;
                 int q = 0;
-                int32_t jj = 0;
+                int64_t jj = 0;
                 if (e < total) {
                     const int ent = W.list[e];
                     const int slot = (ent >> 4) & 0x7FF;
                     q = ent & 15;
                     jj = W.cj[slot];
                     const int fl = W.cmir[slot];
-                    mir = fl == 1 || (fl == 2 && jj != I.q0 + q);
+                    mir = fl == 1 || (fl == 2 && jj != (int64_t)(I.q0 + q));
                     band = true;
                 }
-                band_stage_push<true>(bs, st, P, R, lane, band, I.q0 + q, jj, mir, rechecked);
+                const bool queued = band_push_q(bq, P, lane, band, I.q0 + q, (int32_t)jj, mir);
+                if (band && !queued) {  // queue full: decide here
+                    const double s = direct_sq(P.xs + (int64_t)(I.q0 + q) * DP, P.xs + jj * DP, P.d);
+                    ++rechecked;
+                    if (s <= R.e2) {
+                        nout = mir ? 2 : 1;
+                        qid = (int32_t)(S.qid[q] - R.off);
+                        cid = (int32_t)(W.cperm[(W.list[e] >> 4) & 0x7FF] - R.off);
+                        dist = sqrt(s);
+                    }
+                }
+                stage_emit(st, P, lane, nout, qid, cid, dist);
             }
             __syncwarp();
             }
             }
         }
-        band_stage_flush<EMIT>(bs, st, P, R, lane, rechecked);  // before the next item's route
         __syncwarp();
     }
+    band_q_close(bq, P, lane);
     stage_flush(st, P, lane);
     for (int o = 16; o > 0; o >>= 1) rechecked += __shfl_down_sync(0xffffffffu, rechecked, o);
     if (lane == 0 && rechecked) atomicAdd(&P.counters[2], rechecked);
@@ -373,15 +398,18 @@ __global__ void __launch_bounds__(128) k_recheck(JoinParams P) {
     const unsigned long long count = queued < P.band_cap ? queued : P.band_cap;
     const unsigned long long gw = (unsigned long long)blockIdx.x * 4 + wid;
     const unsigned long long nw = (unsigned long long)gridDim.x * 4;
+    unsigned long long nvalid = 0;
     for (unsigned long long b = gw * 32; b < count; b += nw * 32) {
         const unsigned long long i = b + lane;
         int nout = 0;
         int32_t qid = 0, cid = 0;
         double dist = 0.0;
-        if (i < count) {
-            const int2 e = P.band[i];
-            const int32_t qs = e.x;
-            const int32_t cs = (int32_t)((uint32_t)e.y & ~kMirrorBit);
+        const int2 e = i < count ? P.band[i] : make_int2(-1, -1);
+        const int32_t qs = e.x;
+        const int32_t cs = (int32_t)((uint32_t)e.y & ~kMirrorBit);
+        // closed (unfilled) reservation slots hold (-1, -1)
+        if (qs >= 0 && qs < P.n_points && cs >= 0 && cs < P.n_points) {
+            ++nvalid;
             const bool mir = ((uint32_t)e.y & kMirrorBit) != 0;
             const double s = direct_sq(P.xs + (int64_t)qs * DP, P.xs + (int64_t)cs * DP, P.d);
             if (P.batch) {  // lanes may serve different instances: one lane, one write
@@ -405,7 +433,8 @@ __global__ void __launch_bounds__(128) k_recheck(JoinParams P) {
             stage_emit_pairs(st, P, lane, nout, qid, cid);
     }
     stage_flush(st, P, lane);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && count) atomicAdd(&P.counters[2], count);
+    for (int o = 16; o > 0; o >>= 1) nvalid += __shfl_down_sync(0xffffffffu, nvalid, o);
+    if (lane == 0 && nvalid) atomicAdd(&P.counters[2], nvalid);
 }
 
 template <typename T, int DP, bool EMIT, int RUNS>
@@ -493,6 +522,7 @@ JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist) {
     p.items = ix->items;
     p.runs = ix->runs;
     p.n_items = ix->n_items;
+    p.n_points = ix->n;
     p.counters = ix->counters;
     p.out_pairs = out.out_pairs;
     p.out_dist = out.out_dist;

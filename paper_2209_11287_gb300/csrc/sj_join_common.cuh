@@ -19,6 +19,7 @@ struct JoinParams {
     const Item* items;
     const Run* runs;
     long long n_items;
+    long long n_points;            // packed points (bound of every queued sorted position)
     unsigned long long* counters;  // [0] item queue, [1] result cursor, [2] rechecked
     int2* out_pairs;               // the result pool (pages are views of it)
     double* out_dist;              // distances, or null
@@ -259,73 +260,53 @@ __device__ __forceinline__ bool band_push(const JoinParams& P, int lane, bool wa
     return true;
 }
 
-// Per-warp staging of recheck-queue entries: lanes append (query sorted
-// position, candidate sorted position | mirror) to a shared-memory list, and
-// the list goes to the global queue with one atomic per flush (when full and
-// at the end of every work item), so no tile waits on a queue atomic per
-// entry.  Entries past the queue's capacity are re-decided in the flush with
-// the decision rule and emitted (route R: the item's instance offset and
-// eps^2).
-constexpr int kBandStage = 64;
-struct BandStage {
-    int2* e;  // kBandStage slots of this warp
-    int cnt;  // warp-uniform fill
+// Per-warp reservation in the recheck queue: a warp takes queue slots in
+// chunks of kBandChunk with one atomic and fills them in order, so a tile
+// waits on a queue atomic once per chunk rather than once per round of
+// entries.  Slots a warp reserved but did not fill are closed with the
+// sentinel (-1, -1) before the kernel ends; the recheck kernel skips entries
+// outside [0, n).
+constexpr int kBandChunk = 64;
+struct BandQ {
+    unsigned long long base;  // next reserved slot
+    int left;                 // reserved slots left (warp-uniform)
 };
 
-template <bool EMIT>
-__device__ __forceinline__ void band_stage_flush(BandStage& bs, WarpStage& st, const JoinParams& P,
-                                                 const ItemRoute& R, int lane, unsigned long long& rechecked) {
-    __syncwarp();
-    if (bs.cnt == 0) return;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&P.counters[3], (unsigned long long)bs.cnt);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (int i0 = 0; i0 < bs.cnt; i0 += 32) {
-        const int i = i0 + lane;
-        int nout = 0;
-        int32_t qid = 0, cid = 0;
-        double dist = 0.0;
-        if (i < bs.cnt) {
-            const int2 e = bs.e[i];
-            const unsigned long long pos = base + (unsigned long long)i;
-            if (pos < P.band_cap) {
-                P.band[pos] = e;
-            } else {  // queue full: decide here
-                const int32_t cs = (int32_t)((uint32_t)e.y & ~kMirrorBit);
-                const bool mir = ((uint32_t)e.y & kMirrorBit) != 0;
-                const double s = direct_sq(P.xs + (int64_t)e.x * P.dp, P.xs + (int64_t)cs * P.dp, P.d);
-                ++rechecked;
-                if (s <= R.e2) {
-                    nout = mir ? 2 : 1;
-                    qid = (int32_t)(P.perm[e.x] - R.off);
-                    cid = (int32_t)(P.perm[cs] - R.off);
-                    dist = sqrt(s);
-                }
-            }
-        }
-        if constexpr (EMIT)
-            stage_emit(st, P, lane, nout, qid, cid, dist);
-        else
-            stage_emit_pairs(st, P, lane, nout, qid, cid);
+// Warp-collective: lanes with `want` queue (qs, cs | mirror); returns, per
+// lane, whether its entry found room (if not, the queue is full and the
+// caller re-decides the pair itself).
+__device__ __forceinline__ bool band_push_q(BandQ& bq, const JoinParams& P, int lane, bool want, int32_t qs,
+                                            int32_t cs, bool mirror) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (m == 0) return false;
+    const int n = __popc(m);
+    const int r = __popc(m & ((1u << lane) - 1u));
+    unsigned long long pos;
+    if (n <= bq.left) {
+        pos = bq.base + (unsigned long long)r;
+        bq.base += (unsigned long long)n;
+        bq.left -= n;
+    } else {  // the rest of this chunk, then a fresh one (n <= 32 < kBandChunk)
+        unsigned long long fresh = 0;
+        if (lane == 0) fresh = atomicAdd(&P.counters[3], (unsigned long long)kBandChunk);
+        fresh = __shfl_sync(0xffffffffu, fresh, 0);
+        pos = r < bq.left ? bq.base + (unsigned long long)r : fresh + (unsigned long long)(r - bq.left);
+        const int used = n - bq.left;
+        bq.base = fresh + (unsigned long long)used;
+        bq.left = kBandChunk - used;
     }
-    __syncwarp();
-    bs.cnt = 0;
+    if (!want || pos >= P.band_cap) return false;
+    P.band[pos] = make_int2(qs, (int32_t)((uint32_t)cs | (mirror ? kMirrorBit : 0u)));
+    return true;
 }
 
-// Warp-collective: lanes with `want` append their entry to the warp's band
-// stage (flushed first when it could overflow).
-template <bool EMIT>
-__device__ __forceinline__ void band_stage_push(BandStage& bs, WarpStage& st, const JoinParams& P,
-                                                const ItemRoute& R, int lane, bool want, int32_t qs, int32_t cs,
-                                                bool mirror, unsigned long long& rechecked) {
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (m == 0) return;
-    const int n = __popc(m);
-    if (bs.cnt + n > kBandStage) band_stage_flush<EMIT>(bs, st, P, R, lane, rechecked);
-    if (want)
-        bs.e[bs.cnt + __popc(m & ((1u << lane) - 1u))] =
-            make_int2(qs, (int32_t)((uint32_t)cs | (mirror ? kMirrorBit : 0u)));
-    bs.cnt += n;
+// Closes the warp's reservation: its unfilled slots get the sentinel.
+__device__ __forceinline__ void band_q_close(BandQ& bq, const JoinParams& P, int lane) {
+    for (int i = lane; i < bq.left; i += 32) {
+        const unsigned long long pos = bq.base + (unsigned long long)i;
+        if (pos < P.band_cap) P.band[pos] = make_int2(-1, -1);
+    }
+    bq.left = 0;
 }
 
 // Warp-wide exclusive prefix sum of v; *total gets the sum.

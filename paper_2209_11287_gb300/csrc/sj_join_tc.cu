@@ -106,7 +106,6 @@ struct TcSmem {
     uint8_t rfl[kMaxRuns];
     int2 stage[EPI][kStage];
     double sdist[EPI][EMIT ? kStage : 1];
-    int2 bstage[EPI][kBandStage];  // per epilogue warp: recheck-queue entries awaiting a flush
     uint16_t hits[EPI][32][32];  // per epilogue warp: maybe-in entries of a 32-column chunk, per lane
 };
 
@@ -492,7 +491,7 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
         const float* __restrict__ TO = static_cast<const float*>(P.thr_out);
         const float* __restrict__ TI = static_cast<const float*>(P.thr_in);
         WarpStage st{S.stage[ew], EMIT ? S.sdist[ew] : nullptr, 0, 0};
-        BandStage bs{S.bstage[ew], 0};
+        BandQ bq{0, 0};
         unsigned long long rechecked = 0;
         uint32_t it_i = 0, it_ph = 0, m_i = 0, m_ph = 0, acc = 0, acc_ph = 0;
         for (;;) {
@@ -587,6 +586,7 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                     for (int i = 0; __any_sync(0xffffffffu, i < hn); ++i) {
                         int nout = 0;
                         int32_t qid = 0, cid = 0, qs = 0;
+                        double dist = 0.0;
                         bool band = false, mir = false;
                         if (i < hn) {
                             const uint32_t e = hits[i][lane];
@@ -600,9 +600,19 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                                 band = true;
                             }
                         }
-                        band_stage_push<EMIT>(bs, st, P, R, lane, band, qs, cp, mir, rechecked);
+                        const bool queued = band_push_q(bq, P, lane, band, qs, cp, mir);
+                        if (band && !queued) {  // queue full: decide here
+                            const double s2 = direct_sq(P.xs + (int64_t)qs * P.dp, P.xs + (int64_t)cp * P.dp, P.d);
+                            ++rechecked;
+                            if (s2 <= R.e2) {
+                                nout = mir ? 2 : 1;
+                                qid = (int32_t)(qperm[qs - X.qa] - R.off);
+                                cid = (int32_t)(cpid - R.off);
+                                if (EMIT) dist = sqrt(s2);
+                            }
+                        }
                         if (EMIT)
-                            stage_emit(st, P, lane, nout, qid, cid, 0.0);
+                            stage_emit(st, P, lane, nout, qid, cid, dist);
                         else
                             stage_emit_pairs(st, P, lane, nout, qid, cid);
                     }
@@ -613,11 +623,11 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                 if (++acc == 2) acc = 0, acc_ph ^= 1u;
             }
             if (fail) break;
-            band_stage_flush<EMIT>(bs, st, P, R, lane, rechecked);  // before the next item's route
             __syncwarp();
             if (lane == 0) bar_arrive(&S.item_empty[it_i]);
             if (++it_i == 2) it_i = 0, it_ph ^= 1u;
         }
+        band_q_close(bq, P, lane);
         stage_flush(st, P, lane);
         for (int o = 16; o > 0; o >>= 1) rechecked += __shfl_down_sync(0xffffffffu, rechecked, o);
         if (lane == 0 && rechecked) atomicAdd(&P.counters[2], rechecked);
