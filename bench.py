@@ -75,6 +75,18 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(v: float, world: int, dev) -> float:
+    """The maximum of v over all ranks (the slowest replica's time); v itself
+    on one rank.  dev: the device of the process group's tensors."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 WORKLOAD_TEXT = {
     "uniform4d": "points i.i.d. uniform in [0,1]^4, eps from the 4-ball volume for a mean of 64 neighbours",
     "uniform2d": "points i.i.d. uniform in [0,1]^2, eps = sqrt(32 / (pi n))",
@@ -199,13 +211,8 @@ def run_native(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(v: float) -> float:
+        return max_over_ranks(v, world, dev)
 
     def one_step(opt, host=None, host_out=None):
         h = binding.sj_build_index(pts if host is None else host, w.eps, opt, stream)
@@ -260,13 +267,13 @@ def run_native(args):
         launches = binding.sj_kernel_launches() - launches0
         clocks = sampler.stop() if vi == len(variants) - 1 else None
         times = [a.elapsed_time(b) for a, b in ev]
-        ms = max_over_ranks(sum(times) / len(times))
+        ms = slowest(sum(times) / len(times))
         count, cand, evald, rech, reruns, _, kused = info
         results[kname] = {"kernel": knames.get(kused, kname), "ms_per_step": ms, "count": count,
                           "n_candidates": cand, "n_evaluated": evald,
                           "n_rechecked": rech, "reruns": reruns, "launches": launches, "clocks": clocks,
                           "ms_min": min(times), "ms_max": max(times),
-                          "tile_ms": max_over_ranks(statistics.mean(tile_ms))}
+                          "tile_ms": slowest(statistics.mean(tile_ms))}
 
     # the distance-tile kernel's duration: CUDA events the library records on
     # its stream around the launch, averaged over the timed steps
@@ -287,7 +294,7 @@ def run_native(args):
         one_step(opt, host_pts, host_out)
         torch.cuda.synchronize(dev)
         t_e2e.append(time.perf_counter() - t0)
-    e2e_s = max_over_ranks(statistics.mean(t_e2e))
+    e2e_s = slowest(statistics.mean(t_e2e))
 
     if rank == 0:
         line = make_line(args, w, results, variants, world, kern_ms, e2e_s, head)
