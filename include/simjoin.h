@@ -206,6 +206,34 @@ SJ_API void sj_result_free(sj_result* r);
 /* Releases `count` results in one call (e.g. the results of sj_join_batch). */
 SJ_API void sj_results_free(sj_result* results, int32_t count);
 
+/*
+ * Results larger than device memory.  Runs the self-join of a built index
+ * (the kernel and decision rule of sj_self_join, without distances) in
+ * rounds over consecutive ranges of work items; each round's pairs land in
+ * one of two device buffers of `device_pairs` pairs (at least 1024) and are
+ * copied to `host_pairs` on a second stream while the next round runs
+ * (overlapped when host_pairs is pinned).  The range of the next round is
+ * sized from the last round's pairs per work item to fill about 3/4 of a
+ * buffer; a round whose pairs do not fit is run again on half its range.
+ * The paper batches its result transfers for the same reason (Sec. III-B).
+ *
+ *   host_pairs     host memory with room for host_capacity pairs, (i, j) int32
+ *                  interleaved, input indices, unspecified order
+ *   count_out      |R|, exact even when it exceeds host_capacity (then
+ *                  SJ_ERR_RESULT_OVERFLOW is returned and host_pairs holds
+ *                  host_capacity of the pairs)
+ *   rounds_out     rounds run (may be NULL)
+ *
+ * Device memory used beyond the index: 2 x device_pairs x 8 bytes plus the
+ * recheck queue.  Synchronous with respect to the host.  Errors: SJ_ERR_ARG
+ * (NULL handle or count_out, device memory for host_pairs, device_pairs <
+ * 1024), SJ_ERR_RESULT_OVERFLOW (also when a single work item yields more
+ * than device_pairs pairs; count_out is then 0), SJ_ERR_OOM, SJ_ERR_CUDA,
+ * SJ_ERR_TIMEOUT.
+ */
+SJ_API int sj_self_join_to_host(sj_handle h, int32_t* host_pairs, int64_t host_capacity, int64_t device_pairs,
+                                int64_t* count_out, int32_t* rounds_out);
+
 /* Convenience: build + join + destroy in one call. */
 SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt, void* stream,
             sj_result* out);

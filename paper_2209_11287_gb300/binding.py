@@ -155,6 +155,8 @@ def load():
         lib.sj_tune_lookup.argtypes = [ctypes.c_char_p, _i32, _i32, _i64, ctypes.POINTER(_i32),
                                        ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
         lib.sj_tune_lookup.restype = ctypes.c_int
+        lib.sj_self_join_to_host.argtypes = [_vp, _vp, _i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i32)]
+        lib.sj_self_join_to_host.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -248,6 +250,24 @@ def sj_self_join(handle) -> sj_result:
     r = sj_result()
     _check(load().sj_self_join(handle, ctypes.byref(r)))
     return r
+
+
+def sj_self_join_to_host(handle, pairs_out, device_pairs: int):
+    """Join in rounds into ``pairs_out`` (host int32 array or CPU tensor of
+    shape (capacity, 2); pinned memory overlaps the copies) through device
+    buffers of ``device_pairs`` pairs.  Returns (count, rounds); raises on
+    overflow (the exception's status is SJ_ERR_RESULT_OVERFLOW)."""
+    if hasattr(pairs_out, "data_ptr"):
+        if str(pairs_out.dtype) != "torch.int32" or not pairs_out.is_contiguous() or pairs_out.is_cuda:
+            raise ValueError("pairs_out must be a contiguous int32 CPU tensor")
+        ptr, cap = pairs_out.data_ptr(), pairs_out.numel() // 2
+    else:
+        if pairs_out.dtype != np.int32 or not pairs_out.flags.c_contiguous:
+            raise ValueError("pairs_out must be a contiguous int32 array")
+        ptr, cap = pairs_out.ctypes.data, pairs_out.size // 2
+    cnt, rounds = _i64(0), _i32(0)
+    _check(load().sj_self_join_to_host(handle, ptr, cap, int(device_pairs), ctypes.byref(cnt), ctypes.byref(rounds)))
+    return int(cnt.value), int(rounds.value)
 
 
 def sj_result_copy(result: sj_result, pairs_out=None, dist_out=None):

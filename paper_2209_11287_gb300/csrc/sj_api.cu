@@ -374,6 +374,146 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
     return st;
 }
 
+int sj_self_join_to_host(sj_handle h, int32_t* host_pairs, int64_t host_capacity, int64_t device_pairs,
+                         int64_t* count_out, int32_t* rounds_out) {
+    clear_error();
+    if (!h || !count_out || host_capacity < 0 || (host_capacity > 0 && !host_pairs) || device_pairs < 1024) {
+        set_error("invalid arguments (device_pairs must be at least 1024)");
+        return SJ_ERR_ARG;
+    }
+    if (host_pairs && is_device_pointer(host_pairs)) {
+        set_error("host_pairs must be host memory");
+        return SJ_ERR_ARG;
+    }
+    *count_out = 0;
+    if (rounds_out) *rounds_out = 0;
+    sj_index* ix = h;
+    cudaStream_t s = ix->stream;
+    const int64_t n_items = ix->n_items;
+    const unsigned long long ev = (unsigned long long)std::max<int64_t>(ix->n_evaluated, 1);
+    unsigned long long band_cap = std::min<unsigned long long>(std::max<unsigned long long>(1ull << 20, ev / 64), ev);
+    int2* pool[2] = {nullptr, nullptr};
+    int2* band = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t done[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    int st = SJ_OK;
+    if ((st = dev_alloc_t(&pool[0], (size_t)device_pairs, s)) == SJ_OK &&
+        (st = dev_alloc_t(&pool[1], (size_t)device_pairs, s)) == SJ_OK)
+        st = dev_alloc_t(&band, (size_t)band_cap, s);
+    if (st == SJ_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            set_error("set-up: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+        }
+    }
+    // rounds over consecutive work-item ranges [i0, i0 + L); a round whose
+    // pairs exceed the buffer is run again on half the range
+    unsigned long long total = 0, rechecked = 0;
+    int64_t i0 = 0, L = std::max<int64_t>(1, n_items / 16);
+    int rounds = 0, b = 0;
+    bool copied_pending[2] = {false, false};
+    const int64_t keep_items = ix->n_items;
+    while (st == SJ_OK && i0 < n_items) {
+        const int64_t i1 = std::min<int64_t>(n_items, i0 + L);
+        if (copied_pending[b] && cudaStreamWaitEvent(s, copied[b], 0) != cudaSuccess) st = SJ_ERR_CUDA;
+        unsigned long long c[kCounters] = {};
+        c[0] = (unsigned long long)i0;  // the item queue starts at the range
+        cudaError_t e = st == SJ_OK ? cudaMemcpyAsync(ix->counters, c, sizeof c, cudaMemcpyHostToDevice, s)
+                                    : cudaErrorUnknown;
+        if (e != cudaSuccess) {
+            if (st == SJ_OK) set_error("round set-up: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+            break;
+        }
+        JoinOut jo;
+        jo.out_pairs = pool[b];
+        jo.capacity = (unsigned long long)device_pairs;
+        jo.band = band;
+        jo.band_cap = band_cap;
+        ix->n_items = i1;  // the kernels stop at the range's end
+        if (ix->kernel == SJ_KERNEL_FP64_DMMA)
+            st = launch_join_dmma(ix, jo, 0);
+        else if (is_tensor_kernel(ix->kernel))
+            st = launch_join_tc(ix, jo, 0);
+        else
+            st = launch_join_cc(ix, jo, 0);
+        if (st == SJ_OK) st = launch_recheck(ix, jo, 0);
+        ix->n_items = keep_items;
+        if (st != SJ_OK) break;
+        e = cudaMemcpyAsync(c, ix->counters, sizeof c, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("round: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+            break;
+        }
+        if ((int)c[4] != 0) {
+            set_error("a bounded wait in the tensor-core kernel expired");
+            st = SJ_ERR_TIMEOUT;
+            break;
+        }
+        const unsigned long long got = c[1];
+        if (got > (unsigned long long)device_pairs) {  // did not fit: half the range again
+            if (L == 1) {
+                set_error("work item %lld alone yields %llu pairs, more than device_pairs = %lld", (long long)i0,
+                          got, (long long)device_pairs);
+                st = SJ_ERR_RESULT_OVERFLOW;
+                break;
+            }
+            L = std::max<int64_t>(1, L / 2);
+            continue;
+        }
+        // copy this round's pairs out on the copy stream while the next round runs
+        if (host_pairs && total < (unsigned long long)host_capacity && got > 0) {
+            const unsigned long long room = (unsigned long long)host_capacity - total;
+            const unsigned long long cnt = got < room ? got : room;
+            e = cudaEventRecord(done[b], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, done[b], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(host_pairs + 2 * total, pool[b], cnt * sizeof(int2), cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
+            if (e != cudaSuccess) {
+                set_error("result copy: %s", cudaGetErrorString(e));
+                st = SJ_ERR_CUDA;
+                break;
+            }
+            copied_pending[b] = true;
+        }
+        total += got;
+        rechecked += c[2];
+        ++rounds;
+        // next range: aim at 3/4 of the buffer from this round's pairs per item
+        const double per_item = (double)got / (double)(i1 - i0);
+        const int64_t next = per_item > 0 ? (int64_t)(0.75 * (double)device_pairs / per_item) : 4 * L;
+        L = std::max<int64_t>(1, std::min<int64_t>(next, 4 * L));
+        i0 = i1;
+        b ^= 1;
+    }
+    if (cs) cudaStreamSynchronize(cs);
+    for (int k = 0; k < 2; ++k) {
+        if (done[k]) cudaEventDestroy(done[k]);
+        if (copied[k]) cudaEventDestroy(copied[k]);
+        dev_free(pool[k], s);
+    }
+    dev_free(band, s);
+    if (cs) cudaStreamDestroy(cs);
+    cudaStreamSynchronize(s);
+    if (st != SJ_OK) return st;
+    *count_out = (int64_t)total;
+    if (rounds_out) *rounds_out = rounds;
+    if (total > (unsigned long long)host_capacity) {
+        set_error("result of %llu pairs exceeds host_capacity = %lld (the first pairs were copied)", total,
+                  (long long)host_capacity);
+        return SJ_ERR_RESULT_OVERFLOW;
+    }
+    return SJ_OK;
+}
+
 int sj_self_join(sj_handle h, sj_result* out) {
     clear_error();
     if (!h || !out) {

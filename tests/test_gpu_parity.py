@@ -311,3 +311,30 @@ def test_recheck_queue_overflow(kernel, emit):
     assert st["n_rechecked"] > (1 << 20)
     if emit:
         assert np.array_equal(dists, rd)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_join_to_host_in_rounds(kernel):
+    """Results larger than the device buffers: the join runs in rounds of
+    work items through two buffers of 20000 pairs (the result holds 5.3e5)
+    and the host gets exactly the oracle's set; a host array too small gets
+    the exact count, an overflow status and a prefix of valid pairs."""
+    w = workloads.uniform2d(n=16384, seed=7)
+    ref = oracle.join(w.points, w.eps)
+    pts = torch.from_numpy(w.points).cuda()
+    h = binding.sj_build_index(pts, w.eps, binding.sj_default_options(kernel=kernel))
+    try:
+        out = torch.empty((ref.size + 64, 2), dtype=torch.int32).pin_memory()
+        cnt, rounds = binding.sj_self_join_to_host(h, out, 20000)
+        assert cnt == ref.size and rounds >= ref.size // 20000
+        got = binding.pairs_to_keys(out[:cnt].numpy())
+        assert np.array_equal(got, ref)
+        small = np.empty((1000, 2), dtype=np.int32)  # pageable, too small
+        with pytest.raises(binding.SimJoinError) as ei:
+            binding.sj_self_join_to_host(h, small, 4096)
+        assert ei.value.status == binding.SJ_ERR_RESULT_OVERFLOW
+        assert str(ref.size) in str(ei.value)
+        part = binding.pairs_to_keys(small)
+        assert np.all(np.isin(part, ref)) and np.unique(part).size == 1000
+    finally:
+        binding.sj_destroy(h)
