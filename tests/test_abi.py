@@ -116,3 +116,38 @@ def test_options_layout(lib):
     assert o.kernel == binding.SJ_KERNEL_AUTO and o.symmetric == 1 and o.graph == 0 and o.tune_cache is None
     o = binding.sj_default_options(graph=1, tune_cache="/tmp/x", queries_per_item=8)
     assert o.graph == 1 and o.tune_cache == b"/tmp/x" and o.queries_per_item == 8
+
+
+def test_new_entry_points_reject_bad_arguments_before_the_device(lib):
+    """The autotuner, the round-based join to host memory and the tuning
+    cache reject invalid arguments without touching a GPU."""
+    x = np.zeros((4, 2))
+    best = binding.sj_options()
+    ms = ctypes.c_double()
+    # sj_autotune: NULL points, n < 1, d out of range, eps invalid, NULL result
+    assert lib.sj_autotune(None, 4, 2, 0.1, None, None, 1, None, ctypes.byref(best), ctypes.byref(ms)) == binding.SJ_ERR_ARG
+    assert lib.sj_autotune(x.ctypes.data, 0, 2, 0.1, None, None, 1, None, ctypes.byref(best), None) == binding.SJ_ERR_ARG
+    assert lib.sj_autotune(x.ctypes.data, 4, 0, 0.1, None, None, 1, None, ctypes.byref(best), None) == binding.SJ_ERR_ARG
+    assert lib.sj_autotune(x.ctypes.data, 4, 2, math.nan, None, None, 1, None, ctypes.byref(best), None) == binding.SJ_ERR_ARG
+    assert lib.sj_autotune(x.ctypes.data, 4, 2, 0.1, None, None, 1, None, None, None) == binding.SJ_ERR_ARG
+    # sj_autotune_batch: no instances, a dimension out of range
+    ptrs = (ctypes.c_void_p * 1)(x.ctypes.data)
+    ns = (ctypes.c_int64 * 1)(4)
+    es = (ctypes.c_double * 1)(0.1)
+    ng = ctypes.c_int32()
+    for count, d in ((0, 2), (1, 0), (1, 129)):
+        ds = (ctypes.c_int32 * 1)(d)
+        assert lib.sj_autotune_batch(ptrs, ns, ds, es, count, None, None, 1, None, 0, ctypes.byref(ng), None, None,
+                                     None, None) == binding.SJ_ERR_ARG
+    # sj_self_join_to_host: NULL handle, NULL count, a buffer below 1024 pairs
+    cnt = ctypes.c_int64()
+    out = np.zeros((8, 2), dtype=np.int32)
+    assert lib.sj_self_join_to_host(None, out.ctypes.data, 8, 4096, ctypes.byref(cnt), None) == binding.SJ_ERR_ARG
+    assert lib.sj_self_join_to_host(None, out.ctypes.data, 8, 4096, None, None) == binding.SJ_ERR_ARG
+    assert lib.sj_self_join_to_host(None, out.ctypes.data, 8, 100, ctypes.byref(cnt), None) == binding.SJ_ERR_ARG
+    # sj_tune_lookup: NULL path
+    assert lib.sj_tune_lookup(None, 0, 2, 4, None, None, None) == binding.SJ_ERR_ARG
+    # indexed_dims below SJ_NO_INDEX is an invalid option
+    o = binding.sj_default_options(indexed_dims=-2)
+    h = ctypes.c_void_p()
+    assert lib.sj_build_index(x.ctypes.data, 4, 2, 0.1, ctypes.byref(o), None, ctypes.byref(h)) == binding.SJ_ERR_ARG
