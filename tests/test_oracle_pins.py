@@ -251,3 +251,12 @@ def test_near_ties_decided_exactly(orc):
     for p in range(x.shape[0] // 2):
         i, j = 2 * p, 2 * p + 1
         assert (((i << 32) | j) in keys) == exact_in(x, i, j, eps), p
+
+
+def test_stored_brute_force_eps_is_the_oracle_calibration(orc):
+    """The stored eps of the brute-force 16-D workload is what the oracle's
+    calibration rule gives (mean selectivity 50 over 2000 seeded queries):
+    the value was written by oracle/calibrate_eps.py, not by the GPU path."""
+    from paper_2209_11287_gb300 import workloads
+    w = workloads.brute16d(eps=1.0)
+    assert orc.calibrate_eps(w.points, 50.0) == workloads._stored_eps("brute16d")
