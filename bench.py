@@ -19,6 +19,7 @@ import argparse
 import json
 import math
 import os
+import shutil
 import statistics
 import subprocess
 import tempfile
@@ -630,6 +631,7 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
         t_e2e.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(t_e2e)
+    shutil.rmtree(tune_dir, ignore_errors=True)
     if rank != 0:
         return
     var = {}
