@@ -350,9 +350,10 @@ SJ_API int sj_tune_lookup(const char* path, int32_t batch, int32_t d, int64_t n,
 /* ---- self-join without allocation -------------------------------------- */
 /*
  * No counterpart in the paper: an entry point for callers that must not
- * allocate memory while they run, for instance code inside a CUDA stream
- * capture, a process whose device memory another allocator has reserved up
- * front, or a runtime that forbids cudaMalloc / cudaFree after start-up.
+ * allocate device memory while they run, for instance a process whose device
+ * memory another allocator has reserved up front (a serving runtime that
+ * takes a fixed budget at start-up and owns every later allocation), or an
+ * embedding runtime that forbids cudaMalloc / cudaFree once it has started.
  *
  * Computes the same set as sj_join with SJ_KERNEL_FP64_FMA (the decision rule
  * above) by brute force: all n points form one cell, so every pair is tiled.
@@ -370,8 +371,9 @@ SJ_API int sj_tune_lookup(const char* path, int32_t batch, int32_t d, int64_t n,
  *   count_out  host pointer; receives |R| (exact even when it exceeds
  *              capacity, in which case SJ_ERR_RESULT_OVERFLOW is returned and
  *              pairs_out holds `capacity` of the pairs)
- *   stream     cudaStream_t as void*; the call returns after its work on
- *              `stream` has finished (it reads the count back)
+ *   stream     cudaStream_t as void*; the call synchronizes this stream: it
+ *              reads the extent of the points and the count back to the host
+ *              and returns after its work on `stream` has finished
  *
  * The first call on a device looks up the device address of the static
  * array (cudaGetSymbolAddress) and caches it; make that first call before

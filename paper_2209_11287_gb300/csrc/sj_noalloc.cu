@@ -1,8 +1,7 @@
 // sj_self_join_noalloc: a self-join that allocates no memory at all.
 //
 // Who needs it: callers that cannot allocate device memory while they run,
-// e.g. code that executes inside a captured CUDA stream region it must not
-// break, a process whose device memory is fully reserved up front by another
+// e.g. a process whose device memory is fully reserved up front by another
 // allocator, or an embedding runtime that forbids cudaMalloc / cudaFree after
 // initialisation.  They still pass the input points and the output buffer;
 // every working array this join needs lives in one fixed file-scope device
@@ -67,7 +66,7 @@ static std::mutex g_noalloc_mu;
 static void* g_noalloc_addr[64];
 
 // Device address of the scratch on the current device, resolved once per
-// device (the first call on a device does this; it must not happen inside a
+// device (the first call on a device does this; make that call before any
 // stream capture).
 static int scratch_address(unsigned char** out) {
     int dev = 0;

@@ -1,8 +1,9 @@
 """The allocation-free entry point sj_self_join_noalloc, for callers that
-cannot allocate memory while they run (stream capture, a device memory budget
-reserved up front, runtimes that forbid cudaMalloc after start-up): it must
-return exactly the pair set of the regular entry point with the plain FP64
-kernel, call after call, although every call reuses the same static scratch.
+cannot allocate device memory while they run (a device memory budget that
+another allocator reserved up front, a runtime that forbids cudaMalloc after
+start-up): it must return exactly the oracle's pair set (Sec. II-A, Eq. 1), and
+the regular entry point's with the plain FP64 kernel, call after call,
+although every call reuses the same static scratch.
 
 This file is collected last so that a run stopping at its first failure has
 already run every other test.
@@ -10,6 +11,7 @@ already run every other test.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2209_11287_gb300 import binding, workloads
 
 pytestmark = pytest.mark.gpu
@@ -43,14 +45,30 @@ def _noalloc(x, eps, capacity):
     return cnt, _keys(out[:cnt].cpu().numpy())
 
 
-def test_two_calls_match_regular_entry_point():
+def test_two_calls_match_oracle_and_regular_entry_point():
     # first call: a larger 4-D set; second call: a smaller 2-D set, so any
     # state the first call left in the shared scratch would show
     a = workloads.uniform4d(n=30000, seed=5)
     b = workloads.uniform2d(n=9000, seed=6)
     for w in (a, b):
-        ref = _regular(w.points, w.eps)
+        ref = oracle.join(w.points, w.eps)
         cnt, got = _noalloc(w.points, w.eps, capacity=ref.size + 1024)
+        assert cnt == ref.size
+        assert np.array_equal(got, ref)
+        assert np.array_equal(_regular(w.points, w.eps), ref)
+
+
+def test_largest_accepted_size():
+    """n = SJ_NOALLOC_MAX_N points of d = SJ_NOALLOC_MAX_D dims fill every
+    region of the scratch (packed rows of all padded columns, perm, items);
+    uniform in [0,1]^8 with eps for about 32 neighbours.  Run twice so the
+    second call starts from the first call's leftovers."""
+    n, d = 32768, 8
+    x = np.random.Generator(np.random.PCG64(2024)).random((n, d))
+    eps = workloads.ball_eps(n, d, 32.0)
+    ref = oracle.join(x, eps)
+    for _ in range(2):
+        cnt, got = _noalloc(x, eps, capacity=ref.size + 64)
         assert cnt == ref.size
         assert np.array_equal(got, ref)
 
