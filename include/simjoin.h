@@ -234,6 +234,33 @@ SJ_API void sj_results_free(sj_result* results, int32_t count);
 SJ_API int sj_self_join_to_host(sj_handle h, int32_t* host_pairs, int64_t host_capacity, int64_t device_pairs,
                                 int64_t* count_out, int32_t* rounds_out);
 
+/* ---- sharding one join over several GPUs (Sec. III-B) -------------------- */
+/*
+ * The work items of an index (the queries of one cell with the candidate
+ * runs of its neighbourhood) are independent units: every GPU can build the
+ * same index from the same points (the build is deterministic) and run a
+ * contiguous range of items; the union of the ranges' results is the join.
+ *
+ * sj_index_item_work: the pair evaluations of each work item (n_items int64,
+ * host memory; n_items from sj_index_info), as the tile kernels perform them.
+ *
+ * sj_shard_bounds: host only (no GPU needed).  Splits items [0, n_items)
+ * into n_shards contiguous ranges [bounds[k], bounds[k + 1]) of about equal
+ * total work: boundary k is the item boundary whose work prefix is nearest
+ * to k / n_shards of the total.  bounds: n_shards + 1 int64; bounds[0] = 0,
+ * bounds[n_shards] = n_items, non-decreasing.  A pure function of its
+ * inputs, so every rank computes the same partition.  Errors: SJ_ERR_ARG.
+ *
+ * sj_self_join_range: sj_self_join restricted to work items [item_begin,
+ * item_end) (pairs of the items' queries, both orders of mirrored pairs, as
+ * in the full join); n_candidates and n_evaluated of the result are those of
+ * the whole index.  Errors: those of sj_self_join, SJ_ERR_ARG for a range
+ * outside [0, n_items].
+ */
+SJ_API int sj_index_item_work(sj_handle h, int64_t* work_out);
+SJ_API int sj_shard_bounds(const int64_t* item_work, int64_t n_items, int32_t n_shards, int64_t* bounds);
+SJ_API int sj_self_join_range(sj_handle h, int64_t item_begin, int64_t item_end, sj_result* out);
+
 /* Convenience: build + join + destroy in one call. */
 SJ_API int sj_join(const double* pts, int64_t n, int32_t d, double eps, const sj_options* opt, void* stream,
             sj_result* out);
@@ -387,6 +414,67 @@ SJ_API int sj_tune_lookup(const char* path, int32_t batch, int32_t d, int64_t n,
 #define SJ_NOALLOC_MAX_D 8
 SJ_API int sj_self_join_noalloc(const double* pts, int64_t n, int32_t d, double eps, int32_t* pairs_out,
                                 int64_t capacity, int64_t* count_out, void* stream);
+
+/* ---- test aid: the certified filter's own values -------------------------- */
+/*
+ * The low-precision filters certify each decision with an error bound
+ * (simjoin.h: decision rule).  For a built index whose kernel is
+ * SJ_KERNEL_FILTER_F32 (padded d <= 8) or a tensor-core filter, this runs
+ * the join once (the result is discarded) with a recording mode of the same
+ * kernel that writes, for every evaluated (query, candidate) pair, the
+ * filter's value a = -||y_q||^2 / 2 + y_q . y_c exactly as the kernel holds
+ * it (FP32 accumulator of the fma chain or of the tensor-core MMA), and
+ * copies the index arrays needed to check it.  The kernel's bound says
+ * |s_y - (pc - 2 a)| <= E = c1 (P + pc), with s_y = ||y_q - y_c||^2 of the
+ * stored kernel coordinates and pc = -2 h_c; a >= thr_in certifies "in" and
+ * a < thr_out certifies "out" under the decision rule.  No counterpart in the
+ * paper; a measurement aid for tests (slow: one atomic per pair).
+ *
+ *   perm, y, hnorm, thr_out, thr_in   host arrays of n (y: n x dp) entries in
+ *                                     cell order, or NULL: input index, kernel
+ *                                     coordinates, -||y||^2 / 2, thresholds
+ *   records    host array of 4 * capacity int32: per evaluated pair (query
+ *              position, candidate position, bits of a as float, 0), positions
+ *              in cell order; pairs past capacity are counted, not stored
+ *   info       sizes and the bound: n, dp, kernel, c1, P, e2, records (pairs
+ *              evaluated, exact), count (|R| of the join); with every array
+ *              NULL and capacity 0 only the sizes and the bound are filled
+ *              (records = count = -1) and nothing runs
+ * Errors: SJ_ERR_ARG, SJ_ERR_UNSUPPORTED (another kernel), SJ_ERR_OOM,
+ * SJ_ERR_CUDA.
+ */
+typedef struct sj_filter_dump {
+    int64_t n;
+    int32_t dp;
+    int32_t kernel;
+    double c1;
+    double pbound;
+    double e2;
+    int64_t records;
+    int64_t count;
+} sj_filter_dump;
+SJ_API int sj_debug_filter_dump(sj_handle h, int32_t* perm, float* y, float* hnorm, float* thr_out, float* thr_in,
+                                int32_t* records, int64_t capacity, sj_filter_dump* info);
+
+/*
+ * The cell order of a built index: perm_out[p] is the input index of the
+ * point at sorted position p (points sorted by grid cell key, Sec. III-B;
+ * inside a cell the order is unspecified).  perm_out: n int32, host or
+ * device.  Synchronous.  Errors: SJ_ERR_ARG, SJ_ERR_CUDA.
+ */
+SJ_API int sj_index_perm(sj_handle h, int32_t* perm_out);
+
+/* ---- test aids: allocation failures ------------------------------------ */
+/*
+ * No counterpart in the paper.  sj_debug_fail_allocations(k): the library's
+ * next k device allocations succeed and every later one fails with
+ * SJ_ERR_OOM until the injection is switched off with a negative k
+ * (process-wide, all threads).  sj_debug_live_allocations(): device blocks
+ * the library holds at the moment (allocated and not yet released); a call
+ * that fails must leave it where it was.
+ */
+SJ_API void sj_debug_fail_allocations(int64_t after);
+SJ_API int64_t sj_debug_live_allocations(void);
 
 /* ---- status ------------------------------------------------------------ */
 SJ_API const char* sj_error_string(int status);

@@ -84,6 +84,19 @@ class sj_result(ctypes.Structure):
     ]
 
 
+class sj_filter_dump(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("dp", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("c1", ctypes.c_double),
+        ("pbound", ctypes.c_double),
+        ("e2", ctypes.c_double),
+        ("records", ctypes.c_int64),
+        ("count", ctypes.c_int64),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -157,6 +170,20 @@ def load():
         lib.sj_tune_lookup.restype = ctypes.c_int
         lib.sj_self_join_to_host.argtypes = [_vp, _vp, _i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i32)]
         lib.sj_self_join_to_host.restype = ctypes.c_int
+        lib.sj_debug_filter_dump.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, ctypes.POINTER(sj_filter_dump)]
+        lib.sj_debug_filter_dump.restype = ctypes.c_int
+        lib.sj_index_perm.argtypes = [_vp, _vp]
+        lib.sj_index_perm.restype = ctypes.c_int
+        lib.sj_debug_fail_allocations.argtypes = [_i64]
+        lib.sj_debug_fail_allocations.restype = None
+        lib.sj_debug_live_allocations.argtypes = []
+        lib.sj_debug_live_allocations.restype = ctypes.c_int64
+        lib.sj_index_item_work.argtypes = [_vp, _vp]
+        lib.sj_index_item_work.restype = ctypes.c_int
+        lib.sj_shard_bounds.argtypes = [_vp, _i64, _i32, _vp]
+        lib.sj_shard_bounds.restype = ctypes.c_int
+        lib.sj_self_join_range.argtypes = [_vp, _i64, _i64, ctypes.POINTER(sj_result)]
+        lib.sj_self_join_range.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -486,3 +513,68 @@ def pairs_to_keys(pairs: np.ndarray) -> np.ndarray:
     """Sorted 64-bit keys (i << 32) | j of an (i, j) int32 pair array."""
     p = np.asarray(pairs).astype(np.int64)
     return np.sort((p[:, 0] << 32) | p[:, 1])
+
+
+def sj_debug_filter_dump(handle, capacity: int):
+    """The filter's own value for every evaluated pair of a built index
+    (test aid): returns (info, records, arrays) with records an (m, 3) int64
+    array of (query position, candidate position, float32 bits of a) in cell
+    order (m = min(info.records, capacity)) and arrays a dict of the index's
+    perm, y (n x dp float32), h, thr_out, thr_in in cell order."""
+    lib = load()
+    info = sj_filter_dump()
+    # sizes first (no arrays, no records: nothing runs), then the dump
+    _check(lib.sj_debug_filter_dump(handle, None, None, None, None, None, None, 0, ctypes.byref(info)))
+    nn, dp = int(info.n), int(info.dp)
+    perm = np.empty(nn, dtype=np.int32)
+    y = np.empty((nn, dp), dtype=np.float32)
+    h = np.empty(nn, dtype=np.float32)
+    to = np.empty(nn, dtype=np.float32)
+    ti = np.empty(nn, dtype=np.float32)
+    rec = np.empty((max(int(capacity), 1), 4), dtype=np.int32)
+    _check(lib.sj_debug_filter_dump(handle, perm.ctypes.data, y.ctypes.data, h.ctypes.data, to.ctypes.data,
+                                    ti.ctypes.data, rec.ctypes.data, int(capacity), ctypes.byref(info)))
+    m = min(int(info.records), int(capacity))
+    return info, rec[:m, :3].astype(np.int64), {"perm": perm, "y": y, "h": h, "thr_out": to, "thr_in": ti}
+
+
+def sj_index_perm(handle, n: int) -> np.ndarray:
+    """The cell order of a built index: input index of each sorted position."""
+    out = np.empty(int(n), dtype=np.int32)
+    _check(load().sj_index_perm(handle, out.ctypes.data))
+    return out
+
+
+def sj_debug_fail_allocations(after: int) -> None:
+    """Test aid: the next ``after`` device allocations succeed, later ones fail
+    with SJ_ERR_OOM; a negative value switches the injection off."""
+    load().sj_debug_fail_allocations(int(after))
+
+
+def sj_debug_live_allocations() -> int:
+    """Test aid: device blocks the library holds at the moment."""
+    return int(load().sj_debug_live_allocations())
+
+
+def sj_index_item_work(handle) -> np.ndarray:
+    """Pair evaluations of each work item of a built index (int64)."""
+    n_items = sj_index_info(handle)["n_items"]
+    out = np.zeros(n_items, dtype=np.int64)
+    _check(load().sj_index_item_work(handle, out.ctypes.data))
+    return out
+
+
+def sj_shard_bounds(item_work, n_shards: int) -> np.ndarray:
+    """Contiguous item ranges of about equal work (host only): bounds[k] ..
+    bounds[k + 1] is shard k."""
+    w = np.ascontiguousarray(item_work, dtype=np.int64)
+    out = np.zeros(int(n_shards) + 1, dtype=np.int64)
+    _check(load().sj_shard_bounds(w.ctypes.data, w.size, int(n_shards), out.ctypes.data))
+    return out
+
+
+def sj_self_join_range(handle, item_begin: int, item_end: int) -> sj_result:
+    """sj_self_join over work items [item_begin, item_end)."""
+    r = sj_result()
+    _check(load().sj_self_join_range(handle, int(item_begin), int(item_end), ctypes.byref(r)))
+    return r

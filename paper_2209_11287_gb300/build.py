@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with ThreadPoolExecutor(max_workers=min(16, len(srcs), max(4, os.cpu_count() or 4))) as ex:
         res = list(ex.map(compile_one, srcs))
     if verbose:
         for _, err in res:

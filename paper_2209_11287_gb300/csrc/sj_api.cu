@@ -57,7 +57,19 @@ static int pool_for(int dev, cudaMemPool_t* out) {
     return SJ_OK;
 }
 
+// Test aid: allocations still allowed before injected failures start (-1:
+// no injection), and the device blocks currently held.
+static std::atomic<long long> g_fail_after{-1};
+static std::atomic<long long> g_live_blocks{0};
+
 int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (g_fail_after.load(std::memory_order_relaxed) >= 0 &&
+        g_fail_after.fetch_sub(1, std::memory_order_relaxed) <= 0) {
+        g_fail_after.store(0, std::memory_order_relaxed);
+        set_error("device allocation of %zu bytes failed (injected)", bytes);
+        return SJ_ERR_OOM;
+    }
     int dev = 0;
     SJ_CK(cudaGetDevice(&dev));
     cudaMemPool_t pool;
@@ -66,15 +78,20 @@ int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
+        *p = nullptr;
         set_error("device allocation of %zu bytes failed", bytes);
         return SJ_ERR_OOM;
     }
     SJ_CK(e);
+    g_live_blocks.fetch_add(1, std::memory_order_relaxed);
     return SJ_OK;
 }
 
 void dev_free(void* p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+    if (p) {
+        cudaFreeAsync(p, s);
+        g_live_blocks.fetch_sub(1, std::memory_order_relaxed);
+    }
 }
 
 bool is_device_pointer(const void* p) {
@@ -105,6 +122,7 @@ static void release_index(Index* ix) {
     dev_free(ix->h, s);
     dev_free(ix->thr_out, s);
     dev_free(ix->thr_in, s);
+    dev_free(ix->aux, s);
     dev_free(ix->perm, s);
     dev_free(ix->rows_a, s);
     dev_free(ix->rows_b, s);
@@ -171,6 +189,21 @@ const char* sj_last_error_message(void) { return g_msg; }
 const char* sj_version(void) { return "libsj 0.1 sm_103a"; }
 
 int64_t sj_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+void sj_debug_fail_allocations(int64_t after) { g_fail_after.store(after < 0 ? -1 : after, std::memory_order_relaxed); }
+
+int64_t sj_debug_live_allocations(void) { return (int64_t)g_live_blocks.load(std::memory_order_relaxed); }
+
+int sj_index_perm(sj_handle h, int32_t* perm_out) {
+    clear_error();
+    if (!h || !perm_out) {
+        set_error("NULL argument");
+        return SJ_ERR_ARG;
+    }
+    SJ_CK(cudaMemcpyAsync(perm_out, h->perm, (size_t)h->n * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+    SJ_CK(cudaStreamSynchronize(h->stream));
+    return SJ_OK;
+}
 
 int sj_selftest_bounded_wait(void* stream) {
     clear_error();
@@ -318,36 +351,49 @@ static void free_result_impl(ResultImpl* ri) {
 }
 
 static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist, unsigned long long* count_out,
-                    unsigned long long* rechecked_out) {
+                    unsigned long long* rechecked_out, int4* dbg = nullptr, unsigned long long dbg_cap = 0,
+                    unsigned long long* dbg_count = nullptr, int64_t item_begin = 0, int64_t item_end = -1) {
     cudaStream_t s = ix->stream;
     const int64_t np = (int64_t)ri->pair_pages.size();
     SJ_CK(cudaMemsetAsync(ix->counters, 0, kCounters * sizeof(unsigned long long), s));
+    const int64_t all_items = ix->n_items;
+    if (item_end < 0 || item_end > all_items) item_end = all_items;
+    if (item_begin > 0) {  // the item queue starts at the range
+        const unsigned long long b0 = (unsigned long long)item_begin;
+        SJ_CK(cudaMemcpyAsync(ix->counters, &b0, sizeof b0, cudaMemcpyHostToDevice, s));
+    }
     // deferred-recheck queue: band pairs (and, with distances, every
     // maybe-in pair); pairs past its end are re-decided in place
     const unsigned long long ev = (unsigned long long)std::max<int64_t>(ix->n_evaluated, 1);
     unsigned long long band_cap = dist ? std::max<unsigned long long>(1ull << 20, ev / 8) : std::max<unsigned long long>(1ull << 20, ev / 64);
     band_cap = std::min<unsigned long long>(band_cap, ev);
+    Scratch tmp(s);
     int2* band = nullptr;
-    SJ_TRY(dev_alloc_t(&band, (size_t)band_cap, s));
+    SJ_TRY(tmp.alloc(&band, (size_t)band_cap));
     JoinOut jo;
     jo.out_pairs = reinterpret_cast<int2*>(ri->block);
     jo.out_dist = ri->dblock;
     jo.capacity = (unsigned long long)np * (unsigned long long)page_pairs;
     jo.band = band;
     jo.band_cap = band_cap;
+    jo.dbg = dbg;
+    jo.dbg_cap = dbg_cap;
     int st = SJ_OK;
     if (!ix->ev_tile[0]) {
         SJ_CK(cudaEventCreate(&ix->ev_tile[0]));
         SJ_CK(cudaEventCreate(&ix->ev_tile[1]));
     }
-    if (ix->n_items > 0) {
+    const bool any = item_end > item_begin;
+    if (any) {
         SJ_CK(cudaEventRecord(ix->ev_tile[0], s));
+        ix->n_items = item_end;  // the kernels stop at the range's end
         if (ix->kernel == SJ_KERNEL_FP64_DMMA)
             st = launch_join_dmma(ix, jo, dist ? 1 : 0);
         else if (is_tensor_kernel(ix->kernel))
             st = launch_join_tc(ix, jo, dist ? 1 : 0);
         else
             st = launch_join_cc(ix, jo, dist ? 1 : 0);
+        ix->n_items = all_items;
         if (st == SJ_OK) SJ_CK(cudaEventRecord(ix->ev_tile[1], s));
         if (st == SJ_OK) st = launch_recheck(ix, jo, dist ? 1 : 0);
     }
@@ -363,14 +409,14 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
             st = SJ_ERR_TIMEOUT;
         }
     }
-    dev_free(band, s);
     ix->last_tile_ms = 0.0;
-    if (st == SJ_OK && ix->n_items > 0) {
+    if (st == SJ_OK && any) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ix->ev_tile[0], ix->ev_tile[1]) == cudaSuccess) ix->last_tile_ms = ms;
     }
     *count_out = c[1];
     *rechecked_out = c[2];
+    if (dbg_count) *dbg_count = c[5];
     return st;
 }
 
@@ -514,7 +560,7 @@ int sj_self_join_to_host(sj_handle h, int32_t* host_pairs, int64_t host_capacity
     return SJ_OK;
 }
 
-int sj_self_join(sj_handle h, sj_result* out) {
+static int self_join_impl(sj_handle h, int64_t item_begin, int64_t item_end, sj_result* out) {
     clear_error();
     if (!h || !out) {
         set_error("NULL argument");
@@ -544,14 +590,14 @@ int sj_self_join(sj_handle h, sj_result* out) {
     int st = alloc_pages(ri, np, page_pairs, dist, h->stream);
     unsigned long long count = 0, rechecked = 0;
     int reruns = 0;
-    if (st == SJ_OK) st = run_join(h, ri, page_pairs, dist, &count, &rechecked);
+    if (st == SJ_OK) st = run_join(h, ri, page_pairs, dist, &count, &rechecked, nullptr, 0, nullptr, item_begin, item_end);
     if (st == SJ_OK && count > (unsigned long long)ri->pair_pages.size() * (unsigned long long)page_pairs) {
         // overflow: grow the pool to the exact count and run again
         int64_t need = (int64_t)((count + page_pairs - 1) / page_pairs);
         st = alloc_pages(ri, need, page_pairs, dist, h->stream);
         if (st == SJ_OK) {
             reruns = 1;
-            st = run_join(h, ri, page_pairs, dist, &count, &rechecked);
+            st = run_join(h, ri, page_pairs, dist, &count, &rechecked, nullptr, 0, nullptr, item_begin, item_end);
         }
         if (st == SJ_OK && count > (unsigned long long)ri->pair_pages.size() * (unsigned long long)page_pairs) {
             set_error("result of %llu pairs still exceeds the page pool", count);
@@ -581,6 +627,123 @@ int sj_self_join(sj_handle h, sj_result* out) {
     out->ms_tile = h->last_tile_ms;
     out->internal = ri;
     return st;
+}
+
+int sj_debug_filter_dump(sj_handle h, int32_t* perm, float* y, float* hnorm, float* thr_out, float* thr_in,
+                         int32_t* records, int64_t capacity, sj_filter_dump* info) {
+    clear_error();
+    if (!h || !info || capacity < 0 || (capacity > 0 && !records)) {
+        set_error("invalid argument");
+        return SJ_ERR_ARG;
+    }
+    const bool f32s = h->kernel == SJ_KERNEL_FILTER_F32 && h->dp <= 8;
+    if (!f32s && !is_tensor_kernel(h->kernel)) {
+        set_error("the filter dump covers the FP32 filter (padded d <= 8) and the tensor-core filters");
+        return SJ_ERR_UNSUPPORTED;
+    }
+    info->n = h->n;
+    info->dp = h->dp;
+    info->kernel = h->kernel;
+    info->c1 = h->bound_c1;
+    info->pbound = h->bound_p;
+    info->e2 = h->e2;
+    info->records = -1;
+    info->count = -1;
+    if (!perm && !y && !hnorm && !thr_out && !thr_in && capacity == 0) return SJ_OK;  // sizes only
+    cudaStream_t s = h->stream;
+    const int64_t n = h->n;
+    if (perm) SJ_CK(cudaMemcpyAsync(perm, h->perm, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (y) SJ_CK(cudaMemcpyAsync(y, h->y, n * h->dp * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (hnorm) SJ_CK(cudaMemcpyAsync(hnorm, h->h, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (thr_out) SJ_CK(cudaMemcpyAsync(thr_out, h->thr_out, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (thr_in) SJ_CK(cudaMemcpyAsync(thr_in, h->thr_in, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    int4* dbg = nullptr;
+    SJ_TRY(dev_alloc_t(&dbg, (size_t)std::max<int64_t>(capacity, 1), s));
+    ResultImpl* ri = new (std::nothrow) ResultImpl();
+    if (!ri) {
+        dev_free(dbg, s);
+        return SJ_ERR_OOM;
+    }
+    ri->stream = s;
+    const int64_t page_pairs = kDefaultPagePairs;
+    int st = alloc_pages(ri, std::max<int64_t>(1, (h->n_candidates + page_pairs - 1) / page_pairs), page_pairs,
+                         false, s);
+    unsigned long long count = 0, rechecked = 0, recorded = 0;
+    if (st == SJ_OK) st = run_join(h, ri, page_pairs, false, &count, &rechecked, dbg, (unsigned long long)capacity,
+                                   &recorded);
+    if (st == SJ_OK && capacity > 0) {
+        const int64_t k = std::min<int64_t>((int64_t)recorded, capacity);
+        cudaError_t e = cudaMemcpyAsync(records, dbg, k * sizeof(int4), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("filter dump copy: %s", cudaGetErrorString(e));
+            st = SJ_ERR_CUDA;
+        }
+    }
+    free_result_impl(ri);
+    dev_free(dbg, s);
+    if (st != SJ_OK) return st;
+    info->records = (int64_t)recorded;
+    info->count = (int64_t)count;
+    return SJ_OK;
+}
+
+int sj_self_join(sj_handle h, sj_result* out) { return self_join_impl(h, 0, -1, out); }
+
+int sj_self_join_range(sj_handle h, int64_t item_begin, int64_t item_end, sj_result* out) {
+    if (!h || item_begin < 0 || item_end < item_begin || item_end > h->n_items) {
+        set_error("invalid item range [%lld, %lld) of %lld items", (long long)item_begin, (long long)item_end,
+                  h ? (long long)h->n_items : -1ll);
+        return SJ_ERR_ARG;
+    }
+    return self_join_impl(h, item_begin, item_end, out);
+}
+
+int sj_index_item_work(sj_handle h, int64_t* work_out) {
+    clear_error();
+    if (!h || !work_out) {
+        set_error("NULL argument");
+        return SJ_ERR_ARG;
+    }
+    if (h->n_items == 0) return SJ_OK;
+    Scratch tmp(h->stream);
+    long long* dw = nullptr;
+    SJ_TRY(tmp.alloc(&dw, (size_t)h->n_items));
+    SJ_TRY(launch_item_work(h, dw));
+    SJ_CK(cudaMemcpyAsync(work_out, dw, (size_t)h->n_items * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    SJ_CK(cudaStreamSynchronize(h->stream));
+    return SJ_OK;
+}
+
+int sj_shard_bounds(const int64_t* item_work, int64_t n_items, int32_t n_shards, int64_t* bounds) {
+    clear_error();
+    if (n_items < 0 || n_shards < 1 || !bounds || (n_items > 0 && !item_work)) {
+        set_error("invalid argument");
+        return SJ_ERR_ARG;
+    }
+    long double total = 0;
+    for (int64_t i = 0; i < n_items; ++i) {
+        if (item_work[i] < 0) {
+            set_error("negative work for item %lld", (long long)i);
+            return SJ_ERR_ARG;
+        }
+        total += (long double)item_work[i];
+    }
+    // boundary k: the item boundary whose work prefix is nearest to k / N of
+    // the total (ties to the earlier one); prefixes only grow, so the bounds
+    // are monotone
+    bounds[0] = 0;
+    long double pre = 0;
+    int64_t i = 0;
+    for (int32_t k = 1; k < n_shards; ++k) {
+        const long double target = total * (long double)k / (long double)n_shards;
+        while (i < n_items && pre + (long double)item_work[i] <= target) pre += (long double)item_work[i++];
+        // pre <= target < pre + work[i]: take the nearer boundary
+        if (i < n_items && (pre + (long double)item_work[i]) - target < target - pre) pre += (long double)item_work[i++];
+        bounds[k] = i;
+    }
+    bounds[n_shards] = n_items;
+    return SJ_OK;
 }
 
 int sj_result_copy(const sj_result* r, int32_t* pairs_out, double* dist_out) {

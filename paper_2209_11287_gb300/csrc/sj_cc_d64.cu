@@ -1,0 +1,9 @@
+// CUDA-core distance tiles (sj_join_cc.cuh) instantiated for padded dimension 64.
+#include "sj_join_cc.cuh"
+
+namespace sj {
+
+template int launch_cc_dp<float, 64>(Index*, const JoinParams&);
+template int launch_cc_dp<double, 64>(Index*, const JoinParams&);
+
+}  // namespace sj

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -99,8 +100,9 @@ __global__ void k_cell_keys(const double* __restrict__ x, int64_t n, int d, Grid
 // ---------------------------------------------------------------------------
 // counting sort by cell key, for key spaces of at most a few times n keys
 // ---------------------------------------------------------------------------
-// One count per key, a scan of the counts, a scatter, then the non-empty
-// keys compacted into the cell table.  Lanes of a warp with the same key
+// One count per key, a scan of the counts, a scatter; the key's first
+// position then stands for its cell (no table of non-empty cells is
+// built: the neighbour runs are read per key, k_denum).  Lanes of a warp with the same key
 // share one atomic (match_any), so a crowded cell costs one atomic per warp.
 // Inside a cell the points follow the order in which warps reach it, not the
 // input order: every result of the join is a set and does not depend on it.
@@ -123,8 +125,10 @@ __global__ void k_key_count(const double* __restrict__ x, int64_t n, int d, Grid
     if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], (uint32_t)__popc(peers));
 }
 
-__global__ void k_key_scatter(const uint32_t* __restrict__ key32, int64_t n, const uint32_t* __restrict__ start,
-                              uint32_t* fill, int32_t* perm) {
+// off64[key] >> 32: the key's first sorted position (exclusive scan of the
+// counts).
+__global__ void k_key_scatter(const uint32_t* __restrict__ key32, int64_t n,
+                              const unsigned long long* __restrict__ off64, uint32_t* fill, int32_t* perm) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool valid = i < n;
     const uint32_t key = valid ? key32[i] : kNoKey;
@@ -134,126 +138,132 @@ __global__ void k_key_scatter(const uint32_t* __restrict__ key32, int64_t n, con
     uint32_t b = 0;
     if (valid && lane == leader) b = atomicAdd(&fill[key], (uint32_t)__popc(peers));
     b = __shfl_sync(0xffffffffu, b, leader);
-    if (valid) perm[start[key] + b + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
-}
-
-__global__ void k_nonempty(const uint32_t* __restrict__ cnt, int64_t K, uint32_t* flags) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k < K) flags[k] = cnt[k] != 0u ? 1u : 0u;
-}
-
-// Non-empty key k becomes cell cidx[k]: its key, its first sorted position,
-// and the dense key -> cell table (-1 for empty keys); the last thread writes
-// the cell count M and cell_start[M] = n.
-__global__ void k_bins_to_cells(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ start,
-                                const uint32_t* __restrict__ cidx, int64_t K, int64_t n,
-                                unsigned long long* cell_key, int32_t* cell_start, int32_t* table,
-                                unsigned long long* n_cells) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    const bool ne = cnt[k] != 0u;
-    const uint32_t c = cidx[k];
-    table[k] = ne ? (int32_t)c : -1;
-    if (ne) {
-        cell_key[c] = (unsigned long long)k;
-        cell_start[c] = (int32_t)start[k];
-    }
-    if (k == K - 1) {
-        const uint32_t M = c + (ne ? 1u : 0u);
-        *n_cells = M;
-        cell_start[M] = (int32_t)n;
-    }
+    if (valid) perm[(uint32_t)(off64[key] >> 32) + b + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
 // ---------------------------------------------------------------------------
-// exclusive scan of uint32 (reduce-then-scan over tiles of 4096)
+// exclusive scan (reduce-then-scan over tiles of 4096), of uint32 or of
+// uint64 values produced by a load functor
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T* total) {
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) s_warp[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+        T w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : T(0);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            T y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
         s_warp[lane] = w;
     }
     __syncthreads();
-    uint32_t warp_base = wid ? s_warp[wid - 1] : 0;
+    T warp_base = wid ? s_warp[wid - 1] : T(0);
     *total = s_warp[(blockDim.x >> 5) - 1];
-    uint32_t r = warp_base + x - v;
+    T r = warp_base + x - v;
     __syncthreads();
     return r;
 }
 
-__global__ void k_scan_tile_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* sums) {
-    __shared__ uint32_t s_warp[32];
+struct LoadU32 {
+    const uint32_t* p;
+    __device__ __forceinline__ uint32_t operator()(int64_t i) const { return p[i]; }
+};
+struct LoadU64 {
+    const unsigned long long* p;
+    __device__ __forceinline__ unsigned long long operator()(int64_t i) const { return p[i]; }
+};
+// A key's point count c in the high half and its work items ceil(c / qmax)
+// in the low half: one scan gives each key's first sorted position and its
+// first work item.
+struct LoadCountItems {
+    const uint32_t* cnt;
+    uint32_t qmax;
+    __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
+        const uint32_t c = cnt[i];
+        return ((unsigned long long)c << 32) | (unsigned long long)((c + qmax - 1u) / qmax);
+    }
+};
+
+template <typename T, typename L>
+__global__ void k_scan_tile_sums(L in, int64_t n, T* sums) {
+    __shared__ T s_warp[32];
     int64_t base = (int64_t)blockIdx.x * kScanTile;
-    uint32_t acc = 0;
+    T acc = 0;
     for (int i = 0; i < kScanItems; ++i) {
         int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
-        if (idx < n) acc += in[idx];
+        if (idx < n) acc += in(idx);
     }
-    uint32_t tot;
-    block_exclusive_scan(acc, s_warp, &tot);
+    T tot;
+    block_exclusive_scan<T>(acc, s_warp, &tot);
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
 // Scans one tile (thread t owns items t*kScanItems .. +kScanItems, a
-// contiguous chunk) and adds the tile's base offset.
-__global__ void k_scan_tiles(const uint32_t* __restrict__ in, uint32_t* out, int64_t n,
-                             const uint32_t* __restrict__ tile_base) {
-    __shared__ uint32_t s_warp[32];
+// contiguous chunk) and adds the tile's base offset; the last tile writes
+// the total to out[n] when `with_total`.
+template <typename T, typename L>
+__global__ void k_scan_tiles(L in, T* out, int64_t n, const T* __restrict__ tile_base, int with_total) {
+    __shared__ T s_warp[32];
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t v[kScanItems];
-    uint32_t acc = 0;
+    T v[kScanItems];
+    T acc = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         int64_t idx = base + i;
-        v[i] = idx < n ? in[idx] : 0;
+        v[i] = idx < n ? in(idx) : T(0);
         acc += v[i];
     }
-    uint32_t tot;
-    uint32_t run = block_exclusive_scan(acc, s_warp, &tot) + (tile_base ? tile_base[blockIdx.x] : 0);
+    T tot;
+    T run = block_exclusive_scan<T>(acc, s_warp, &tot) + (tile_base ? tile_base[blockIdx.x] : T(0));
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         int64_t idx = base + i;
         if (idx < n) out[idx] = run;
         run += v[i];
     }
+    if (with_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;
 }
 
-int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
-    if (n <= 0) return SJ_OK;
+template <typename T, typename L>
+static int scan_exclusive(L in, T* out, int64_t n, bool with_total, cudaStream_t s) {
+    if (n <= 0) {
+        if (with_total) SJ_CK(cudaMemsetAsync(out, 0, sizeof(T), s));
+        return SJ_OK;
+    }
     int64_t tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles == 1) {
-        k_scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        k_scan_tiles<T, L><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, with_total ? 1 : 0);
         note_launch();
         SJ_CK(cudaGetLastError());
         return SJ_OK;
     }
-    uint32_t* sums = nullptr;
-    SJ_TRY(dev_alloc_t(&sums, (size_t)tiles * 2, s));
-    uint32_t* sums_scan = sums + tiles;
-    k_scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
+    Scratch tmp(s);
+    T* sums = nullptr;
+    SJ_TRY(tmp.alloc(&sums, (size_t)tiles * 2));
+    T* sums_scan = sums + tiles;
+    k_scan_tile_sums<T, L><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
     note_launch();
     SJ_CK(cudaGetLastError());
-    int st = scan_exclusive_u32(sums, sums_scan, tiles, s);
+    int st = SJ_OK;
+    if constexpr (sizeof(T) == 4)
+        st = scan_exclusive<T, LoadU32>(LoadU32{sums}, sums_scan, tiles, false, s);
+    else
+        st = scan_exclusive<T, LoadU64>(LoadU64{sums}, sums_scan, tiles, false, s);
     if (st == SJ_OK) {
-        k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums_scan);
+        k_scan_tiles<T, L><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums_scan, with_total ? 1 : 0);
         note_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -261,8 +271,11 @@ int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_
             st = SJ_ERR_CUDA;
         }
     }
-    dev_free(sums, s);
     return st;
+}
+
+int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
+    return scan_exclusive<uint32_t, LoadU32>(LoadU32{in}, out, n, false, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -338,20 +351,14 @@ int radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cud
         set_error("radix sort: input too large");
         return SJ_ERR_ARG;
     }
+    Scratch tmp(s);
     unsigned long long* k2 = nullptr;
     int32_t* v2 = nullptr;
     uint32_t* hist = nullptr;
     int st = SJ_OK;
-    if ((st = dev_alloc_t(&k2, n, s)) != SJ_OK) return st;
-    if ((st = dev_alloc_t(&v2, n, s)) != SJ_OK) {
-        dev_free(k2, s);
-        return st;
-    }
-    if ((st = dev_alloc_t(&hist, (size_t)tiles * 256 * 2, s)) != SJ_OK) {
-        dev_free(k2, s);
-        dev_free(v2, s);
-        return st;
-    }
+    SJ_TRY(tmp.alloc(&k2, (size_t)n));
+    SJ_TRY(tmp.alloc(&v2, (size_t)n));
+    SJ_TRY(tmp.alloc(&hist, (size_t)tiles * 256 * 2));
     uint32_t* offs = hist + tiles * 256;
     unsigned long long* ka = reinterpret_cast<unsigned long long*>(keys);
     int32_t* va = vals;
@@ -382,9 +389,6 @@ int radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cud
             st = SJ_ERR_CUDA;
         }
     }
-    dev_free(k2, s);
-    dev_free(v2, s);
-    dev_free(hist, s);
     return st;
 }
 
@@ -479,25 +483,79 @@ __device__ __forceinline__ float thr_up(double a, float pc, double b) {
 __device__ __forceinline__ double thr_up(double a, double pc, double b) { return __fma_ru(a, pc, b); }
 
 // One thread per point: its row is gathered through perm and written in cell
-// order, with its kernel coordinates, norm and thresholds.
+// order, with its kernel coordinates, norm and thresholds (and, for the
+// small-d FP32 filter, its 16-byte record: both thresholds and the input
+// index).  The parameters travel by value.
 template <typename T>
-__global__ void k_pack(const double* __restrict__ x, const int32_t* __restrict__ perm, int64_t n,
-                       const PackParams* __restrict__ pp, double* xs, T* y, T* h, T* thr_out, T* thr_in) {
+__global__ void k_pack(const double* __restrict__ x, const int32_t* __restrict__ perm, int64_t n, const PackParams pp,
+                       double* xs, T* y, T* h, T* thr_out, T* thr_in, float4* aux) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int d = pp->d, dp = pp->dp;
-    const int64_t src = (int64_t)perm[p] * d;
+    const int d = pp.d, dp = pp.dp;
+    const int32_t src_i = perm[p];
+    const int64_t src = (int64_t)src_i * d;
     T nrm = T(0);
     for (int k = 0; k < dp; ++k) {
         const double v = k < d ? x[src + k] : 0.0;
         xs[p * dp + k] = v;
-        const T yk = k < d ? T(v - pp->lo[k]) : T(0);
+        const T yk = k < d ? T(v - pp.lo[k]) : T(0);
         y[p * dp + k] = yk;
         nrm = fma_pack(yk, yk, nrm);
     }
     h[p] = -nrm * T(0.5);
-    thr_out[p] = thr_down(pp->a_out, nrm, pp->b_out);
-    thr_in[p] = pp->has_in ? thr_up(pp->a_in, nrm, pp->b_in) : T(INFINITY);
+    const T to = thr_down(pp.a_out, nrm, pp.b_out);
+    const T ti = pp.has_in ? thr_up(pp.a_in, nrm, pp.b_in) : T(INFINITY);
+    thr_out[p] = to;
+    thr_in[p] = ti;
+    if (aux) aux[p] = make_float4((float)to, (float)ti, __int_as_float(src_i), 0.f);
+}
+
+// Per-point records of the small-d FP32 filter: its two thresholds and its
+// input index in one 16-byte load.
+__global__ void k_aux(const float* __restrict__ to, const float* __restrict__ ti, const int32_t* __restrict__ perm,
+                      int64_t n, float4* aux) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) aux[p] = make_float4(to[p], ti[p], __int_as_float(perm[p]), 0.f);
+}
+
+int build_aux(Index* ix) {
+    cudaStream_t s = ix->stream;
+    float4* aux = nullptr;
+    SJ_TRY(dev_alloc_t(&aux, (size_t)std::max<int64_t>(ix->n, 1), s));
+    ix->aux = aux;
+    k_aux<<<(unsigned)((ix->n + 255) / 256), 256, 0, s>>>(static_cast<const float*>(ix->thr_out),
+                                                          static_cast<const float*>(ix->thr_in), ix->perm, ix->n, aux);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    return SJ_OK;
+}
+
+// Pair evaluations per work item: its queries times the candidates of its
+// runs (a self-cell run starts at the item's first query when the join
+// evaluates self-cell triangles, as the tile kernels load it).
+__global__ void k_item_work(const Item* __restrict__ items, const Run* __restrict__ runs, int64_t n_items, int tri,
+                            long long* work) {
+    const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (it >= n_items) return;
+    const Item I = items[it];
+    long long c = 0;
+    for (int32_t r = I.r0; r < I.r1; ++r) {
+        const Run R = runs[r];
+        const bool mirror = (R.end_flags & kMirrorBit) != 0u;
+        const int32_t end = (int32_t)(R.end_flags & ~kMirrorBit);
+        const int32_t start = (tri && !mirror) ? I.q0 : R.start;
+        c += (long long)(end - start);
+    }
+    work[it] = c * (long long)(I.q1 - I.q0);
+}
+
+int launch_item_work(Index* ix, long long* work) {
+    if (ix->n_items <= 0) return SJ_OK;
+    k_item_work<<<(unsigned)((ix->n_items + 255) / 256), 256, 0, ix->stream>>>(ix->items, ix->runs, ix->n_items,
+                                                                            uses_triangle(ix) ? 1 : 0, work);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    return SJ_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -509,7 +567,6 @@ struct EnumParams {
     unsigned long long stride[kMaxM];
     int symmetric;
     int qmax;
-    const int32_t* table;  // dense key -> cell index (-1 = empty), or null
     // a cell key is prefix | local key: the grid arithmetic uses the local
     // part (key & local_mask), neighbour keys keep the prefix (a batched
     // index puts the instance number there; a single index has no prefix)
@@ -533,21 +590,8 @@ __device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long* a, 
 __device__ __forceinline__ void cells_in_key_range(const EnumParams& e, const unsigned long long* __restrict__ cell_key,
                                                    int64_t n_cells, unsigned long long k_lo, unsigned long long k_hi,
                                                    int64_t& ca, int64_t& cb) {
-    if (e.table) {
-        ca = -1;
-        cb = -1;
-        for (unsigned long long k = k_lo; k <= k_hi; ++k) {
-            const int32_t c = e.table[k];
-            if (c >= 0) {
-                if (ca < 0) ca = c;
-                cb = c + 1;
-            }
-        }
-        if (ca < 0) ca = cb = 0;
-    } else {
-        ca = lower_bound_u64(cell_key, n_cells, k_lo);
-        cb = lower_bound_u64(cell_key, n_cells, k_hi + 1);
-    }
+    ca = lower_bound_u64(cell_key, n_cells, k_lo);
+    cb = lower_bound_u64(cell_key, n_cells, k_hi + 1);
 }
 
 // Visits the candidate runs of cell c: for every offset vector o of the
@@ -695,6 +739,127 @@ __global__ void k_enum_fill(EnumParams e, const unsigned long long* __restrict__
 }
 
 // ---------------------------------------------------------------------------
+// neighbour runs and work items from the counting sort (dense key spaces)
+// ---------------------------------------------------------------------------
+// The counting sort gives, for every key k of the grid, its first sorted
+// position start(k) = off64[k] >> 32 and its first work item off64[k] &
+// 0xFFFFFFFF.  A range of consecutive keys [a, b] (a run of cells along the
+// last indexed dim) is then the range of sorted points [start(a),
+// start(b + 1)) directly: no table of non-empty cells is needed.  One thread
+// per key; the run arithmetic is visit_runs' (same offsets, same order).
+struct DenseEnum {
+    int m;
+    uint32_t ncell[kMaxM];
+    uint32_t stride[kMaxM];
+    int symmetric;
+    uint32_t qmax;
+    int64_t K;
+};
+
+struct DenseTotals {
+    unsigned long long n_evaluated, sum_sq, tri_skip, n_cells;
+};
+
+template <bool FILL>
+__global__ void k_denum(DenseEnum e, const unsigned long long* __restrict__ off64, uint32_t* run_cnt,
+                        const uint32_t* __restrict__ run_off, Run* runs, Item* items, DenseTotals* tot) {
+    const int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long my_eval = 0, my_sq = 0, my_skip = 0, my_cells = 0;
+    if (key < e.K) {
+        const unsigned long long a0 = off64[key], a1 = off64[key + 1];
+        const uint32_t s0 = (uint32_t)(a0 >> 32);
+        const uint32_t q = (uint32_t)(a1 >> 32) - s0;
+        uint32_t nr = 0;
+        unsigned long long ev = 0;
+        const uint32_t r0 = FILL ? run_off[key] : 0u;
+        auto emit = [&](uint32_t ka, uint32_t kb, bool mirror) {  // keys [ka, kb]
+            const int32_t a = (int32_t)(off64[ka] >> 32), b = (int32_t)(off64[kb + 1] >> 32);
+            if (a >= b) return;
+            if (FILL) {
+                Run rr;
+                rr.start = a;
+                rr.end_flags = (uint32_t)b | (mirror ? kMirrorBit : 0u);
+                runs[r0 + nr] = rr;
+            }
+            ++nr;
+            ev += (unsigned long long)(b - a);
+        };
+        if (q > 0) {
+            if (e.m == 0) {
+                emit(0u, 0u, false);  // one cell holding every point
+            } else {
+                const uint32_t k32 = (uint32_t)key;
+                uint32_t cc[kMaxM];
+                for (int k = 0; k < e.m; ++k) cc[k] = (k32 / e.stride[k]) % e.ncell[k];
+                const int mm = e.m - 1;
+                int nvec = 1;
+                for (int k = 0; k < mm; ++k) nvec *= 3;
+                const uint32_t last = cc[mm];
+                const uint32_t lo_l = last > 0 ? last - 1 : 0;
+                const uint32_t hi_l = last + 1 < e.ncell[mm] ? last + 1 : e.ncell[mm] - 1;
+#pragma unroll 3
+                for (int vi = 0; vi < nvec; ++vi) {
+                    int rem = vi, sign = 0;
+                    long long delta = 0;
+                    bool inside = true;
+                    for (int k = 0; k < mm; ++k) {
+                        const int o = rem % 3 - 1;
+                        rem /= 3;
+                        if (sign == 0 && o != 0) sign = o;
+                        const long long c = (long long)cc[k] + o;
+                        if (c < 0 || c >= (long long)e.ncell[k]) inside = false;
+                        delta += (long long)o * (long long)e.stride[k];
+                    }
+                    if (!inside || (e.symmetric && sign < 0)) continue;
+                    const uint32_t base = (uint32_t)((long long)k32 + delta);
+                    if (!e.symmetric) {
+                        emit(base - (last - lo_l), base + (hi_l - last), false);
+                    } else if (sign > 0) {
+                        emit(base - (last - lo_l), base + (hi_l - last), true);
+                    } else {
+                        emit(base, base, false);
+                        if (hi_l > last) emit(base + 1, base + (hi_l - last), true);
+                    }
+                }
+            }
+        }
+        if (FILL) {
+            const uint32_t it0 = (uint32_t)(a0 & 0xFFFFFFFFull);
+            for (uint32_t t = 0; t * e.qmax < q; ++t) {
+                Item x;
+                x.q0 = (int32_t)(s0 + t * e.qmax);
+                x.q1 = (int32_t)(s0 + min(q, (t + 1) * e.qmax));
+                x.r0 = (int32_t)r0;
+                x.r1 = (int32_t)(r0 + nr);
+                items[it0 + t] = x;
+            }
+        } else {
+            run_cnt[key] = nr;
+            if (q > 0) {
+                my_eval = ev * (unsigned long long)q;
+                my_sq = (unsigned long long)q * (unsigned long long)q;
+                if (e.symmetric) my_skip = tri_skip((int64_t)q, (int)e.qmax);
+                my_cells = 1;
+            }
+        }
+    }
+    if (!FILL) {
+        for (int o = 16; o > 0; o >>= 1) {
+            my_eval += __shfl_down_sync(0xffffffffu, my_eval, o);
+            my_sq += __shfl_down_sync(0xffffffffu, my_sq, o);
+            my_skip += __shfl_down_sync(0xffffffffu, my_skip, o);
+            my_cells += __shfl_down_sync(0xffffffffu, my_cells, o);
+        }
+        if ((threadIdx.x & 31) == 0 && my_cells) {
+            atomicAdd(&tot->n_evaluated, my_eval);
+            atomicAdd(&tot->sum_sq, my_sq);
+            atomicAdd(&tot->tri_skip, my_skip);
+            atomicAdd(&tot->n_cells, my_cells);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
 static int choose_grid(Index* ix) {
@@ -778,23 +943,24 @@ template <typename T>
 static int pack_points(Index* ix, const double* pts, const PackParams& hp) {
     cudaStream_t s = ix->stream;
     const int64_t n = ix->n;
-    PackParams* dpp = nullptr;
-    SJ_TRY(dev_alloc_t(&dpp, 1, s));
-    SJ_CK(cudaMemcpyAsync(dpp, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
+    // each array goes into the index as soon as it exists (released with it)
     T *y, *h, *to, *ti;
     SJ_TRY(dev_alloc_t(&y, (size_t)n * ix->dp, s));
-    SJ_TRY(dev_alloc_t(&h, (size_t)n, s));
-    SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
-    SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
     ix->y = y;
+    SJ_TRY(dev_alloc_t(&h, (size_t)n, s));
     ix->h = h;
+    SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
     ix->thr_out = to;
+    SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
     ix->thr_in = ti;
-    k_pack<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, ix->perm, n, dpp, ix->xs, y, h, to, ti);
+    float4* aux = nullptr;
+    if (std::is_same<T, float>::value && wants_aux(ix)) {
+        SJ_TRY(dev_alloc_t(&aux, (size_t)n, s));
+        ix->aux = aux;
+    }
+    k_pack<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, ix->perm, n, hp, ix->xs, y, h, to, ti, aux);
     note_launch();
     SJ_CK(cudaGetLastError());
-    // the pack parameters are read by the kernel before the free is ordered
-    dev_free(dpp, s);
     return SJ_OK;
 }
 
@@ -886,8 +1052,8 @@ static int pack_split_rows(Index* ix) {
     const size_t elems = (size_t)nrows * ix->kp;
     __nv_bfloat16 *ra = nullptr, *rb = nullptr;
     SJ_TRY(dev_alloc_t(&ra, elems, s));
-    SJ_TRY(dev_alloc_t(&rb, elems, s));
     ix->rows_a = ra;
+    SJ_TRY(dev_alloc_t(&rb, elems, s));
     ix->rows_b = rb;
     SJ_CK(cudaMemsetAsync(ra, 0, elems * sizeof(__nv_bfloat16), s));
     SJ_CK(cudaMemsetAsync(rb, 0, elems * sizeof(__nv_bfloat16), s));
@@ -923,9 +1089,10 @@ int build_index(Index* ix, const double* pts) {
     cudaStream_t s = ix->stream;
     const int64_t n = ix->n;
     const int d = ix->d;
+    Scratch tmp(s);  // temporaries, released on every return
     // ---- extent and finiteness check (one sync) ----
     unsigned long long* ext = nullptr;
-    SJ_TRY(dev_alloc_t(&ext, (size_t)2 * d + 1, s));
+    SJ_TRY(tmp.alloc(&ext, (size_t)2 * d + 1));
     std::vector<unsigned long long> init(2 * d + 1);
     for (int k = 0; k < d; ++k) {
         init[k] = ~0ull;
@@ -945,7 +1112,6 @@ int build_index(Index* ix, const double* pts) {
     std::vector<unsigned long long> got(2 * d + 1);
     SJ_CK(cudaMemcpyAsync(got.data(), ext, got.size() * 8, cudaMemcpyDeviceToHost, s));
     SJ_CK(cudaStreamSynchronize(s));
-    dev_free(ext, s);
     if (*reinterpret_cast<int*>(&got[2 * d]) != 0) {
         set_error("non-finite coordinate in the input points");
         return SJ_ERR_ARG;
@@ -959,8 +1125,6 @@ int build_index(Index* ix, const double* pts) {
     SJ_TRY(choose_grid(ix));
 
     // ---- cell keys and sort ----
-    unsigned long long* keys = nullptr;
-    SJ_TRY(dev_alloc_t(&keys, (size_t)n, s));
     SJ_TRY(dev_alloc_t(&ix->perm, (size_t)n, s));
     GridParams gp{};
     gp.m = ix->m;
@@ -972,67 +1136,58 @@ int build_index(Index* ix, const double* pts) {
         gp.stride[i] = ix->stride[i];
     }
     // the key space: small enough (at most max(4 n, 2^22) keys) for a
-    // counting sort and a dense key -> cell table
+    // counting sort whose per-key first positions index the cells directly
     long double kspace = 1;
     for (int i = 0; i < ix->m; ++i) kspace *= (long double)ix->ncell[i];
     const bool dense = kspace <= (long double)std::max<int64_t>(4 * n, int64_t(1) << 22) &&
                        kspace < (long double)0x7FFFFFFF;
-    unsigned long long* dcount = nullptr;
-    SJ_TRY(dev_alloc_t(&dcount, 1, s));
-    uint32_t *flags = nullptr, *idx = nullptr, *bins = nullptr, *key32 = nullptr;
-    unsigned long long* ckey_tmp = nullptr;
+    const int qmax = item_qmax(ix);
+    const int64_t K = dense ? (int64_t)kspace : 0;
+    unsigned long long* off64 = nullptr;     // dense: K + 1 of (first position << 32 | first item)
+    unsigned long long* ckey_tmp = nullptr;  // sparse: cell table before the cell count is known
     int32_t* cstart_tmp = nullptr;
-    int32_t* table = nullptr;
+    unsigned long long* dcount = nullptr;
     if (dense) {
-        // ---- counting sort and cell table ----
-        const int64_t K = (int64_t)kspace;
-        const int64_t cap = std::min<int64_t>(n, K);  // non-empty cells at most
-        SJ_TRY(dev_alloc_t(&key32, (size_t)n, s));
-        SJ_TRY(dev_alloc_t(&bins, (size_t)K * 4, s));
-        uint32_t *cnt = bins, *fill = bins + K, *start = bins + 2 * K, *cidx = bins + 3 * K;
+        // ---- counting sort: per-key counts, one scan for first positions
+        // and first work items, scatter ----
+        uint32_t *key32 = nullptr, *bins = nullptr;
+        SJ_TRY(tmp.alloc(&key32, (size_t)n));
+        SJ_TRY(tmp.alloc(&bins, (size_t)K * 2));
+        SJ_TRY(tmp.alloc(&off64, (size_t)K + 1));
+        uint32_t *cnt = bins, *fill = bins + K;
         SJ_CK(cudaMemsetAsync(bins, 0, (size_t)K * 2 * sizeof(uint32_t), s));  // cnt and fill
         k_key_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, n, d, gp, key32, cnt);
         note_launch();
         SJ_CK(cudaGetLastError());
-        SJ_TRY(scan_exclusive_u32(cnt, start, K, s));
-        k_key_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(key32, n, start, fill, ix->perm);
+        SJ_TRY((scan_exclusive<unsigned long long, LoadCountItems>(LoadCountItems{cnt, (uint32_t)qmax}, off64, K,
+                                                                   true, s)));
+        k_key_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(key32, n, off64, fill, ix->perm);
         note_launch();
         SJ_CK(cudaGetLastError());
-        k_nonempty<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(cnt, K, fill);
-        note_launch();
-        SJ_CK(cudaGetLastError());
-        SJ_TRY(scan_exclusive_u32(fill, cidx, K, s));
-        SJ_TRY(dev_alloc_t(&ix->cell_key, (size_t)cap, s));
-        SJ_TRY(dev_alloc_t(&ix->cell_start, (size_t)cap + 1, s));
-        SJ_TRY(dev_alloc_t(&table, (size_t)K, s));
-        k_bins_to_cells<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(cnt, start, cidx, K, n, ix->cell_key,
-                                                                    ix->cell_start, table, dcount);
-        note_launch();
-        SJ_CK(cudaGetLastError());
-        dev_free(key32, s);
-        dev_free(bins, s);
-        dev_free(keys, s);
-        keys = nullptr;
     } else {
         // ---- radix sort and cell table ----
+        unsigned long long* keys = nullptr;
+        uint32_t *flags = nullptr, *idx = nullptr;
+        SJ_TRY(tmp.alloc(&keys, (size_t)n));
+        SJ_TRY(tmp.alloc(&dcount, 1));
         k_cell_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, n, d, gp, keys, ix->perm);
         note_launch();
         SJ_CK(cudaGetLastError());
         SJ_TRY(radix_sort_pairs(reinterpret_cast<uint64_t*>(keys), ix->perm, n, ix->key_bits, s));
-        SJ_TRY(dev_alloc_t(&flags, (size_t)n, s));
-        SJ_TRY(dev_alloc_t(&idx, (size_t)n, s));
+        SJ_TRY(tmp.alloc(&flags, (size_t)n));
+        SJ_TRY(tmp.alloc(&idx, (size_t)n));
         k_heads<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, flags);
         note_launch();
         SJ_CK(cudaGetLastError());
         SJ_TRY(scan_exclusive_u32(flags, idx, n, s));
-        SJ_TRY(dev_alloc_t(&ckey_tmp, (size_t)n, s));
-        SJ_TRY(dev_alloc_t(&cstart_tmp, (size_t)n + 1, s));
+        SJ_TRY(tmp.alloc(&ckey_tmp, (size_t)n));
+        SJ_TRY(tmp.alloc(&cstart_tmp, (size_t)n + 1));
         k_cells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, flags, idx, n, ckey_tmp, cstart_tmp, dcount);
         note_launch();
         SJ_CK(cudaGetLastError());
     }
 
-    // ---- packing (independent of the cell count) ----
+    // ---- packing (independent of the cells) ----
     SJ_TRY(dev_alloc_t(&ix->xs, (size_t)n * ix->dp, s));
     // kernel coordinates y = x - centre of the extent: |y_k| <= R_k / 2, which
     // keeps the norms in the expanded form (and the certified band) small
@@ -1060,25 +1215,86 @@ int build_index(Index* ix, const double* pts) {
         SJ_TRY(pack_points<double>(ix, pts, hp));
     if (tensor) SJ_TRY(pack_split_rows(ix));
     ix->filter_band_rel = 2.0 * (c1 > 0 ? c1 : 6.2 * gamma_n(u_t, ix->dp + 1)) * 2.0 * pbound / ix->e2;
+    ix->bound_c1 = c1 > 0 ? c1 : 6.2 * gamma_n(u_t, ix->dp + 1);
+    ix->bound_p = pbound;
 
+    if (dense) {
+        // ---- neighbour runs and work items, per key; one read-back at the
+        // end of the build ----
+        DenseEnum de{};
+        de.m = ix->m;
+        for (int i = 0; i < ix->m; ++i) {
+            de.ncell[i] = (uint32_t)ix->ncell[i];
+            de.stride[i] = (uint32_t)ix->stride[i];
+        }
+        de.symmetric = ix->opt.symmetric ? 1 : 0;
+        de.qmax = (uint32_t)qmax;
+        de.K = K;
+        uint32_t* run_cnt = nullptr;  // K counts, then K + 1 offsets
+        DenseTotals* dtot = nullptr;
+        SJ_TRY(tmp.alloc(&run_cnt, (size_t)2 * K + 1));
+        uint32_t* run_off = run_cnt + K;
+        SJ_TRY(tmp.alloc(&dtot, 1));
+        SJ_CK(cudaMemsetAsync(dtot, 0, sizeof(DenseTotals), s));
+        const unsigned eb = (unsigned)((K + 127) / 128);
+        k_denum<false><<<eb, 128, 0, s>>>(de, off64, run_cnt, nullptr, nullptr, nullptr, dtot);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        SJ_TRY((scan_exclusive<uint32_t, LoadU32>(LoadU32{run_cnt}, run_off, K, true, s)));
+        // upper bounds (non-empty cells <= min(n, K), each with at most
+        // 3^(m-1) + 1 runs and at most q / qmax + 1 items) size the run and
+        // item arrays without a read-back; when the run bound is large the
+        // exact count is read back first
+        int mm = ix->m > 0 ? ix->m - 1 : 0, per = 1;
+        for (int k = 0; k < mm; ++k) per *= 3;
+        const int64_t cells_max = std::min<int64_t>(n, K);
+        int64_t runs_cap = cells_max * (int64_t)(per + 1);
+        const int64_t items_cap = cells_max + n / qmax + 1;
+        if (runs_cap * (int64_t)sizeof(Run) > (int64_t(1) << 30)) {
+            uint32_t total = 0;
+            SJ_CK(cudaMemcpyAsync(&total, run_off + K, 4, cudaMemcpyDeviceToHost, s));
+            SJ_CK(cudaStreamSynchronize(s));
+            runs_cap = (int64_t)total;
+        }
+        SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(runs_cap, 1), s));
+        SJ_TRY(dev_alloc_t(&ix->items, (size_t)std::max<int64_t>(items_cap, 1), s));
+        k_denum<true><<<eb, 128, 0, s>>>(de, off64, nullptr, run_off, ix->runs, ix->items, nullptr);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        struct {
+            DenseTotals t;
+            unsigned long long last_off;
+            uint32_t runs;
+        } got{};
+        SJ_CK(cudaMemcpyAsync(&got.t, dtot, sizeof(DenseTotals), cudaMemcpyDeviceToHost, s));
+        SJ_CK(cudaMemcpyAsync(&got.last_off, off64 + K, 8, cudaMemcpyDeviceToHost, s));
+        SJ_CK(cudaMemcpyAsync(&got.runs, run_off + K, 4, cudaMemcpyDeviceToHost, s));
+        SJ_CK(cudaStreamSynchronize(s));
+        ix->n_cells = (int64_t)got.t.n_cells;
+        ix->n_runs = (int64_t)got.runs;
+        ix->n_items = (int64_t)(got.last_off & 0xFFFFFFFFull);
+        ix->n_candidates =
+            de.symmetric ? (int64_t)(2 * got.t.n_evaluated - got.t.sum_sq) : (int64_t)got.t.n_evaluated;
+        ix->n_evaluated = (int64_t)(got.t.n_evaluated - (uses_triangle(ix) ? got.t.tri_skip : 0ull));
+        if ((int64_t)(got.last_off >> 32) != n || ix->n_runs > runs_cap || ix->n_items > items_cap) {
+            set_error("internal: dense index sizes inconsistent (%lld points, %lld runs, %lld items)",
+                      (long long)(got.last_off >> 32), (long long)ix->n_runs, (long long)ix->n_items);
+            return SJ_ERR_CUDA;
+        }
+        SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
+        return SJ_OK;
+    }
+
+    // ---- sparse key space: cell table, neighbour runs and items (one sync
+    // for the cell count, one for the totals) ----
     unsigned long long M = 0;
     SJ_CK(cudaMemcpyAsync(&M, dcount, 8, cudaMemcpyDeviceToHost, s));
     SJ_CK(cudaStreamSynchronize(s));
     ix->n_cells = (int64_t)M;
-    if (!dense) {
-        SJ_TRY(dev_alloc_t(&ix->cell_key, (size_t)M, s));
-        SJ_TRY(dev_alloc_t(&ix->cell_start, (size_t)M + 1, s));
-        SJ_CK(cudaMemcpyAsync(ix->cell_key, ckey_tmp, M * 8, cudaMemcpyDeviceToDevice, s));
-        SJ_CK(cudaMemcpyAsync(ix->cell_start, cstart_tmp, (M + 1) * 4, cudaMemcpyDeviceToDevice, s));
-    }
-    dev_free(ckey_tmp, s);
-    dev_free(cstart_tmp, s);
-    dev_free(keys, s);
-    dev_free(flags, s);
-    dev_free(idx, s);
-    dev_free(dcount, s);
-
-    // ---- neighbour runs and items (one sync for the totals) ----
+    SJ_TRY(dev_alloc_t(&ix->cell_key, (size_t)M, s));
+    SJ_TRY(dev_alloc_t(&ix->cell_start, (size_t)M + 1, s));
+    SJ_CK(cudaMemcpyAsync(ix->cell_key, ckey_tmp, M * 8, cudaMemcpyDeviceToDevice, s));
+    SJ_CK(cudaMemcpyAsync(ix->cell_start, cstart_tmp, (M + 1) * 4, cudaMemcpyDeviceToDevice, s));
     EnumParams ep{};
     ep.m = ix->m;
     for (int i = 0; i < ix->m; ++i) {
@@ -1086,24 +1302,16 @@ int build_index(Index* ix, const double* pts) {
         ep.stride[i] = ix->stride[i];
     }
     ep.symmetric = ix->opt.symmetric ? 1 : 0;
-    ep.qmax = item_qmax(ix);
+    ep.qmax = qmax;
     const int64_t Mc = (int64_t)M;
-    // the dense key -> cell table (from the counting sort) makes neighbour
-    // lookups O(1); otherwise they binary-search the cell keys.  A grid of no
-    // indexed dims has one cell and needs no lookups.
-    if (ix->m == 0 && table) {
-        dev_free(table, s);
-        table = nullptr;
-    }
-    ep.table = table;
     ep.local_mask = ~0ull;
     uint32_t *run_cnt, *item_cnt, *run_off, *item_off;
     EnumTotals* dtot;
-    SJ_TRY(dev_alloc_t(&run_cnt, (size_t)Mc * 4, s));
+    SJ_TRY(tmp.alloc(&run_cnt, (size_t)Mc * 4));
     item_cnt = run_cnt + Mc;
     run_off = run_cnt + 2 * Mc;
     item_off = run_cnt + 3 * Mc;
-    SJ_TRY(dev_alloc_t(&dtot, 1, s));
+    SJ_TRY(tmp.alloc(&dtot, 1));
     SJ_CK(cudaMemsetAsync(dtot, 0, sizeof(EnumTotals), s));
     const unsigned eb = (unsigned)((Mc + 127) / 128);
     k_enum_count<<<eb, 128, 0, s>>>(ep, ix->cell_key, ix->cell_start, Mc, run_cnt, item_cnt, dtot);
@@ -1121,7 +1329,6 @@ int build_index(Index* ix, const double* pts) {
     ix->n_evaluated = (int64_t)(tot.n_evaluated - (uses_triangle(ix) ? tot.tri_skip : 0ull));
     if (tot.n_runs >= 0xFFFFFFFFull || tot.n_items >= 0x7FFFFFFFull) {
         set_error("index too large: %llu runs, %llu items", tot.n_runs, tot.n_items);
-        dev_free(table, s);
         return SJ_ERR_ARG;
     }
     SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(ix->n_runs, 1), s));
@@ -1129,9 +1336,6 @@ int build_index(Index* ix, const double* pts) {
     k_enum_fill<<<eb, 128, 0, s>>>(ep, ix->cell_key, ix->cell_start, Mc, run_off, item_off, ix->runs, ix->items);
     note_launch();
     SJ_CK(cudaGetLastError());
-    dev_free(run_cnt, s);
-    dev_free(dtot, s);
-    dev_free(table, s);
     SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
     return SJ_OK;
 }
@@ -1165,10 +1369,10 @@ int pack_params_fill(void* host_pp, const double* lo, int d, int dp, double eps,
     return SJ_OK;
 }
 
-int launch_pack_f64_raw(const double* pts, const int32_t* perm, int64_t n, const void* pp_dev, double* xs, double* y,
+int launch_pack_f64_raw(const double* pts, const int32_t* perm, int64_t n, const void* host_pp, double* xs, double* y,
                         double* h, double* to, double* ti, cudaStream_t s) {
-    k_pack<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, perm, n, static_cast<const PackParams*>(pp_dev),
-                                                             xs, y, h, to, ti);
+    k_pack<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, perm, n, *static_cast<const PackParams*>(host_pp),
+                                                             xs, y, h, to, ti, nullptr);
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
@@ -1373,7 +1577,6 @@ __device__ __forceinline__ EnumParams benum_params(const BEnum& b, const BInst& 
     }
     e.symmetric = b.symmetric;
     e.qmax = b.qmax;
-    e.table = nullptr;
     e.local_mask = (1ull << b.shift) - 1ull;
     return e;
 }
@@ -1459,15 +1662,18 @@ __global__ void k_benum_fill(BEnum b, const BInst* __restrict__ P, const unsigne
 // the cell count.
 static int build_cells(const unsigned long long* keys, int64_t n, unsigned long long** cell_key, int32_t** cell_start,
                        int64_t* n_cells, cudaStream_t s) {
+    Scratch tmp(s);
     uint32_t *flags = nullptr, *idx = nullptr;
     unsigned long long* dcount = nullptr;
     unsigned long long* ck = nullptr;
     int32_t* cs = nullptr;
-    SJ_TRY(dev_alloc_t(&flags, (size_t)n, s));
-    SJ_TRY(dev_alloc_t(&idx, (size_t)n, s));
-    SJ_TRY(dev_alloc_t(&dcount, 1, s));
+    SJ_TRY(tmp.alloc(&flags, (size_t)n));
+    SJ_TRY(tmp.alloc(&idx, (size_t)n));
+    SJ_TRY(tmp.alloc(&dcount, 1));
     SJ_TRY(dev_alloc_t(&ck, (size_t)n, s));
+    *cell_key = ck;  // owned by the caller's index from here on
     SJ_TRY(dev_alloc_t(&cs, (size_t)n + 1, s));
+    *cell_start = cs;
     k_heads<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, flags);
     note_launch();
     SJ_CK(cudaGetLastError());
@@ -1478,9 +1684,6 @@ static int build_cells(const unsigned long long* keys, int64_t n, unsigned long 
     unsigned long long M = 0;
     SJ_CK(cudaMemcpyAsync(&M, dcount, 8, cudaMemcpyDeviceToHost, s));
     SJ_CK(cudaStreamSynchronize(s));
-    dev_free(flags, s);
-    dev_free(idx, s);
-    dev_free(dcount, s);
     *cell_key = ck;
     *cell_start = cs;
     *n_cells = (int64_t)M;
@@ -1490,6 +1693,7 @@ static int build_cells(const unsigned long long* keys, int64_t n, unsigned long 
 int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const int32_t* d_of_host) {
     Index* ix = &g->ix;
     cudaStream_t s = ix->stream;
+    Scratch tmp(s);  // temporaries, released on every return
     const int K = g->n_inst;
     const int dp = ix->dp;
     const int64_t n = ix->n;
@@ -1497,12 +1701,12 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     SJ_TRY(dev_alloc_t(&g->d_off, (size_t)K + 1, s));
     SJ_CK(cudaMemcpyAsync(g->d_off, g->off.data(), (K + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
     int32_t* inst_of = nullptr;
-    SJ_TRY(dev_alloc_t(&inst_of, (size_t)n, s));
+    SJ_TRY(tmp.alloc(&inst_of, (size_t)n));
     // the instances' arrays are read in place
     const double** dsrc = nullptr;
     int32_t* dd = nullptr;
-    SJ_TRY(dev_alloc_t(&dsrc, (size_t)K, s));
-    SJ_TRY(dev_alloc_t(&dd, (size_t)K, s));
+    SJ_TRY(tmp.alloc(&dsrc, (size_t)K));
+    SJ_TRY(tmp.alloc(&dd, (size_t)K));
     SJ_CK(cudaMemcpyAsync(dsrc, src_dev_ptrs, K * sizeof(double*), cudaMemcpyHostToDevice, s));
     SJ_CK(cudaMemcpyAsync(dd, d_of_host, K * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     k_binst<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->d_off, K, n, inst_of);
@@ -1520,9 +1724,9 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     int32_t* dblk_inst = nullptr;
     long long* dblk_start = nullptr;
     unsigned long long* ext = nullptr;
-    SJ_TRY(dev_alloc_t(&dblk_inst, (size_t)nblk, s));
-    SJ_TRY(dev_alloc_t(&dblk_start, (size_t)nblk, s));
-    SJ_TRY(dev_alloc_t(&ext, (size_t)K * (2 * dp + 1), s));
+    SJ_TRY(tmp.alloc(&dblk_inst, (size_t)nblk));
+    SJ_TRY(tmp.alloc(&dblk_start, (size_t)nblk));
+    SJ_TRY(tmp.alloc(&ext, (size_t)K * (2 * dp + 1)));
     SJ_CK(cudaMemcpyAsync(dblk_inst, hblk_inst.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     SJ_CK(cudaMemcpyAsync(dblk_start, hblk_start.data(), nblk * sizeof(long long), cudaMemcpyHostToDevice, s));
     {
@@ -1535,12 +1739,9 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
                                                                          dp, ext);
     note_launch();
     SJ_CK(cudaGetLastError());
-    dev_free(dblk_inst, s);
-    dev_free(dblk_start, s);
     std::vector<unsigned long long> hext((size_t)K * (2 * dp + 1));
     SJ_CK(cudaMemcpyAsync(hext.data(), ext, hext.size() * 8, cudaMemcpyDeviceToHost, s));
     SJ_CK(cudaStreamSynchronize(s));
-    dev_free(ext, s);
     int inst_bits = 0;
     while ((1ll << inst_bits) < K) ++inst_bits;
     std::vector<BInst> hp((size_t)K);
@@ -1608,32 +1809,34 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     }
     BInst* dP = nullptr;
     double* dcentre = nullptr;
-    SJ_TRY(dev_alloc_t(&dP, (size_t)K, s));
-    SJ_TRY(dev_alloc_t(&dcentre, (size_t)K * dp, s));
+    SJ_TRY(tmp.alloc(&dP, (size_t)K));
+    SJ_TRY(tmp.alloc(&dcentre, (size_t)K * dp));
     SJ_TRY(dev_alloc_t(&g->d_e2, (size_t)K, s));
     SJ_CK(cudaMemcpyAsync(dP, hp.data(), K * sizeof(BInst), cudaMemcpyHostToDevice, s));
     SJ_CK(cudaMemcpyAsync(dcentre, centre.data(), centre.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     SJ_CK(cudaMemcpyAsync(g->d_e2, e2.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
     // ---- keys, sort, cells ----
     unsigned long long* keys = nullptr;
-    SJ_TRY(dev_alloc_t(&keys, (size_t)n, s));
+    SJ_TRY(tmp.alloc(&keys, (size_t)n));
     SJ_TRY(dev_alloc_t(&ix->perm, (size_t)n, s));
     k_bkeys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dsrc, dd, g->d_off, n, inst_of, dP, shift, keys, ix->perm);
     note_launch();
     SJ_CK(cudaGetLastError());
     SJ_TRY(radix_sort_pairs(reinterpret_cast<uint64_t*>(keys), ix->perm, n, shift + inst_bits, s));
     SJ_TRY(build_cells(keys, n, &ix->cell_key, &ix->cell_start, &ix->n_cells, s));
-    dev_free(keys, s);
     // ---- packing ----
     SJ_TRY(dev_alloc_t(&ix->xs, (size_t)n * dp, s));
     SJ_TRY(dev_alloc_t(&g->d_inst_of_sorted, (size_t)n, s));
     if (use_f32) {
         float *y, *h, *to, *ti;
         SJ_TRY(dev_alloc_t(&y, (size_t)n * dp, s));
+        ix->y = y;
         SJ_TRY(dev_alloc_t(&h, (size_t)n, s));
+        ix->h = h;
         SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
+        ix->thr_out = to;
         SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
-        ix->y = y, ix->h = h, ix->thr_out = to, ix->thr_in = ti;
+        ix->thr_in = ti;
         if (dp <= 32)
             k_bpack_lanes<float><<<(unsigned)((n * dp + 255) / 256), 256, 0, s>>>(
                 dsrc, dd, g->d_off, ix->perm, inst_of, dP, dcentre, n, dp, ix->xs, y, h, to, ti, g->d_inst_of_sorted);
@@ -1644,10 +1847,13 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     } else {
         double *y, *h, *to, *ti;
         SJ_TRY(dev_alloc_t(&y, (size_t)n * dp, s));
+        ix->y = y;
         SJ_TRY(dev_alloc_t(&h, (size_t)n, s));
+        ix->h = h;
         SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
+        ix->thr_out = to;
         SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
-        ix->y = y, ix->h = h, ix->thr_out = to, ix->thr_in = ti;
+        ix->thr_in = ti;
         if (dp <= 32)
             k_bpack_lanes<double><<<(unsigned)((n * dp + 255) / 256), 256, 0, s>>>(
                 dsrc, dd, g->d_off, ix->perm, inst_of, dP, dcentre, n, dp, ix->xs, y, h, to, ti, g->d_inst_of_sorted);
@@ -1659,19 +1865,20 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     note_launch();
     SJ_CK(cudaGetLastError());
     if (tensor) SJ_TRY(pack_split_rows(ix));
+    if (wants_aux(ix)) SJ_TRY(build_aux(ix));
     // perm now maps packed points to their place in the group; the join
     // subtracts the instance's first position to get instance-local indices
     // ---- runs and items (one read-back) ----
     const int64_t M = ix->n_cells;
     BEnum be{shift, ix->opt.symmetric ? 1 : 0, item_qmax(ix)};
     uint32_t* cnt = nullptr;
-    SJ_TRY(dev_alloc_t(&cnt, (size_t)M * 4, s));
+    SJ_TRY(tmp.alloc(&cnt, (size_t)M * 4));
     uint32_t *run_cnt = cnt, *item_cnt = cnt + M, *run_off = cnt + 2 * M, *item_off = cnt + 3 * M;
     unsigned long long* ev = nullptr;
-    SJ_TRY(dev_alloc_t(&ev, (size_t)3 * K, s));
+    SJ_TRY(tmp.alloc(&ev, (size_t)3 * K));
     SJ_CK(cudaMemsetAsync(ev, 0, 3 * K * sizeof(unsigned long long), s));
     EnumTotals* dtot = nullptr;
-    SJ_TRY(dev_alloc_t(&dtot, 1, s));
+    SJ_TRY(tmp.alloc(&dtot, 1));
     SJ_CK(cudaMemsetAsync(dtot, 0, sizeof(EnumTotals), s));
     k_benum_count<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(be, dP, ix->cell_key, ix->cell_start, M, run_cnt,
                                                               item_cnt, ev, ev + K, ev + 2 * K, dtot);
@@ -1707,14 +1914,6 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
                                                              item_off, ix->runs, ix->items, g->d_item_inst);
     note_launch();
     SJ_CK(cudaGetLastError());
-    dev_free(cnt, s);
-    dev_free(ev, s);
-    dev_free(dtot, s);
-    dev_free(dP, s);
-    dev_free(dcentre, s);
-    dev_free(dsrc, s);
-    dev_free(dd, s);
-    dev_free(inst_of, s);
     SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
     return SJ_OK;
 }

@@ -50,6 +50,26 @@ int dev_alloc_t(T** p, size_t count, cudaStream_t s) {
 
 bool is_device_pointer(const void* p);
 
+// Device temporaries of one host routine: every block taken through it is
+// freed (stream-ordered) when it goes out of scope, on success and on every
+// error return alike.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    ~Scratch() {
+        for (void* p : ptrs) dev_free(p, s);
+    }
+    template <typename T>
+    int alloc(T** p, size_t count) {
+        const int st = dev_alloc_t(p, count, s);
+        if (st == SJ_OK) ptrs.push_back(*p);
+        return st;
+    }
+};
+
 // ---- work item and candidate run ---------------------------------------------
 // A work item: queries [q0, q1) of one cell (sorted positions) and the cell's
 // candidate runs [r0, r1) in the run array.
@@ -89,6 +109,8 @@ struct Index {
     void* h = nullptr;          // n: -||y||^2 / 2
     void* thr_out = nullptr;    // n: maybe-in threshold on (y_q.y_c - ||y_q||^2/2)
     void* thr_in = nullptr;     // n: certain-in threshold
+    void* aux = nullptr;        // FP32 filter, padded d <= 8: n float4 records
+                                // (thr_out, thr_in, input index bits, 0)
     int32_t* perm = nullptr;    // sorted position -> input index
     void* rows_a = nullptr;     // tensor-core filter: n x kp bf16 split rows, candidate role
     void* rows_b = nullptr;     // n x kp bf16 split rows, query role
@@ -99,6 +121,7 @@ struct Index {
     Item* items = nullptr;
     int64_t n_cells = 0, n_runs = 0, n_items = 0, n_candidates = 0, n_evaluated = 0;
     double filter_band_rel = 0;  // predicted certified band (relative to eps^2)
+    double bound_c1 = 0, bound_p = 0;  // certified bound E = c1 (P + pc) of the filter
 
     // per-join scratch: counters (item queue, result cursor, recheck count,
     // recheck queue fill)
@@ -179,8 +202,20 @@ struct JoinOut {
     int2* band = nullptr;          // deferred-recheck queue
     unsigned long long band_cap = 0;
     const void* batch = nullptr;   // device BatchJoin of a batched join, or null
+    int4* dbg = nullptr;           // filter dump (sj_debug_filter_dump), or null
+    unsigned long long dbg_cap = 0;
 };
 int launch_join_cc(Index* ix, const JoinOut& out, int emit_dist);
+// The small-d FP32 filter without distances (sj_join_f32s.cu).
+bool f32s_supported(const Index* ix, int emit_dist);
+int launch_join_f32s(Index* ix, const JoinOut& out);
+// Whether an index gets the per-point records of that kernel.
+inline bool wants_aux(const Index* ix) { return ix->kernel == SJ_KERNEL_FILTER_F32 && ix->dp <= 8; }
+int build_aux(Index* ix);
+// Pair evaluations of each work item of a built index (n_items values), as
+// the tile kernels perform them (self-cell runs from the item's first query
+// in joins that evaluate triangles).
+int launch_item_work(Index* ix, long long* work);
 int launch_join_tc(Index* ix, const JoinOut& out, int emit_dist);
 int selftest_bounded_wait(cudaStream_t s);
 int launch_recheck(Index* ix, const JoinOut& out, int emit_dist);

@@ -37,9 +37,26 @@ struct JoinParams {
     int2* band;
     unsigned long long band_cap;
     const BatchJoin* batch;  // null for a single join
+    const float4* aux;       // small-d FP32 filter: per point (thr_out, thr_in, input index bits, 0)
+    // test aid (sj_debug_filter_dump): when set, the FP32 filters record
+    // every evaluated (query, candidate) pair with their filter value a as
+    // (query sorted position, candidate sorted position, bits of a, 0);
+    // counters[5] counts records, those past dbg_cap are dropped
+    int4* dbg;
+    unsigned long long dbg_cap;
 };
 
+// Records one evaluated pair for the filter dump.
+__device__ __forceinline__ void dbg_record(const JoinParams& P, int32_t qs, int32_t cs, float a) {
+    const unsigned long long k = atomicAdd(&P.counters[5], 1ull);
+    if (k < P.dbg_cap) P.dbg[k] = make_int4(qs, cs, __float_as_int(a), 0);
+}
+
 JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist);
+// CUDA-core tile launch for padded dimension DP (sj_join_cc.cuh; explicit
+// instantiations in sj_cc_d*.cu).
+template <typename T, int DP>
+int launch_cc_dp(Index* ix, const JoinParams& p);
 
 // Fused multiply-add in the kernel type, one rounding (explicit intrinsics so
 // a float chain never runs on the FP64 pipe).
@@ -71,10 +88,11 @@ __device__ __forceinline__ double direct_sq(const double* __restrict__ a, const 
 }
 
 struct WarpStage {
-    int2* pairs;   // kStage slots of this warp
-    double* dist;  // kStage slots (used when distances are emitted)
+    int2* pairs;   // cap slots of this warp
+    double* dist;  // cap slots (used when distances are emitted)
     int cnt;       // warp-uniform fill
     int gid;       // batched join: the instance the staged pairs belong to
+    int cap = kStage;  // slots
 };
 
 // Batched join: the slot of pair position p of instance gid in the shared
@@ -115,6 +133,7 @@ __device__ __forceinline__ int32_t batch_page(const BatchJoin& B, int gid, unsig
 }
 
 static_assert(kStage / 64 + 1 <= 32, "a warp's flush must touch at most 32 pages");
+constexpr int kStageMax = 31 * 64;  // largest stage whose flush touches at most 32 pages of 64
 
 // Pool slot of position p of instance gid's result, or -1.
 __device__ __forceinline__ long long batch_slot(const BatchJoin& B, int gid, unsigned long long p) {
@@ -134,8 +153,8 @@ __device__ __forceinline__ void stage_flush(WarpStage& st, const JoinParams& P, 
         if (lane == 0 && st.cnt > 0) base = atomicAdd(&B.cursor[st.gid], (unsigned long long)st.cnt);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (st.cnt > 0) {
-            // pages of at least 64 pairs: a flush of <= kStage pairs touches
-            // at most kStage / 64 + 1 <= 32 pages, one lane resolves each
+            // pages of at least 64 pairs: a flush of <= kStageMax pairs
+            // touches at most 32 pages, one lane resolves each
             const unsigned long long pg0 = base >> B.page_log2;
             const int npg = (int)(((base + (unsigned long long)st.cnt - 1ull) >> B.page_log2) - pg0) + 1;
             const int32_t mine = lane < npg ? batch_page(B, st.gid, pg0 + (unsigned long long)lane) : -1;
@@ -215,7 +234,7 @@ __device__ __forceinline__ void stage_emit(WarpStage& st, const JoinParams& P, i
     const unsigned b2 = __ballot_sync(0xffffffffu, nout == 2);
     const int tot = __popc(b1) + __popc(b2);
     if (tot == 0) return;
-    if (st.cnt + tot > kStage) stage_flush(st, P, lane);
+    if (st.cnt + tot > st.cap) stage_flush(st, P, lane);
     const int pos = st.cnt + __popc(b1 & lt) + __popc(b2 & lt);
     if (nout >= 1) {
         st.pairs[pos] = make_int2(qid, cid);
@@ -236,7 +255,7 @@ __device__ __forceinline__ void stage_emit_pairs(WarpStage& st, const JoinParams
     const unsigned b2 = __ballot_sync(0xffffffffu, nout == 2);
     const int tot = __popc(b1) + __popc(b2);
     if (tot == 0) return;
-    if (st.cnt + tot > kStage) stage_flush(st, P, lane);
+    if (st.cnt + tot > st.cap) stage_flush(st, P, lane);
     const int pos = st.cnt + __popc(b1 & lt) + __popc(b2 & lt);
     if (nout >= 1) st.pairs[pos] = make_int2(qid, cid);
     if (nout == 2) st.pairs[pos + 1] = make_int2(cid, qid);

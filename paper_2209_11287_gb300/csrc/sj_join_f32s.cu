@@ -1,0 +1,416 @@
+// Certified FP32 distance tiles for small dimensions (padded d <= 8), without
+// distances: the filter of the low-precision join on CUDA cores, fused with
+// the eps threshold and the compaction into result pages.
+//
+// What a tile computes is the same as k_join_cc<float> (sj_join_cc.cu): per
+// (query q, candidate c) of a work item (the queries of one grid cell and the
+// candidate runs of its neighbourhood, Sec. III-B),
+//     a = -||y_q||^2 / 2 + sum_k y_qk * y_ck        (fma chain, k ascending)
+// the expanded form of Eq. 3 with the candidate's norm moved into its two
+// certified thresholds: a < thr_out means out, a >= thr_in means in, and the
+// pairs in between are re-decided by the binary64 decision rule (k_recheck).
+// Only the instruction stream differs; the kernel is bound by instruction
+// issue, so every step is shaped to spend few instructions per pair:
+//
+//  * each lane holds TC candidates in registers as pairs (paired FMA over two
+//    candidates, one rounding per component as the scalar FMA), the query
+//    rows sit in shared memory with every coordinate duplicated, so a query
+//    coordinate is one operand of the paired FMA without repacking;
+//  * the threshold tests are paired adds a + (-thr): the sign of a
+//    round-to-nearest sum is the sign of the exact sum (zero only when the
+//    operands cancel exactly, which gives +0 since -thr is never -0), so the
+//    sign bit is the test a < thr; a funnel shift moves it into the lane's
+//    miss mask (queries are visited last to first, so bit q is query q);
+//  * a candidate's thresholds and input index come in one 16-byte record,
+//    its coordinates in one more load (two for d = 8);
+//  * a lane walks the item's runs with a cursor (slots only grow), instead of
+//    searching the run list for every slot;
+//  * chunks of 32 TC slots (with TC > 2: while they fill, then chunks of 64
+//    for the tail);
+//  * emission: one warp scan of the lanes' output counts, then each lane
+//    writes its pairs straight into the warp's shared-memory stage (both
+//    orders for pairs of adjacent cells and for the self-cell triangle); a
+//    chunk whose output would not fit the stage takes a general path that
+//    emits one pair per lane per round.
+#include "sj_join_common.cuh"
+
+namespace sj {
+
+// Candidate slots per lane of the main chunks (register budget: 2 for d = 8)
+// and pairs in a warp's stage (a main chunk emits about 32 TC x the mean
+// queries per item x 13% x 2 pairs on the uniform workloads; the stage holds
+// a typical chunk's output).  Compile-time tuning constants.
+#ifndef SJ_F32S_TC_SMALL
+#define SJ_F32S_TC_SMALL 2
+#endif
+#ifndef SJ_F32S_STAGE
+#define SJ_F32S_STAGE 512
+#endif
+template <int DP>
+constexpr int f32s_tc() { return DP <= 4 ? SJ_F32S_TC_SMALL : 2; }
+constexpr int kF32sStage = SJ_F32S_STAGE;
+static_assert(kF32sStage <= kStageMax, "a stage flush resolves at most 32 pages");
+
+template <int DP, int RUNS>
+struct F32sWarp {
+    float2 qd[kQMax][DP];  // query coordinates, each as (v, v)
+    float2 qh2[kQMax];     // (h, h), h = -||y_q||^2 / 2
+    int32_t qid[kQMax];    // output index of each query (batched: instance-local)
+    int32_t rstart[RUNS];  // first sorted position of each run
+    uint32_t rpre[RUNS + 1];  // prefix of the run lengths
+    uint8_t rmir[RUNS];    // 0 plain, 1 mirrored, 2 self-cell triangle
+    int32_t cj[32 * f32s_tc<DP>()];   // per slot of a chunk: sorted position
+    int32_t cid[32 * f32s_tc<DP>()];  // per slot: output index
+    int2 stage[kF32sStage];
+};
+
+// Candidate coordinates of one point as DP floats, loaded with vector loads.
+template <int DP>
+__device__ __forceinline__ void load_coords(const float* __restrict__ Y, int32_t j, float (&c)[DP]) {
+    if constexpr (DP == 2) {
+        const float2 v = reinterpret_cast<const float2*>(Y)[j];
+        c[0] = v.x;
+        c[1] = v.y;
+    } else {
+#pragma unroll
+        for (int h = 0; h < DP / 4; ++h) {
+            const float4 v = reinterpret_cast<const float4*>(Y)[(int64_t)j * (DP / 4) + h];
+            c[4 * h] = v.x;
+            c[4 * h + 1] = v.y;
+            c[4 * h + 2] = v.z;
+            c[4 * h + 3] = v.w;
+        }
+    }
+}
+
+// (mask << 1) | sign bit of v: one funnel shift.
+__device__ __forceinline__ uint32_t push_sign(uint32_t mask, float v) {
+    return __funnelshift_l(__float_as_uint(v), mask, 1);
+}
+
+// One chunk of 32 TC candidate slots [base, base + 32 TC) against the item's
+// Q queries.  `r` is the lane's run cursor (kept across chunks).
+template <int DP, int RUNS, int TC, bool DBG>
+__device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st, const JoinParams& P,
+                                           const Item& I, const ItemRoute& R, int Q, uint32_t C, uint32_t base,
+                                           int lane, int& r, unsigned long long& rechecked) {
+    static_assert(TC % 2 == 0, "candidates go in pairs");
+    const float* __restrict__ Y = static_cast<const float*>(P.y);
+    const float4* __restrict__ AUX = P.aux;
+
+    float2 cy[TC / 2][DP];  // candidate pairs, per dim
+    float2 nto[TC / 2], nti[TC / 2];  // negated thresholds, never -0
+    // per slot, 8 bits: the run flag (bits 0-1) and, for a self-cell
+    // candidate among the item's queries, 1 + its query index (bits 2-7)
+    uint32_t meta = 0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t) {
+        const uint32_t v = base + (uint32_t)(t * 32 + lane);
+        float c[DP];
+        float to = INFINITY, ti = INFINITY;
+        if (v < C) {
+            while (W.rpre[r + 1] <= v) ++r;
+            const int32_t jj = W.rstart[r] + (int32_t)(v - W.rpre[r]);
+            const uint32_t f = W.rmir[r];
+            load_coords<DP>(Y, jj, c);
+            const float4 ax = AUX[jj];
+            to = ax.x;
+            ti = ax.y;
+            W.cj[t * 32 + lane] = jj;
+            W.cid[t * 32 + lane] = (int32_t)(__float_as_int(ax.z) - (int32_t)R.off);
+            // self-cell triangle: queries q0 .. jj pair with jj
+            const uint32_t dg1 = (f == 2 && jj < I.q1) ? (uint32_t)(jj - I.q0 + 1) : 0u;
+            meta |= (f | (dg1 << 2)) << (8 * t);
+        } else {
+#pragma unroll
+            for (int k = 0; k < DP; ++k) c[k] = 0.f;
+        }
+        const float nt_o = __fsub_rn(0.f, to), nt_i = __fsub_rn(0.f, ti);
+        if (t & 1) {
+#pragma unroll
+            for (int k = 0; k < DP; ++k) cy[t / 2][k].y = c[k];
+            nto[t / 2].y = nt_o;
+            nti[t / 2].y = nt_i;
+        } else {
+#pragma unroll
+            for (int k = 0; k < DP; ++k) cy[t / 2][k].x = c[k];
+            nto[t / 2].x = nt_o;
+            nti[t / 2].x = nt_i;
+        }
+    }
+
+    // miss masks: bit q set <=> a(q, slot) < thr
+    uint32_t mo[TC], mi[TC];
+#pragma unroll
+    for (int t = 0; t < TC; ++t) mo[t] = mi[t] = 0u;
+    const float2* __restrict__ qrow = &W.qd[Q - 1][0];
+    const float2* __restrict__ qh = &W.qh2[Q - 1];
+#pragma unroll
+    for (int qq = 0; qq < kQMax; ++qq) {
+        if (qq >= Q) break;
+        const float2 h2 = qh[-qq];
+        float2 qv[DP];
+#pragma unroll
+        for (int k = 0; k < DP; ++k) qv[k] = qrow[k - qq * DP];
+#pragma unroll
+        for (int p = 0; p < TC / 2; ++p) {
+            float2 a = h2;
+#pragma unroll
+            for (int k = 0; k < DP; ++k) a = __ffma2_rn(qv[k], cy[p][k], a);
+            const float2 dout = __fadd2_rn(a, nto[p]);
+            const float2 din = __fadd2_rn(a, nti[p]);
+            mo[2 * p] = push_sign(mo[2 * p], dout.x);
+            mo[2 * p + 1] = push_sign(mo[2 * p + 1], dout.y);
+            mi[2 * p] = push_sign(mi[2 * p], din.x);
+            mi[2 * p + 1] = push_sign(mi[2 * p + 1], din.y);
+            if constexpr (DBG) {
+                const int q = Q - 1 - qq;
+                if (base + (uint32_t)(2 * p * 32 + lane) < C)
+                    dbg_record(P, I.q0 + q, W.cj[2 * p * 32 + lane], a.x);
+                if (base + (uint32_t)((2 * p + 1) * 32 + lane) < C)
+                    dbg_record(P, I.q0 + q, W.cj[(2 * p + 1) * 32 + lane], a.y);
+            }
+        }
+    }
+
+    // classify: certain-in (emitted now) and uncertain (re-decided later)
+    const uint32_t qm = (1u << Q) - 1u;  // Q <= 16
+    uint32_t cin[TC], unc[TC];
+    int nout = 0;
+    uint32_t any_unc = 0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t) {
+        const uint32_t f = (meta >> (8 * t)) & 3u;
+        const uint32_t dg1 = (meta >> (8 * t + 2)) & 63u;
+        const uint32_t tri = dg1 ? (1u << dg1) - 1u : 0xFFFFFFFFu;
+        const uint32_t mb = ~mo[t] & qm & tri;
+        cin[t] = ~mi[t] & mb;
+        unc[t] = mb & mi[t];
+        any_unc |= unc[t];
+        const int c = __popc(cin[t]);
+        nout += f ? 2 * c : c;
+        if (dg1 && ((cin[t] >> (dg1 - 1u)) & 1u)) nout -= 1;  // the diagonal once
+    }
+    int total;
+    const int off = warp_excl_scan(nout, lane, &total);
+    if (total > 0) {
+        if (st.cnt + total > st.cap) stage_flush(st, P, lane);
+        if (st.cnt + total <= st.cap) {
+            // the common case: the chunk's output fits the stage
+            int pos = st.cnt + off;
+#pragma unroll
+            for (int t = 0; t < TC; ++t) {
+                uint32_t b = cin[t];
+                if (!b) continue;
+                const bool two = ((meta >> (8 * t)) & 3u) != 0u;
+                const int dg = (int)((meta >> (8 * t + 2)) & 63u) - 1;
+                const int32_t ci = W.cid[t * 32 + lane];
+                while (b) {
+                    const int q = __ffs(b) - 1;
+                    b &= b - 1u;
+                    const int32_t qi = W.qid[q];
+                    st.pairs[pos++] = make_int2(qi, ci);
+                    if (two && q != dg) st.pairs[pos++] = make_int2(ci, qi);
+                }
+            }
+            st.cnt += total;
+        } else {
+            // dense cells: the output in stage-sized windows; each lane
+            // writes the outputs of its range [off, off + nout) that fall in
+            // the window, the stage is flushed after each window
+            for (int w0 = 0; w0 < total;) {  // warp-uniform
+                const int w1 = min(total, w0 + (st.cap - st.cnt));
+                if (off < w1 && off + nout > w0) {
+                    int idx = off;
+#pragma unroll
+                    for (int t = 0; t < TC; ++t) {
+                        uint32_t b = cin[t];
+                        if (!b) continue;
+                        const bool two = ((meta >> (8 * t)) & 3u) != 0u;
+                        const int dg = (int)((meta >> (8 * t + 2)) & 63u) - 1;
+                        const int32_t ci = W.cid[t * 32 + lane];
+                        while (b) {
+                            const int q = __ffs(b) - 1;
+                            b &= b - 1u;
+                            const int32_t qi = W.qid[q];
+                            if (idx >= w0 && idx < w1) st.pairs[st.cnt + idx - w0] = make_int2(qi, ci);
+                            ++idx;
+                            if (two && q != dg) {
+                                if (idx >= w0 && idx < w1) st.pairs[st.cnt + idx - w0] = make_int2(ci, qi);
+                                ++idx;
+                            }
+                        }
+                    }
+                }
+                st.cnt += w1 - w0;
+                w0 = w1;
+                if (st.cnt == st.cap) stage_flush(st, P, lane);
+            }
+        }
+    }
+    if (!__any_sync(0xffffffffu, any_unc != 0u)) return;
+    // uncertain pairs: queued for the binary64 recheck (or re-decided here
+    // when the queue is full), one per lane per round
+    for (;;) {
+        bool want = false;
+        int q = 0, t_sel = 0;
+#pragma unroll
+        for (int t = 0; t < TC; ++t)
+            if (!want && unc[t]) {
+                q = __ffs(unc[t]) - 1;
+                unc[t] &= unc[t] - 1u;
+                want = true;
+                t_sel = t;
+            }
+        if (!__any_sync(0xffffffffu, want)) break;
+        const uint32_t ms = (meta >> (8 * t_sel)) & 0xFFu;
+        const int32_t jj = want ? W.cj[t_sel * 32 + lane] : 0;
+        const int32_t ci = want ? W.cid[t_sel * 32 + lane] : 0;
+        const bool mir = want && (ms & 3u) != 0u && q != (int)(ms >> 2) - 1;
+        const bool queued = band_push(P, lane, want, I.q0 + q, jj, mir);
+        int no = 0;
+        int32_t qi = 0;
+        if (want && !queued) {
+            const double s = direct_sq(P.xs + (int64_t)(I.q0 + q) * P.dp, P.xs + (int64_t)jj * P.dp, P.d);
+            ++rechecked;
+            if (s <= R.e2) {
+                no = mir ? 2 : 1;
+                qi = W.qid[q];
+            }
+        }
+        stage_emit_pairs(st, P, lane, no, qi, ci);
+    }
+}
+
+// Minimum resident CTAs per SM asked of the register allocator (4 warps
+// each), per padded dimension.  Compile-time tuning constants.
+#ifndef SJ_F32S_MIN_BLOCKS_D2
+#define SJ_F32S_MIN_BLOCKS_D2 8
+#endif
+#ifndef SJ_F32S_MIN_BLOCKS_D4
+#define SJ_F32S_MIN_BLOCKS_D4 8
+#endif
+#ifndef SJ_F32S_MIN_BLOCKS_D8
+#define SJ_F32S_MIN_BLOCKS_D8 7
+#endif
+constexpr int kF32sWarps = 4;
+template <int DP>
+constexpr int f32s_min_blocks() {
+    return DP == 2 ? SJ_F32S_MIN_BLOCKS_D2 : DP == 4 ? SJ_F32S_MIN_BLOCKS_D4 : SJ_F32S_MIN_BLOCKS_D8;
+}
+
+template <int DP, int RUNS, bool DBG>
+__global__ void __launch_bounds__(kF32sWarps * 32, f32s_min_blocks<DP>()) k_join_f32s(JoinParams P) {
+    constexpr int TC = f32s_tc<DP>();
+    constexpr uint32_t SLOTS = 32u * TC;
+    __shared__ F32sWarp<DP, RUNS> smem[kF32sWarps];
+    const float* __restrict__ Y = static_cast<const float*>(P.y);
+    const float* __restrict__ H = static_cast<const float*>(P.h);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    F32sWarp<DP, RUNS>& W = smem[wid];
+    WarpStage st{W.stage, nullptr, 0, 0, kF32sStage};
+    unsigned long long rechecked = 0;
+
+    long long next = 0;
+    if (lane == 0) next = (long long)atomicAdd(&P.counters[0], 1ull);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    for (;;) {
+        const long long it = next;
+        if (it >= P.n_items) break;
+        if (lane == 0) next = (long long)atomicAdd(&P.counters[0], 1ull);  // used next iteration
+        next = __shfl_sync(0xffffffffu, next, 0);
+        const Item I = P.items[it];
+        const int Q = I.q1 - I.q0;
+        const int nr = I.r1 - I.r0;
+        const ItemRoute R = item_route(st, P, it, lane);
+        // the item's queries (duplicated coordinates) and runs
+        for (int i = lane; i < kQMax * DP; i += 32) {
+            const int q = i / DP;
+            const float v = q < Q ? Y[(int64_t)I.q0 * DP + i] : 0.f;
+            W.qd[q][i % DP] = make_float2(v, v);
+        }
+        if (lane < kQMax) {
+            const float h = lane < Q ? H[I.q0 + lane] : -INFINITY;
+            W.qh2[lane] = make_float2(h, h);
+            W.qid[lane] = lane < Q ? (int32_t)(P.perm[I.q0 + lane] - R.off) : 0;
+        }
+        uint32_t carry = 0;
+        for (int b = 0; b < nr; b += 32) {
+            const int rr = b + lane;
+            uint32_t len = 0;
+            if (rr < nr) {
+                const Run Rn = P.runs[I.r0 + rr];
+                const bool self = P.tri && !(Rn.end_flags & kMirrorBit);
+                const int32_t start = self ? I.q0 : Rn.start;
+                W.rstart[rr] = start;
+                W.rmir[rr] = self ? (uint8_t)2 : (uint8_t)(Rn.end_flags >> 31);
+                len = (uint32_t)((int32_t)(Rn.end_flags & ~kMirrorBit) - start);
+            }
+            uint32_t v = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (rr < nr) W.rpre[rr + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) W.rpre[0] = 0;
+        __syncwarp();
+        const uint32_t C = carry;
+        int r = 0;
+        uint32_t base = 0;
+        if constexpr (TC == 2) {  // one chunk shape (one copy of the code)
+            for (; base < C; base += SLOTS)
+                f32s_chunk<DP, RUNS, TC, DBG>(W, st, P, I, R, Q, C, base, lane, r, rechecked);
+        } else {
+            for (; base + SLOTS <= C; base += SLOTS)
+                f32s_chunk<DP, RUNS, TC, DBG>(W, st, P, I, R, Q, C, base, lane, r, rechecked);
+            for (; base < C; base += 64u)
+                f32s_chunk<DP, RUNS, 2, DBG>(W, st, P, I, R, Q, C, base, lane, r, rechecked);
+        }
+        __syncwarp();
+    }
+    stage_flush(st, P, lane);
+    for (int o = 16; o > 0; o >>= 1) rechecked += __shfl_down_sync(0xffffffffu, rechecked, o);
+    if (lane == 0 && rechecked) atomicAdd(&P.counters[2], rechecked);
+}
+
+template <int DP, int RUNS, bool DBG>
+static int launch_f32s_dr(Index* ix, const JoinParams& p) {
+    auto kern = k_join_f32s<DP, RUNS, DBG>;
+    int per_sm = 0;
+    SJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32sWarps * 32, 0));
+    if (per_sm < 1) per_sm = 1;
+    long long blocks = (long long)device_sm_count(ix->device) * per_sm;
+    const long long need = (ix->n_items + kF32sWarps - 1) / kF32sWarps;
+    if (blocks > need) blocks = need > 0 ? need : 1;
+    kern<<<(unsigned)blocks, kF32sWarps * 32, 0, ix->stream>>>(p);
+    note_launch();
+    SJ_CK(cudaGetLastError());
+    return SJ_OK;
+}
+
+template <int DP>
+static int launch_f32s_d(Index* ix, const JoinParams& p) {
+    if (p.dbg) return launch_f32s_dr<DP, kMaxRuns, true>(ix, p);  // the filter dump (test aid)
+    return ix->m <= 4 ? launch_f32s_dr<DP, 28, false>(ix, p) : launch_f32s_dr<DP, kMaxRuns, false>(ix, p);
+}
+
+bool f32s_supported(const Index* ix, int emit_dist) {
+    return ix->kernel == SJ_KERNEL_FILTER_F32 && !emit_dist && ix->dp <= 8 && ix->aux != nullptr;
+}
+
+int launch_join_f32s(Index* ix, const JoinOut& out) {
+    const JoinParams p = make_join_params(ix, out, 0);
+    switch (ix->dp) {
+        case 2: return launch_f32s_d<2>(ix, p);
+        case 4: return launch_f32s_d<4>(ix, p);
+        case 8: return launch_f32s_d<8>(ix, p);
+        default:
+            set_error("no small-d FP32 kernel for padded dimension %d", ix->dp);
+            return SJ_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace sj

@@ -561,6 +561,13 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                         tmem_ld32(taddr + (uint32_t)c0, v);
                     }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (P.dbg && cvalid && has_cols) {  // the filter dump (test aid)
+                        for (int k = 0; k < 32 && c0 + k < X.ncol; ++k) {
+                            const int col = c0 + k;
+                            if ((uint32_t)(col - col_lo) <= col_span)
+                                dbg_record(P, X.qa + col, cp, __uint_as_float(v[k]));
+                        }
+                    }
                     // maxima of 8-column groups, then of all 32 (three-input max)
                     float m8[4];
 #pragma unroll

@@ -25,7 +25,7 @@ namespace sj {
 int launch_extent_raw(const double* pts, int64_t n, int d, unsigned long long* ext, cudaStream_t s);
 size_t pack_params_size();
 int pack_params_fill(void* host_pp, const double* lo, int d, int dp, double eps, double pbound, double delta);
-int launch_pack_f64_raw(const double* pts, const int32_t* perm, int64_t n, const void* pp_dev, double* xs, double* y,
+int launch_pack_f64_raw(const double* pts, const int32_t* perm, int64_t n, const void* host_pp, double* xs, double* y,
                         double* h, double* to, double* ti, cudaStream_t s);
 
 namespace {
@@ -42,9 +42,8 @@ constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign;
 // Layout of the scratch array (byte offsets).
 constexpr size_t kOffCounters = 0;                                         // 4 x u64
 constexpr size_t kOffExt = align_up(kOffCounters + 4 * 8);                 // (2 d + 1) x u64
-constexpr size_t kOffParams = align_up(kOffExt + (2 * SJ_MAX_D + 1) * 8);  // PackParams
-constexpr size_t kParamsBytes = 2048;                                      // >= sizeof(PackParams)
-constexpr size_t kOffPerm = align_up(kOffParams + kParamsBytes);           // n x i32
+constexpr size_t kParamsBytes = 2048;                                      // host copy, >= sizeof(PackParams)
+constexpr size_t kOffPerm = align_up(kOffExt + (2 * SJ_MAX_D + 1) * 8);    // n x i32
 constexpr size_t kOffXs = align_up(kOffPerm + kMaxN * 4);                  // n x kDp f64
 constexpr size_t kOffY = align_up(kOffXs + kMaxN * kDp * 8);               // n x kDp f64
 constexpr size_t kOffH = align_up(kOffY + kMaxN * kDp * 8);                // n f64
@@ -131,7 +130,7 @@ extern "C" int sj_self_join_noalloc(const double* pts, int64_t n, int32_t d, dou
         return SJ_ERR_ARG;
     }
     if (pack_params_size() > kParamsBytes) {
-        set_error("internal: packing parameters larger than their scratch slot");
+        set_error("internal: packing parameters larger than their host buffer");
         return SJ_ERR_UNSUPPORTED;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -175,7 +174,6 @@ extern "C" int sj_self_join_noalloc(const double* pts, int64_t n, int32_t d, dou
     // packing parameters, identity order, one item per 16 queries, one run
     alignas(16) unsigned char pp[kParamsBytes];
     SJ_TRY(pack_params_fill(pp, lo, d, kDp, eps, pbound, 1.01 * ldexp(1.0, -53) * rmax));
-    SJ_CK(cudaMemcpyAsync(base + kOffParams, pp, pack_params_size(), cudaMemcpyHostToDevice, s));
     const int64_t n_items = (n + kQMax - 1) / kQMax;
     int32_t* perm = reinterpret_cast<int32_t*>(base + kOffPerm);
     Item* items = reinterpret_cast<Item*>(base + kOffItems);
@@ -188,7 +186,7 @@ extern "C" int sj_self_join_noalloc(const double* pts, int64_t n, int32_t d, dou
     double* h = reinterpret_cast<double*>(base + kOffH);
     double* to = reinterpret_cast<double*>(base + kOffTo);
     double* ti = reinterpret_cast<double*>(base + kOffTi);
-    SJ_TRY(launch_pack_f64_raw(pts, perm, n, base + kOffParams, xs, y, h, to, ti, s));
+    SJ_TRY(launch_pack_f64_raw(pts, perm, n, pp, xs, y, h, to, ti, s));
 
     // the plain FP64 join kernel and its deferred recheck on the scratch
     Index ix;  // a view of the scratch (its host vectors stay empty)

@@ -1,0 +1,54 @@
+"""Sharding one join over several GPUs (Sec. III-B: the work items, the
+queries of one cell with their candidate runs, are independent units), run
+here as the shards one after another on one GPU: every shard builds the same
+index, runs its contiguous range of work items, and the disjoint union of
+the shards' pair sets must be the oracle's set."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2209_11287_gb300 import binding, workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_11287_gb300 import build
+    build.build()
+    binding.load()
+
+
+@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x2"])
+@pytest.mark.parametrize("n_shards", [2, 3, 8])
+def test_shards_union_is_the_join(kernel, n_shards):
+    w = workloads.uniform4d(n=60000, seed=21)
+    ref = oracle.join(w.points, w.eps)
+    pts = torch.from_numpy(w.points).cuda()
+    parts, works = [], []
+    for k in range(n_shards):
+        h = binding.sj_build_index(pts, w.eps, binding.sj_default_options(kernel=kernel))
+        try:
+            work = binding.sj_index_item_work(h)
+            bounds = binding.sj_shard_bounds(work, n_shards)
+            r = binding.sj_self_join_range(h, int(bounds[k]), int(bounds[k + 1]))
+            try:
+                pairs, _ = binding.sj_result_copy(r)
+            finally:
+                binding.sj_result_free(r)
+            info = binding.sj_index_info(h)
+        finally:
+            binding.sj_destroy(h)
+        assert work.sum() == info["n_evaluated"]  # the items' work is the join's
+        works.append(int(work[bounds[k]:bounds[k + 1]].sum()))
+        parts.append(binding.pairs_to_keys(pairs))
+    got = np.sort(np.concatenate(parts))
+    assert np.all(np.diff(got) > 0), "a pair came from two shards"
+    assert np.array_equal(got, ref)
+    # balanced: every shard within one item's work of an equal share
+    total = sum(works)
+    assert max(abs(x - total / n_shards) for x in works) <= work.max()

@@ -1,7 +1,9 @@
 """The multi-process path of bench.py on CPU: two gloo ranks, launched the
 way torchrun launches the bench (RANK / WORLD_SIZE / LOCAL_RANK and a
-127.0.0.1 rendezvous), agree on the slowest rank's time, which sets the
-whole-job rate of independent replicas (no data-path collective)."""
+127.0.0.1 rendezvous), agree on the slowest rank's time, partition the work
+items of one join into contiguous shards of equal work (the library's host
+side partition, no GPU needed) and gather their result counts, the one
+exchange of a sharded join (Sec. III-B: the work items are independent)."""
 import os
 import socket
 import sys
@@ -53,3 +55,52 @@ def test_one_rank_needs_no_process_group():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.25, 1, torch.device("cpu")) == 3.25
+
+
+def _shard_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch.distributed as dist
+
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # the per-item work of an index: every rank holds the same array (the
+    # build is deterministic); heavy-tailed like dense cells
+    g = np.random.Generator(np.random.PCG64(77))
+    work = (g.pareto(1.5, size=50000) * 1000).astype(np.int64) + 1
+    i0, i1 = bench.shard_of(work, rank, world)
+    mine = int(work[i0:i1].sum())
+    counts = bench.gather_counts(mine, world, torch.device("cpu"))
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, i0, i1, mine, counts, int(work.sum()), int(work.max())))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_shard_the_items_and_gather_counts(world):
+    from paper_2209_11287_gb300 import binding, build
+    build.build()
+    binding.load()
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    total, wmax = out[0][5], out[0][6]
+    # contiguous, disjoint, covering [0, n_items)
+    assert out[0][1] == 0 and out[-1][2] == 50000
+    assert all(out[k][2] == out[k + 1][1] for k in range(world - 1))
+    # balanced to within one item's work of an equal share
+    assert all(abs(o[3] - total / world) <= wmax for o in out)
+    # every rank gathered the same counts, rank order, summing to the whole
+    for o in out:
+        assert o[4] == [x[3] for x in out]
+        assert sum(o[4]) == total
