@@ -41,11 +41,12 @@ L2_FLUSH_BYTES = 256 << 20
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
 FP64_DFMA_TFLOPS = 1.255                                  # measured, profiles/fp64_peaks_gb300.txt
 FP64_DMMA_TFLOPS = 1.102                                  # measured, profiles/fp64_peaks_gb300.txt
-KERNEL_NAMES = {"filter_f32": "k_join_cc<float>", "fp64_fma": "k_join_cc<double>", "fp64_dmma": "k_join_dmma",
+KERNEL_NAMES = {"filter_f32": "k_join_cc<float>", "fp64_fma": "k_join_cc<double>",
+                "fp64_fma_sc": "k_join_cc<double> (short-circuit)", "fp64_dmma": "k_join_dmma",
                 "filter_bf16x3": "k_join_tc", "filter_bf16x2": "k_join_tc"}
 DTYPES = {"auto": "bf16x2|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64",
           "filter_bf16x2": "bf16x2+f64", "fp64_fma": "f64",
-          "fp64_dmma": "f64", "tuned": "bf16x2|bf16x3|f32+f64", "tuned_graph": "bf16x2|bf16x3|f32+f64",
+          "fp64_dmma": "f64", "fp64_fma_sc": "f64", "tuned": "bf16x2|bf16x3|f32+f64", "tuned_graph": "bf16x2|bf16x3|f32+f64",
           "auto_graph": "bf16x2|f32+f64"}
 
 
@@ -132,9 +133,9 @@ METRICS = {
 DEFAULT_VARIANTS = {
     "uniform4d": ["filter_f32", "tuned", "fp64_fma", "fp64_dmma"],
     "uniform2d": ["filter_f32", "fp64_fma", "fp64_dmma", "filter_bf16x2"],
-    "mixture16d": ["filter_bf16x2", "tuned", "filter_bf16x3", "filter_f32", "fp64_fma"],
+    "mixture16d": ["filter_bf16x2", "tuned", "filter_bf16x3", "filter_f32", "fp64_fma", "fp64_fma_sc"],
     "expo64d": ["filter_bf16x2", "filter_bf16x3", "filter_f32"],
-    "brute16d": ["filter_bf16x2", "filter_bf16x3", "filter_f32", "fp64_fma", "fp64_dmma"],
+    "brute16d": ["filter_bf16x2", "filter_bf16x3", "filter_f32", "fp64_fma", "fp64_fma_sc", "fp64_dmma"],
 }
 
 
@@ -240,8 +241,15 @@ def run_native(args):
     def one_step(opt, host=None, host_out=None):
         """Build + join (+ copy out).  With several ranks every rank builds the
         same index, runs its shard of the work items and the counts are
-        gathered; the step's count is the whole join's."""
+        gathered; the step's count is the whole join's.  End to end on one
+        GPU (host points, host_out given) the join runs in rounds whose pairs
+        are copied to host_out while the next round runs."""
         h = binding.sj_build_index(pts if host is None else host, w.eps, opt, stream)
+        if world == 1 and host_out is not None:
+            count, _ = binding.sj_self_join_to_host(h, host_out, e2e_device_pairs)
+            info = binding.sj_index_info(h)
+            binding.sj_destroy(h)
+            return (count, info["n_candidates"], info["n_evaluated"], 0, 0, 0.0, -1)
         if world > 1:
             i0, i1 = shard_of(binding.sj_index_item_work(h), rank, world)
             r = binding.sj_self_join_range(h, i0, i1)
@@ -263,7 +271,9 @@ def run_native(args):
         """Options of a variant: a kernel name, or "tuned" (the autotuner's
         pick for this workload, tuned once before the variant's warm-up)."""
         if kname != "tuned":
-            return binding.sj_default_options(kernel=kname, max_pairs_hint=args.hint,
+            sc = kname.endswith("_sc")  # FP64 tile with the variance order and short-circuit
+            return binding.sj_default_options(kernel=kname[:-3] if sc else kname, max_pairs_hint=args.hint,
+                                              short_circuit=int(sc),
                                               indexed_dims=binding.SJ_NO_INDEX if w.name == "brute16d" else 0)
         if not tuned:
             t0 = time.perf_counter()
@@ -277,13 +287,15 @@ def run_native(args):
     variants = [v for v in args.variants.split(",") if v]
     if args.variants == ",".join(VARIANTS):
         variants = DEFAULT_VARIANTS[args.workload]
+    # the clock sampler (an nvidia-smi process) starts before the first
+    # warm-up and settles, so its start-up does not fall into timed steps
+    sampler.start()
+    time.sleep(1.0)
     for vi, kname in enumerate(variants):
         opt = make_opt(kname)
         for _ in range(args.warmup):
             one_step(opt)
         barrier()
-        if vi == 0:
-            sampler.start()  # sampled over the timed steps of every kernel
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         launches0 = binding.sj_kernel_launches()
         info = None
@@ -311,9 +323,14 @@ def run_native(args):
     head = results[variants[0]]
     kern_ms = head["tile_ms"]
 
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    # the timed region; the pairs reach host memory in rounds of work items
+    # (two device buffers of about an eighth of the result each), each
+    # round's copy overlapping the next round's tiles
     host_pts = torch.from_numpy(w.points).pin_memory()
     host_out = torch.empty((head["count"] + 16, 2), dtype=torch.int32).pin_memory()
+    e2e_device_pairs = max(1 << 20, head["count"] // 8)
+    link = link_bandwidth(host_pts, host_out, dev)
     opt = make_opt(variants[0])
     one_step(opt, host_pts, host_out)
     barrier()
@@ -329,6 +346,11 @@ def run_native(args):
 
     if rank == 0:
         line = make_line(args, w, results, variants, world, kern_ms, e2e_s, head)
+        line["e2e"].update(link)
+        line["e2e"]["d2h_floor_ms"] = round(head["count"] * 8 / (link["d2h_gbs"] * 1e9) * 1e3, 3)
+        line["e2e"]["path"] = ("sj_build_index on pinned host points, sj_self_join_to_host into pinned host memory "
+                               "(rounds of work items, copies overlapping the next round)" if world == 1 else
+                               "sj_build_index on pinned host points, sj_self_join_range, sj_result_copy")
         if tuned:
             o = tuned["opt"]
             line["autotune"] = {"kernel": knames.get(o.kernel, "?"), "queries_per_item": o.queries_per_item,
@@ -341,6 +363,29 @@ def run_native(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def link_bandwidth(host_pts, host_out, dev):
+    """Host-link copy rates with the step's own pinned buffers: the points
+    host to device, the first 256 MB of the result buffer device to host."""
+    import torch
+    d_pts = torch.empty_like(host_pts, device=dev)
+    nb = min(host_out.numel() * 4, 256 << 20) // 4
+    h_out = host_out.view(-1)[:nb]
+    d_out = torch.empty(nb, dtype=torch.int32, device=dev)
+    out = {}
+    for name, dst, src, nbytes in (("h2d_gbs", d_pts, host_pts, host_pts.numel() * 8),
+                                   ("d2h_gbs", h_out, d_out, nb * 4)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(5):
+            dst.copy_(src, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize(dev)
+        out[name] = round(5 * nbytes / (a.elapsed_time(b) * 1e-3) / 1e9, 1)
+    return out
 
 
 def kernel_source_sha(kname):
@@ -626,13 +671,13 @@ def run_batched(args):
 
     sampler = ClockSampler(local)
     results = {}
+    sampler.start()  # before the first warm-up, so its start-up is not timed
+    time.sleep(1.0)
     for vi, kname in enumerate(variants):
         opt = make_opt(kname)
         for _ in range(args.warmup):
             one_step(opt, prepared)
         sync_all()
-        if vi == 0:
-            sampler.start()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         l0 = binding.sj_kernel_launches()
         tiles = []

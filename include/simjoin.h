@@ -126,6 +126,13 @@ typedef struct sj_options {
                                  batched join, per group, the entry of the
                                  group's padded dimension.  A missing file is
                                  an empty cache. */
+    int32_t short_circuit;    /* SJ_KERNEL_FP64_FMA with d > 8: 1 = order the
+                                 kernel coordinates' dims by decreasing variance
+                                 (Sec. II-D) and stop a warp's distance tile
+                                 after a block of 8 dims once every pair of it
+                                 is certainly out (Sec. III-B); the result set
+                                 is unchanged.  0 (default) = every tile runs
+                                 all dims.  Ignored by the other kernels. */
 } sj_options;
 
 /* Fills *opt with the defaults (kernel AUTO, no distances, automatic m,
@@ -236,20 +243,27 @@ SJ_API int sj_self_join_to_host(sj_handle h, int32_t* host_pairs, int64_t host_c
 
 /* ---- sharding one join over several GPUs (Sec. III-B) -------------------- */
 /*
- * The work items of an index (the queries of one cell with the candidate
- * runs of its neighbourhood) are independent units: every GPU can build the
- * same index from the same points (the build is deterministic) and run a
- * contiguous range of items; the union of the ranges' results is the join.
+ * The queries of one grid cell, with the candidate runs of its
+ * neighbourhood, are an independent unit: every GPU can build the index from
+ * the same points and run a contiguous range of whole cells; the union of
+ * the ranges' results is the join.  The cells, their order and the work
+ * items' positions are the same in every build; the order of the points
+ * inside a cell is not, so a cell split into several work items must not be
+ * split across GPUs: shards are ranges of whole cells.
  *
- * sj_index_item_work: the pair evaluations of each work item (n_items int64,
- * host memory; n_items from sj_index_info), as the tile kernels perform them.
+ * sj_index_item_work: per work item (n_items int64, host memory; n_items
+ * from sj_index_info), the pair evaluations of its whole cell (as the tile
+ * kernels perform them) at the cell's first item, 0 at the cell's other
+ * items.  The sum is the index's n_evaluated.
  *
  * sj_shard_bounds: host only (no GPU needed).  Splits items [0, n_items)
  * into n_shards contiguous ranges [bounds[k], bounds[k + 1]) of about equal
  * total work: boundary k is the item boundary whose work prefix is nearest
- * to k / n_shards of the total.  bounds: n_shards + 1 int64; bounds[0] = 0,
- * bounds[n_shards] = n_items, non-decreasing.  A pure function of its
- * inputs, so every rank computes the same partition.  Errors: SJ_ERR_ARG.
+ * to k / n_shards of the total, moved past items of no work (so with the
+ * work of sj_index_item_work every boundary is the first item of a cell).
+ * bounds: n_shards + 1 int64; bounds[0] = 0, bounds[n_shards] = n_items,
+ * non-decreasing.  A pure function of its inputs, so every rank computes
+ * the same partition.  Errors: SJ_ERR_ARG.
  *
  * sj_self_join_range: sj_self_join restricted to work items [item_begin,
  * item_end) (pairs of the items' queries, both orders of mirrored pairs, as
@@ -463,6 +477,43 @@ SJ_API int sj_debug_filter_dump(sj_handle h, int32_t* perm, float* y, float* hno
  * device.  Synchronous.  Errors: SJ_ERR_ARG, SJ_ERR_CUDA.
  */
 SJ_API int sj_index_perm(sj_handle h, int32_t* perm_out);
+
+/* ---- reuse of the join: DBSCAN ----------------------------------------- */
+/*
+ * Density-based clustering on a join's eps-neighbourhoods (the paper names
+ * this reuse of its join as future work, Sec. V; DBSCAN: Ester et al.
+ * 1996).  `r` is the result of sj_self_join / sj_join over `n` points with
+ * the clustering's eps (pages still on the device); a point is core iff its
+ * neighbourhood, itself included, holds at least min_pts points; clusters
+ * are the connected components of the core points under the core-core
+ * pairs, numbered 0, 1, ... in the order of their smallest core point; a
+ * non-core point with a core neighbour (border point) gets the smallest of
+ * its core neighbours' cluster numbers, every other point -1 (noise).  The
+ * labels are deterministic.
+ *
+ *   labels_out  n int32, host or device
+ *   n_clusters  host pointer (may be NULL)
+ * Synchronous.  Errors: SJ_ERR_ARG (a batched result, n, min_pts < 1),
+ * SJ_ERR_RESULT_OVERFLOW (a result that holds only part of its pairs),
+ * SJ_ERR_OOM, SJ_ERR_CUDA, SJ_ERR_TIMEOUT (a union-find update ran out of
+ * its bounded retries).
+ */
+SJ_API int sj_dbscan(const sj_result* r, int64_t n, int32_t min_pts, int32_t* labels_out, int64_t* n_clusters);
+
+/* ---- tracing ------------------------------------------------------------ */
+/*
+ * No counterpart in the paper (which reports response times only).
+ * sj_set_tracing(1) makes every later sj_build_index of the process record a
+ * CUDA event and the host clock at its phase boundaries (0 switches it off).
+ * sj_index_phase_ms gives, for a handle built with tracing on, the device
+ * and host milliseconds of its four build phases: extent + grid choice, sort
+ * by cell key, packing (coordinates, norms, thresholds; the tensor-core
+ * filter's operand rows), neighbour runs + work items (each array of 4 may
+ * be NULL; -1 where not traced).  The join's
+ * tile time is sj_result.ms_tile.
+ */
+SJ_API void sj_set_tracing(int32_t on);
+SJ_API int sj_index_phase_ms(sj_handle h, double* device_ms, double* host_ms);
 
 /* ---- test aids: allocation failures ------------------------------------ */
 /*

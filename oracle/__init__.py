@@ -265,3 +265,52 @@ def calibrate_eps(x, target: float, n_queries: int = 2000, seed: int = 12345) ->
     allv = np.concatenate(pooled)
     s = np.partition(allv, k - 1)[k - 1]
     return float(np.sqrt(s))
+
+
+# --------------------------------------------------------------------------
+# DBSCAN on the join's result (reuse of the self-join for density-based
+# clustering, which the paper names as future work for its join, Sec. V).
+# Definition followed (Ester et al. 1996, stated on the eps-neighbourhoods
+# the self-join returns): a point is core iff its neighbourhood (itself
+# included) holds at least min_pts points; clusters are the connected
+# components of the graph whose vertices are the core points and whose edges
+# are the core-core pairs of the join; a non-core point with at least one
+# core neighbour is a border point and joins, of its core neighbours'
+# clusters, the one with the smallest identifier; the rest is noise (-1).
+# A cluster's identifier is its rank among all clusters ordered by their
+# smallest core point index.
+# --------------------------------------------------------------------------
+
+def dbscan(x, eps: float, min_pts: int):
+    """Labels (n int64, -1 for noise) and the number of clusters."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    x = _pts(x)
+    n = x.shape[0]
+    keys = join(x, eps)
+    i = keys >> 32
+    j = keys & 0xFFFFFFFF
+    deg = np.bincount(i, minlength=n)
+    core = deg >= int(min_pts)
+    cc = core[i] & core[j]
+    g = coo_matrix((np.ones(int(cc.sum()), dtype=np.int8), (i[cc], j[cc])), shape=(n, n))
+    _, comp = connected_components(g, directed=False)
+    # cluster identifier: rank of the component's smallest core index
+    first = np.full(comp.max() + 1 if n else 0, n, dtype=np.int64)
+    core_idx = np.nonzero(core)[0]
+    np.minimum.at(first, comp[core_idx], core_idx)
+    roots = np.unique(first[comp[core_idx]]) if core_idx.size else np.zeros(0, dtype=np.int64)
+    rank = {int(r): k for k, r in enumerate(roots.tolist())}
+    labels = np.full(n, -1, dtype=np.int64)
+    for p in core_idx.tolist():
+        labels[p] = rank[int(first[comp[p]])]
+    # border points: the smallest cluster identifier among core neighbours
+    bm = (~core[i]) & core[j]
+    if bm.any():
+        bi, bj = i[bm], j[bm]
+        cand = labels[bj]
+        best = np.full(n, np.iinfo(np.int64).max, dtype=np.int64)
+        np.minimum.at(best, bi, cand)
+        hit = best != np.iinfo(np.int64).max
+        labels[hit] = best[hit]
+    return labels, int(roots.size)

@@ -63,6 +63,7 @@ class sj_options(ctypes.Structure):
         ("page_pairs", ctypes.c_int64),
         ("max_pairs_hint", ctypes.c_int64),
         ("tune_cache", ctypes.c_char_p),
+        ("short_circuit", ctypes.c_int32),
     ]
 
 
@@ -184,6 +185,12 @@ def load():
         lib.sj_shard_bounds.restype = ctypes.c_int
         lib.sj_self_join_range.argtypes = [_vp, _i64, _i64, ctypes.POINTER(sj_result)]
         lib.sj_self_join_range.restype = ctypes.c_int
+        lib.sj_dbscan.argtypes = [ctypes.POINTER(sj_result), _i64, _i32, _vp, ctypes.POINTER(_i64)]
+        lib.sj_dbscan.restype = ctypes.c_int
+        lib.sj_set_tracing.argtypes = [_i32]
+        lib.sj_set_tracing.restype = None
+        lib.sj_index_phase_ms.argtypes = [_vp, _vp, _vp]
+        lib.sj_index_phase_ms.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -467,12 +474,13 @@ def sj_kernel_launches() -> int:
 # ---- convenience ------------------------------------------------------------------
 
 def self_join(points, eps: float, kernel="auto", emit_distances=False, symmetric=True, indexed_dims=0,
-              max_pairs_hint=0, queries_per_item=0, tune_cache=None, stream=None):
+              max_pairs_hint=0, queries_per_item=0, tune_cache=None, short_circuit=0, stream=None):
     """Build, join and copy out in one call: returns (pairs int32 n x 2 numpy,
     distances or None, stats dict)."""
     opt = sj_default_options(kernel=kernel, emit_distances=int(emit_distances), symmetric=int(symmetric),
                              indexed_dims=indexed_dims, max_pairs_hint=max_pairs_hint,
-                             queries_per_item=queries_per_item, tune_cache=tune_cache)
+                             queries_per_item=queries_per_item, tune_cache=tune_cache,
+                             short_circuit=int(short_circuit))
     h = sj_build_index(points, eps, opt, stream)
     try:
         info = sj_index_info(h)
@@ -578,3 +586,26 @@ def sj_self_join_range(handle, item_begin: int, item_end: int) -> sj_result:
     r = sj_result()
     _check(load().sj_self_join_range(handle, int(item_begin), int(item_end), ctypes.byref(r)))
     return r
+
+
+def sj_set_tracing(on: bool) -> None:
+    """Record the build phases of later sj_build_index calls."""
+    load().sj_set_tracing(int(bool(on)))
+
+
+def sj_index_phase_ms(handle):
+    """(device ms, host ms) of the four build phases of a traced index:
+    extent + grid, sort, packing, runs + items (-1 where not traced)."""
+    dev = np.zeros(4)
+    host = np.zeros(4)
+    _check(load().sj_index_phase_ms(handle, dev.ctypes.data, host.ctypes.data))
+    return dev, host
+
+
+def sj_dbscan(result: sj_result, n: int, min_pts: int):
+    """DBSCAN labels (n int32 numpy, -1 for noise) and the cluster count from
+    a single join's result over n points."""
+    labels = np.empty(int(n), dtype=np.int32)
+    k = _i64(0)
+    _check(load().sj_dbscan(ctypes.byref(result), int(n), int(min_pts), labels.ctypes.data, ctypes.byref(k)))
+    return labels, int(k.value)

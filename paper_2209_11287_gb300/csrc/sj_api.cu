@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <mutex>
 #include <new>
 
@@ -26,6 +27,36 @@ void set_error(const char* fmt, ...) {
 void clear_error() { g_msg[0] = 0; }
 
 static std::atomic<long long> g_launches{0};
+static std::atomic<bool> g_tracing{false};
+bool tracing_on() { return g_tracing.load(std::memory_order_relaxed); }
+
+static double host_ms_now() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+PhaseClock::PhaseClock(cudaStream_t st) : on(tracing_on()), s(st) {}
+PhaseClock::~PhaseClock() {
+    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+}
+void PhaseClock::mark() {
+    if (!on || n >= 5) return;
+    if (cudaEventCreate(&ev[n]) != cudaSuccess) {
+        on = false;
+        return;
+    }
+    cudaEventRecord(ev[n], s);
+    host[n] = host_ms_now();
+    ++n;
+}
+void PhaseClock::finish(Index* ix) {
+    if (!on || n < 5) return;
+    cudaEventSynchronize(ev[4]);
+    for (int k = 0; k < 4; ++k) {
+        float ms = 0.f;
+        ix->phase_dev_ms[k] = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess ? ms : -1.0;
+        ix->phase_host_ms[k] = host[k + 1] - host[k];
+    }
+}
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ---- device memory pool -------------------------------------------------------------
@@ -123,6 +154,7 @@ static void release_index(Index* ix) {
     dev_free(ix->thr_out, s);
     dev_free(ix->thr_in, s);
     dev_free(ix->aux, s);
+    dev_free(ix->sc_w, s);
     dev_free(ix->perm, s);
     dev_free(ix->rows_a, s);
     dev_free(ix->rows_b, s);
@@ -189,6 +221,21 @@ const char* sj_last_error_message(void) { return g_msg; }
 const char* sj_version(void) { return "libsj 0.1 sm_103a"; }
 
 int64_t sj_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+void sj_set_tracing(int32_t on) { g_tracing.store(on != 0, std::memory_order_relaxed); }
+
+int sj_index_phase_ms(sj_handle h, double* device_ms, double* host_ms) {
+    clear_error();
+    if (!h) {
+        set_error("NULL handle");
+        return SJ_ERR_ARG;
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (device_ms) device_ms[k] = h->phase_dev_ms[k];
+        if (host_ms) host_ms[k] = h->phase_host_ms[k];
+    }
+    return SJ_OK;
+}
 
 void sj_debug_fail_allocations(int64_t after) { g_fail_after.store(after < 0 ? -1 : after, std::memory_order_relaxed); }
 
@@ -740,6 +787,9 @@ int sj_shard_bounds(const int64_t* item_work, int64_t n_items, int32_t n_shards,
         while (i < n_items && pre + (long double)item_work[i] <= target) pre += (long double)item_work[i++];
         // pre <= target < pre + work[i]: take the nearer boundary
         if (i < n_items && (pre + (long double)item_work[i]) - target < target - pre) pre += (long double)item_work[i++];
+        // a boundary never falls before an item of no work (an item that
+        // continues its cell: the cell's work sits at its first item)
+        while (i < n_items && item_work[i] == 0) ++i;
         bounds[k] = i;
     }
     bounds[n_shards] = n_items;

@@ -66,6 +66,27 @@ __global__ void k_extent(const double* __restrict__ x, int64_t total, int d, uns
     }
 }
 
+// Per-dim sum and sum of squares (binary64) of the points, for the
+// variance order of the short-circuit (an order only: its rounding changes no
+// result).  Same thread layout as k_extent.
+__global__ void k_moments(const double* __restrict__ x, int64_t total, int d, double* mom) {
+    extern __shared__ double s_mom[];  // [2 * d]
+    for (int k = threadIdx.x; k < 2 * d; k += blockDim.x) s_mom[k] = 0.0;
+    __syncthreads();
+    double s1 = 0.0, s2 = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += stride) {
+        const double v = x[i];
+        s1 += v;
+        s2 = fma(v, v, s2);
+    }
+    const int k = threadIdx.x % d;
+    atomicAdd(&s_mom[k], s1);
+    atomicAdd(&s_mom[d + k], s2);
+    __syncthreads();
+    for (int k2 = threadIdx.x; k2 < 2 * d; k2 += blockDim.x) atomicAdd(&mom[k2], s_mom[k2]);
+}
+
 struct GridParams {
     int m;
     int dims[kMaxM];
@@ -125,21 +146,6 @@ __global__ void k_key_count(const double* __restrict__ x, int64_t n, int d, Grid
     if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], (uint32_t)__popc(peers));
 }
 
-// off64[key] >> 32: the key's first sorted position (exclusive scan of the
-// counts).
-__global__ void k_key_scatter(const uint32_t* __restrict__ key32, int64_t n,
-                              const unsigned long long* __restrict__ off64, uint32_t* fill, int32_t* perm) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const bool valid = i < n;
-    const uint32_t key = valid ? key32[i] : kNoKey;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    uint32_t b = 0;
-    if (valid && lane == leader) b = atomicAdd(&fill[key], (uint32_t)__popc(peers));
-    b = __shfl_sync(0xffffffffu, b, leader);
-    if (valid) perm[(uint32_t)(off64[key] >> 32) + b + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
-}
 
 // ---------------------------------------------------------------------------
 // exclusive scan (reduce-then-scan over tiles of 4096), of uint32 or of
@@ -425,6 +431,13 @@ struct PackParams {
     double a_out, b_out, a_in, b_in;
     int has_in;
     int d, dp;
+    // kernel coordinate k is input dim order[k] (identity unless the
+    // short-circuit orders dims by variance)
+    uint8_t order[SJ_MAX_D];
+    // short-circuit: the checkpoint (kernel dims before it; 0: off) and the
+    // margin coefficient (see pack_one)
+    int sc_b;
+    double sc_coef, sc_p;
 };
 
 __host__ __device__ inline double gamma_n(double u, int k) { return k * u / (1.0 - k * u); }
@@ -486,28 +499,79 @@ __device__ __forceinline__ double thr_up(double a, double pc, double b) { return
 // order, with its kernel coordinates, norm and thresholds (and, for the
 // small-d FP32 filter, its 16-byte record: both thresholds and the input
 // index).  The parameters travel by value.
+// Output arrays of the packing (cell order).
 template <typename T>
-__global__ void k_pack(const double* __restrict__ x, const int32_t* __restrict__ perm, int64_t n, const PackParams pp,
-                       double* xs, T* y, T* h, T* thr_out, T* thr_in, float4* aux) {
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
+struct PackOut {
+    double* xs;
+    T* y;
+    T* h;
+    T* thr_out;
+    T* thr_in;
+    float4* aux;   // or null
+    double* sc_w;  // or null
+};
+
+// Packs input point src_i (row xr) at sorted position p: its original row,
+// its kernel coordinates (in the kernel dim order), norm and thresholds
+// (and, for the small-d FP32 filter, its 16-byte record: both thresholds and
+// the input index; for the short-circuit, its checkpoint bounds).
+template <typename T>
+__device__ __forceinline__ void pack_one(const double* __restrict__ xr, int32_t src_i, int64_t p, const PackParams& pp,
+                                         const PackOut<T>& o) {
     const int d = pp.d, dp = pp.dp;
-    const int32_t src_i = perm[p];
-    const int64_t src = (int64_t)src_i * d;
-    T nrm = T(0);
+    for (int k = 0; k < dp; ++k) o.xs[p * dp + k] = k < d ? xr[k] : 0.0;  // input order
+    T nrm = T(0), nrm_b = T(0);
     for (int k = 0; k < dp; ++k) {
-        const double v = k < d ? x[src + k] : 0.0;
-        xs[p * dp + k] = v;
-        const T yk = k < d ? T(v - pp.lo[k]) : T(0);
-        y[p * dp + k] = yk;
+        const int ok = k < d ? pp.order[k] : k;
+        const T yk = k < d ? T(xr[ok] - pp.lo[ok]) : T(0);
+        o.y[p * dp + k] = yk;
         nrm = fma_pack(yk, yk, nrm);
+        if (k + 1 == pp.sc_b) nrm_b = nrm;  // the partial norm at the short-circuit checkpoint
     }
-    h[p] = -nrm * T(0.5);
+    o.h[p] = -nrm * T(0.5);
     const T to = thr_down(pp.a_out, nrm, pp.b_out);
     const T ti = pp.has_in ? thr_up(pp.a_in, nrm, pp.b_in) : T(INFINITY);
-    thr_out[p] = to;
-    thr_in[p] = ti;
-    if (aux) aux[p] = make_float4((float)to, (float)ti, __int_as_float(src_i), 0.f);
+    o.thr_out[p] = to;
+    o.thr_in[p] = ti;
+    if (o.aux) o.aux[p] = make_float4((float)to, (float)ti, __int_as_float(src_i), 0.f);
+    if (o.sc_w) {
+        // w = half the norm over the dims after the checkpoint (rounded up)
+        // plus E_sc / 2, E_sc = sc_coef (P + pc): the remaining products satisfy
+        // y_q y_c <= (y_q^2 + y_c^2) / 2, so a pair's accumulator at the
+        // checkpoint plus w of both points (the margins covering every
+        // rounding involved) bounds its full filter value from above
+        const double full = (double)nrm;
+        const double e_half = 0.5 * __dmul_ru(pp.sc_coef, __dadd_ru(pp.sc_p, full));
+        o.sc_w[p] = __dadd_ru(0.5 * __dsub_ru(full, (double)nrm_b), e_half);
+    }
+}
+
+// One thread per sorted position: the point is gathered through perm.
+template <typename T>
+__global__ void k_pack(const double* __restrict__ x, const int32_t* __restrict__ perm, int64_t n, const PackParams pp,
+                       PackOut<T> o) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t src_i = perm[p];
+    pack_one<T>(x + (int64_t)src_i * pp.d, src_i, p, pp, o);
+}
+
+// The counting sort's scatter: one thread per input point takes its sorted
+// position, off64[key] >> 32 plus its rank among the key's points (in the
+// order warps reach the key).  (Fusing the packing into this scatter was
+// measured slower: its scattered row writes cost more than k_pack's gather.)
+__global__ void k_key_scatter(const uint32_t* __restrict__ key32, int64_t n,
+                              const unsigned long long* __restrict__ off64, uint32_t* fill, int32_t* perm) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t key = valid ? key32[i] : kNoKey;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t b = 0;
+    if (valid && lane == leader) b = atomicAdd(&fill[key], (uint32_t)__popc(peers));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    if (valid) perm[(uint32_t)(off64[key] >> 32) + b + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
 // Per-point records of the small-d FP32 filter: its two thresholds and its
@@ -530,14 +594,10 @@ int build_aux(Index* ix) {
     return SJ_OK;
 }
 
-// Pair evaluations per work item: its queries times the candidates of its
-// runs (a self-cell run starts at the item's first query when the join
+// Pair evaluations of one work item: its queries times the candidates of
+// its runs (a self-cell run starts at the item's first query when the join
 // evaluates self-cell triangles, as the tile kernels load it).
-__global__ void k_item_work(const Item* __restrict__ items, const Run* __restrict__ runs, int64_t n_items, int tri,
-                            long long* work) {
-    const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (it >= n_items) return;
-    const Item I = items[it];
+__device__ __forceinline__ long long item_evals(const Item& I, const Run* __restrict__ runs, int tri) {
     long long c = 0;
     for (int32_t r = I.r0; r < I.r1; ++r) {
         const Run R = runs[r];
@@ -546,7 +606,29 @@ __global__ void k_item_work(const Item* __restrict__ items, const Run* __restric
         const int32_t start = (tri && !mirror) ? I.q0 : R.start;
         c += (long long)(end - start);
     }
-    work[it] = c * (long long)(I.q1 - I.q0);
+    return c * (long long)(I.q1 - I.q0);
+}
+
+// Work per cell, reported at the cell's first work item (0 at its other
+// items).  The items of one cell are consecutive and share their run list
+// (the same r0), so a cell's first item is the one whose predecessor has
+// another r0.
+__global__ void k_item_work(const Item* __restrict__ items, const Run* __restrict__ runs, int64_t n_items, int tri,
+                            long long* work) {
+    const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (it >= n_items) return;
+    const Item I = items[it];
+    if (it > 0 && items[it - 1].r0 == I.r0) {
+        work[it] = 0;
+        return;
+    }
+    long long c = item_evals(I, runs, tri);
+    for (int64_t k = it + 1; k < n_items; ++k) {
+        const Item J = items[k];
+        if (J.r0 != I.r0) break;
+        c += item_evals(J, runs, tri);
+    }
+    work[it] = c;
 }
 
 int launch_item_work(Index* ix, long long* work) {
@@ -757,21 +839,27 @@ struct DenseEnum {
 };
 
 struct DenseTotals {
-    unsigned long long n_evaluated, sum_sq, tri_skip, n_cells;
+    unsigned long long n_evaluated, sum_sq, tri_skip, n_cells, n_runs;
 };
 
-template <bool FILL>
+// MODE 0: count the runs of every key (run_cnt) and the totals; MODE 1: write
+// runs at run_off[key] and the items; MODE 2: both in one pass, the runs of
+// key k in fixed slots from k * slots (no count pass, no scan).
+template <int MODE>
 __global__ void k_denum(DenseEnum e, const unsigned long long* __restrict__ off64, uint32_t* run_cnt,
-                        const uint32_t* __restrict__ run_off, Run* runs, Item* items, DenseTotals* tot) {
+                        const uint32_t* __restrict__ run_off, Run* runs, Item* items, DenseTotals* tot,
+                        uint32_t slots) {
+    constexpr bool FILL = MODE >= 1;
+    constexpr bool COUNT = MODE != 1;
     const int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long my_eval = 0, my_sq = 0, my_skip = 0, my_cells = 0;
+    unsigned long long my_eval = 0, my_sq = 0, my_skip = 0, my_cells = 0, my_runs = 0;
     if (key < e.K) {
         const unsigned long long a0 = off64[key], a1 = off64[key + 1];
         const uint32_t s0 = (uint32_t)(a0 >> 32);
         const uint32_t q = (uint32_t)(a1 >> 32) - s0;
         uint32_t nr = 0;
         unsigned long long ev = 0;
-        const uint32_t r0 = FILL ? run_off[key] : 0u;
+        const uint32_t r0 = MODE == 1 ? run_off[key] : MODE == 2 ? (uint32_t)key * slots : 0u;
         auto emit = [&](uint32_t ka, uint32_t kb, bool mirror) {  // keys [ka, kb]
             const int32_t a = (int32_t)(off64[ka] >> 32), b = (int32_t)(off64[kb + 1] >> 32);
             if (a >= b) return;
@@ -833,28 +921,32 @@ __global__ void k_denum(DenseEnum e, const unsigned long long* __restrict__ off6
                 x.r1 = (int32_t)(r0 + nr);
                 items[it0 + t] = x;
             }
-        } else {
-            run_cnt[key] = nr;
+        }
+        if (COUNT) {
+            if (MODE == 0) run_cnt[key] = nr;
             if (q > 0) {
                 my_eval = ev * (unsigned long long)q;
                 my_sq = (unsigned long long)q * (unsigned long long)q;
                 if (e.symmetric) my_skip = tri_skip((int64_t)q, (int)e.qmax);
                 my_cells = 1;
+                my_runs = nr;
             }
         }
     }
-    if (!FILL) {
+    if (COUNT) {
         for (int o = 16; o > 0; o >>= 1) {
             my_eval += __shfl_down_sync(0xffffffffu, my_eval, o);
             my_sq += __shfl_down_sync(0xffffffffu, my_sq, o);
             my_skip += __shfl_down_sync(0xffffffffu, my_skip, o);
             my_cells += __shfl_down_sync(0xffffffffu, my_cells, o);
+            my_runs += __shfl_down_sync(0xffffffffu, my_runs, o);
         }
         if ((threadIdx.x & 31) == 0 && my_cells) {
             atomicAdd(&tot->n_evaluated, my_eval);
             atomicAdd(&tot->sum_sq, my_sq);
             atomicAdd(&tot->tri_skip, my_skip);
             atomicAdd(&tot->n_cells, my_cells);
+            atomicAdd(&tot->n_runs, my_runs);
         }
     }
 }
@@ -944,21 +1036,27 @@ static int pack_points(Index* ix, const double* pts, const PackParams& hp) {
     cudaStream_t s = ix->stream;
     const int64_t n = ix->n;
     // each array goes into the index as soon as it exists (released with it)
-    T *y, *h, *to, *ti;
-    SJ_TRY(dev_alloc_t(&y, (size_t)n * ix->dp, s));
-    ix->y = y;
-    SJ_TRY(dev_alloc_t(&h, (size_t)n, s));
-    ix->h = h;
-    SJ_TRY(dev_alloc_t(&to, (size_t)n, s));
-    ix->thr_out = to;
-    SJ_TRY(dev_alloc_t(&ti, (size_t)n, s));
-    ix->thr_in = ti;
-    float4* aux = nullptr;
+    PackOut<T> o{};
+    SJ_TRY(dev_alloc_t(&ix->xs, (size_t)n * ix->dp, s));
+    o.xs = ix->xs;
+    SJ_TRY(dev_alloc_t(&o.y, (size_t)n * ix->dp, s));
+    ix->y = o.y;
+    SJ_TRY(dev_alloc_t(&o.h, (size_t)n, s));
+    ix->h = o.h;
+    SJ_TRY(dev_alloc_t(&o.thr_out, (size_t)n, s));
+    ix->thr_out = o.thr_out;
+    SJ_TRY(dev_alloc_t(&o.thr_in, (size_t)n, s));
+    ix->thr_in = o.thr_in;
     if (std::is_same<T, float>::value && wants_aux(ix)) {
-        SJ_TRY(dev_alloc_t(&aux, (size_t)n, s));
-        ix->aux = aux;
+        SJ_TRY(dev_alloc_t(&o.aux, (size_t)n, s));
+        ix->aux = o.aux;
     }
-    k_pack<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, ix->perm, n, hp, ix->xs, y, h, to, ti, aux);
+    if (std::is_same<T, double>::value && hp.sc_b > 0) {
+        SJ_TRY(dev_alloc_t(&o.sc_w, (size_t)n, s));
+        ix->sc_w = o.sc_w;
+        ix->sc_b = hp.sc_b;
+    }
+    k_pack<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, ix->perm, n, hp, o);
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
@@ -1090,6 +1188,8 @@ int build_index(Index* ix, const double* pts) {
     const int64_t n = ix->n;
     const int d = ix->d;
     Scratch tmp(s);  // temporaries, released on every return
+    PhaseClock clock(s);
+    clock.mark();
     // ---- extent and finiteness check (one sync) ----
     unsigned long long* ext = nullptr;
     SJ_TRY(tmp.alloc(&ext, (size_t)2 * d + 1));
@@ -1109,6 +1209,21 @@ int build_index(Index* ix, const double* pts) {
         note_launch();
         SJ_CK(cudaGetLastError());
     }
+    // the short-circuit of the FP64 tile orders the kernel dims by variance
+    const bool short_circuit = ix->kernel == SJ_KERNEL_FP64_FMA && ix->opt.short_circuit && ix->dp >= 16;
+    std::vector<double> mom(2 * d, 0.0);
+    double* dmom = nullptr;
+    if (short_circuit) {
+        SJ_TRY(tmp.alloc(&dmom, (size_t)2 * d));
+        SJ_CK(cudaMemsetAsync(dmom, 0, 2 * d * sizeof(double), s));
+        const int64_t total = n * d;
+        const int bs = 256 - (256 % d);
+        const int blocks = (int)std::min<int64_t>((total + bs - 1) / bs, (int64_t)device_sm_count(ix->device) * 8);
+        k_moments<<<blocks, bs, 2 * d * sizeof(double), s>>>(pts, total, d, dmom);
+        note_launch();
+        SJ_CK(cudaGetLastError());
+        SJ_CK(cudaMemcpyAsync(mom.data(), dmom, 2 * d * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     std::vector<unsigned long long> got(2 * d + 1);
     SJ_CK(cudaMemcpyAsync(got.data(), ext, got.size() * 8, cudaMemcpyDeviceToHost, s));
     SJ_CK(cudaStreamSynchronize(s));
@@ -1123,8 +1238,50 @@ int build_index(Index* ix, const double* pts) {
         ix->hi[k] = from_ord(got[d + k]);
     }
     SJ_TRY(choose_grid(ix));
+    clock.mark();
 
-    // ---- cell keys and sort ----
+    // ---- packing parameters ----
+    // kernel coordinates y = x - centre of the extent: |y_k| <= R_k / 2, which
+    // keeps the norms in the expanded form (and the certified band) small
+    PackParams hp{};
+    double pb = 0, rmax = 0;
+    for (int k = 0; k < d; ++k) {
+        hp.lo[k] = 0.5 * (ix->lo[k] + ix->hi[k]);
+        const double r = 0.5 * (ix->hi[k] - ix->lo[k]) * (1.0 + ldexp(1.0, -40));
+        pb += r * r;
+        rmax = std::max(rmax, r);
+    }
+    const double pbound = pb * (1.0 + ldexp(1.0, -20));
+    hp.d = d;
+    hp.dp = ix->dp;
+    // kernel dim order: input order, or decreasing variance (ties: input
+    // order) for the short-circuit, so the partial sums grow fastest
+    std::vector<int> order(d);
+    std::iota(order.begin(), order.end(), 0);
+    if (short_circuit) {
+        std::vector<double> var(d);
+        for (int k = 0; k < d; ++k) {
+            const double mean = mom[k] / (double)n;
+            var[k] = mom[d + k] / (double)n - mean * mean;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return var[a] > var[b]; });
+        // one checkpoint at half the dims (a multiple of 8): a pair whose
+        // partial distance there already exceeds eps is out
+        hp.sc_b = std::max(8, ix->dp / 2 / 8 * 8);
+        hp.sc_coef = 8.0 * gamma_n(ldexp(1.0, -53), ix->dp + 1);
+        hp.sc_p = pbound;
+    }
+    for (int k = 0; k < d; ++k) hp.order[k] = (uint8_t)order[k];
+    ix->dim_order = order;
+    const bool tensor = is_tensor_kernel(ix->kernel);
+    const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32 || tensor;
+    const double u_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
+    const double delta = 1.01 * u_t * rmax;
+    double c1 = -1.0;  // (the tensor-core filter's bound: tc_c1)
+    if (tensor) c1 = tc_c1(ix->dp, ix->kernel);
+    pack_coefficients(ix->eps, pbound, delta, u_t, d, ix->dp, &hp, c1);
+
+    // ---- cell keys, sort and packing ----
     SJ_TRY(dev_alloc_t(&ix->perm, (size_t)n, s));
     GridParams gp{};
     gp.m = ix->m;
@@ -1186,29 +1343,8 @@ int build_index(Index* ix, const double* pts) {
         note_launch();
         SJ_CK(cudaGetLastError());
     }
-
-    // ---- packing (independent of the cells) ----
-    SJ_TRY(dev_alloc_t(&ix->xs, (size_t)n * ix->dp, s));
-    // kernel coordinates y = x - centre of the extent: |y_k| <= R_k / 2, which
-    // keeps the norms in the expanded form (and the certified band) small
-    PackParams hp{};
-    double pb = 0, rmax = 0;
-    for (int k = 0; k < d; ++k) {
-        hp.lo[k] = 0.5 * (ix->lo[k] + ix->hi[k]);
-        const double r = 0.5 * (ix->hi[k] - ix->lo[k]) * (1.0 + ldexp(1.0, -40));
-        pb += r * r;
-        rmax = std::max(rmax, r);
-    }
-    const double pbound = pb * (1.0 + ldexp(1.0, -20));
-    hp.d = d;
-    hp.dp = ix->dp;
-    const bool tensor = is_tensor_kernel(ix->kernel);
-    const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32 || tensor;
-    const double u_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
-    const double delta = 1.01 * u_t * rmax;
-    double c1 = -1.0;  // (the tensor-core filter's bound: tc_c1)
-    if (tensor) c1 = tc_c1(ix->dp, ix->kernel);
-    pack_coefficients(ix->eps, pbound, delta, u_t, d, ix->dp, &hp, c1);
+    clock.mark();
+    // ---- packing (gathered through perm) ----
     if (use_f32)
         SJ_TRY(pack_points<float>(ix, pts, hp));
     else
@@ -1217,6 +1353,7 @@ int build_index(Index* ix, const double* pts) {
     ix->filter_band_rel = 2.0 * (c1 > 0 ? c1 : 6.2 * gamma_n(u_t, ix->dp + 1)) * 2.0 * pbound / ix->e2;
     ix->bound_c1 = c1 > 0 ? c1 : 6.2 * gamma_n(u_t, ix->dp + 1);
     ix->bound_p = pbound;
+    clock.mark();
 
     if (dense) {
         // ---- neighbour runs and work items, per key; one read-back at the
@@ -1230,58 +1367,71 @@ int build_index(Index* ix, const double* pts) {
         de.symmetric = ix->opt.symmetric ? 1 : 0;
         de.qmax = (uint32_t)qmax;
         de.K = K;
-        uint32_t* run_cnt = nullptr;  // K counts, then K + 1 offsets
         DenseTotals* dtot = nullptr;
-        SJ_TRY(tmp.alloc(&run_cnt, (size_t)2 * K + 1));
-        uint32_t* run_off = run_cnt + K;
         SJ_TRY(tmp.alloc(&dtot, 1));
         SJ_CK(cudaMemsetAsync(dtot, 0, sizeof(DenseTotals), s));
         const unsigned eb = (unsigned)((K + 127) / 128);
-        k_denum<false><<<eb, 128, 0, s>>>(de, off64, run_cnt, nullptr, nullptr, nullptr, dtot);
-        note_launch();
-        SJ_CK(cudaGetLastError());
-        SJ_TRY((scan_exclusive<uint32_t, LoadU32>(LoadU32{run_cnt}, run_off, K, true, s)));
-        // upper bounds (non-empty cells <= min(n, K), each with at most
-        // 3^(m-1) + 1 runs and at most q / qmax + 1 items) size the run and
-        // item arrays without a read-back; when the run bound is large the
-        // exact count is read back first
+        // runs of a cell: at most 3^(m-1), one more when the self offset
+        // splits (symmetric joins); items: at most q / qmax + 1 per cell
         int mm = ix->m > 0 ? ix->m - 1 : 0, per = 1;
         for (int k = 0; k < mm; ++k) per *= 3;
+        const int64_t slots = per + 1;
         const int64_t cells_max = std::min<int64_t>(n, K);
-        int64_t runs_cap = cells_max * (int64_t)(per + 1);
         const int64_t items_cap = cells_max + n / qmax + 1;
-        if (runs_cap * (int64_t)sizeof(Run) > (int64_t(1) << 30)) {
-            uint32_t total = 0;
-            SJ_CK(cudaMemcpyAsync(&total, run_off + K, 4, cudaMemcpyDeviceToHost, s));
-            SJ_CK(cudaStreamSynchronize(s));
-            runs_cap = (int64_t)total;
-        }
-        SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(runs_cap, 1), s));
+        int64_t runs_cap = 0;
+        uint32_t* run_off = nullptr;  // count pass: K + 1 run offsets
         SJ_TRY(dev_alloc_t(&ix->items, (size_t)std::max<int64_t>(items_cap, 1), s));
-        k_denum<true><<<eb, 128, 0, s>>>(de, off64, nullptr, run_off, ix->runs, ix->items, nullptr);
-        note_launch();
-        SJ_CK(cudaGetLastError());
+        if (K * slots * (int64_t)sizeof(Run) <= (int64_t(512) << 20)) {
+            // one pass: the runs of key k in the fixed slots k * slots ..
+            runs_cap = K * slots;
+            SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(runs_cap, 1), s));
+            k_denum<2><<<eb, 128, 0, s>>>(de, off64, nullptr, nullptr, ix->runs, ix->items, dtot, (uint32_t)slots);
+            note_launch();
+            SJ_CK(cudaGetLastError());
+        } else {
+            // count pass, scan, fill pass; the run array sized by the upper
+            // bound (non-empty cells <= min(n, K)) when that is moderate, else
+            // by the exact count read back
+            uint32_t* run_cnt = nullptr;  // K counts, then K + 1 offsets
+            SJ_TRY(tmp.alloc(&run_cnt, (size_t)2 * K + 1));
+            run_off = run_cnt + K;
+            k_denum<0><<<eb, 128, 0, s>>>(de, off64, run_cnt, nullptr, nullptr, nullptr, dtot, 0u);
+            note_launch();
+            SJ_CK(cudaGetLastError());
+            SJ_TRY((scan_exclusive<uint32_t, LoadU32>(LoadU32{run_cnt}, run_off, K, true, s)));
+            runs_cap = cells_max * slots;
+            if (runs_cap * (int64_t)sizeof(Run) > (int64_t(1) << 30)) {
+                uint32_t total = 0;
+                SJ_CK(cudaMemcpyAsync(&total, run_off + K, 4, cudaMemcpyDeviceToHost, s));
+                SJ_CK(cudaStreamSynchronize(s));
+                runs_cap = (int64_t)total;
+            }
+            SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(runs_cap, 1), s));
+            k_denum<1><<<eb, 128, 0, s>>>(de, off64, nullptr, run_off, ix->runs, ix->items, nullptr, 0u);
+            note_launch();
+            SJ_CK(cudaGetLastError());
+        }
         struct {
             DenseTotals t;
             unsigned long long last_off;
-            uint32_t runs;
         } got{};
         SJ_CK(cudaMemcpyAsync(&got.t, dtot, sizeof(DenseTotals), cudaMemcpyDeviceToHost, s));
         SJ_CK(cudaMemcpyAsync(&got.last_off, off64 + K, 8, cudaMemcpyDeviceToHost, s));
-        SJ_CK(cudaMemcpyAsync(&got.runs, run_off + K, 4, cudaMemcpyDeviceToHost, s));
         SJ_CK(cudaStreamSynchronize(s));
         ix->n_cells = (int64_t)got.t.n_cells;
-        ix->n_runs = (int64_t)got.runs;
+        ix->n_runs = (int64_t)got.t.n_runs;
         ix->n_items = (int64_t)(got.last_off & 0xFFFFFFFFull);
         ix->n_candidates =
             de.symmetric ? (int64_t)(2 * got.t.n_evaluated - got.t.sum_sq) : (int64_t)got.t.n_evaluated;
         ix->n_evaluated = (int64_t)(got.t.n_evaluated - (uses_triangle(ix) ? got.t.tri_skip : 0ull));
-        if ((int64_t)(got.last_off >> 32) != n || ix->n_runs > runs_cap || ix->n_items > items_cap) {
+        if ((int64_t)(got.last_off >> 32) != n || (run_off && ix->n_runs > runs_cap) || ix->n_items > items_cap) {
             set_error("internal: dense index sizes inconsistent (%lld points, %lld runs, %lld items)",
                       (long long)(got.last_off >> 32), (long long)ix->n_runs, (long long)ix->n_items);
             return SJ_ERR_CUDA;
         }
         SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
+        clock.mark();
+        clock.finish(ix);
         return SJ_OK;
     }
 
@@ -1337,6 +1487,8 @@ int build_index(Index* ix, const double* pts) {
     note_launch();
     SJ_CK(cudaGetLastError());
     SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
+    clock.mark();
+    clock.finish(ix);
     return SJ_OK;
 }
 
@@ -1362,7 +1514,10 @@ size_t pack_params_size() { return sizeof(PackParams); }
 int pack_params_fill(void* host_pp, const double* lo, int d, int dp, double eps, double pbound, double delta) {
     PackParams* pp = static_cast<PackParams*>(host_pp);
     memset(pp, 0, sizeof *pp);
-    for (int k = 0; k < d; ++k) pp->lo[k] = lo[k];
+    for (int k = 0; k < d; ++k) {
+        pp->lo[k] = lo[k];
+        pp->order[k] = (uint8_t)k;
+    }
     pp->d = d;
     pp->dp = dp;
     pack_coefficients(eps, pbound, delta, ldexp(1.0, -53), d, dp, pp);
@@ -1371,8 +1526,9 @@ int pack_params_fill(void* host_pp, const double* lo, int d, int dp, double eps,
 
 int launch_pack_f64_raw(const double* pts, const int32_t* perm, int64_t n, const void* host_pp, double* xs, double* y,
                         double* h, double* to, double* ti, cudaStream_t s) {
+    PackOut<double> o{xs, y, h, to, ti, nullptr, nullptr};
     k_pack<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, perm, n, *static_cast<const PackParams*>(host_pp),
-                                                             xs, y, h, to, ti, nullptr);
+                                                             o);
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;

@@ -109,6 +109,10 @@ struct Index {
     void* h = nullptr;          // n: -||y||^2 / 2
     void* thr_out = nullptr;    // n: maybe-in threshold on (y_q.y_c - ||y_q||^2/2)
     void* thr_in = nullptr;     // n: certain-in threshold
+    double* sc_w = nullptr;     // short-circuit (FP64 FMA, sj_options.short_circuit):
+                                // n half remaining norms (after sc_b dims) plus margin
+    int sc_b = 0;               // the checkpoint: after this many kernel dims (0: off)
+    std::vector<int> dim_order; // kernel coordinate k is input dim dim_order[k]
     void* aux = nullptr;        // FP32 filter, padded d <= 8: n float4 records
                                 // (thr_out, thr_in, input index bits, 0)
     int32_t* perm = nullptr;    // sorted position -> input index
@@ -129,6 +133,26 @@ struct Index {
     // events around the distance-tile kernel and its last duration
     cudaEvent_t ev_tile[2] = {nullptr, nullptr};
     double last_tile_ms = 0.0;
+    // build phases (sj_set_tracing): device and host milliseconds of
+    // extent + grid, sort, packing, runs + items; -1 when not traced
+    double phase_dev_ms[4] = {-1, -1, -1, -1};
+    double phase_host_ms[4] = {-1, -1, -1, -1};
+};
+
+// Tracing of the build phases (process-wide switch, sj_set_tracing).
+bool tracing_on();
+// Marks of a traced build: an event on the stream and the host clock at
+// each phase boundary; finish() fills the index's phase times.
+struct PhaseClock {
+    bool on = false;
+    int n = 0;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[5] = {};
+    double host[5] = {};
+    explicit PhaseClock(cudaStream_t st);
+    ~PhaseClock();
+    void mark();
+    void finish(Index* ix);
 };
 
 // Result internals.

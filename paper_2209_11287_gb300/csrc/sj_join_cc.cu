@@ -127,6 +127,8 @@ JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist) {
     p.band_cap = out.band_cap;
     p.batch = static_cast<const BatchJoin*>(out.batch);
     p.aux = static_cast<const float4*>(ix->aux);
+    p.sc_w = ix->sc_w;
+    p.sc_b = ix->sc_b;
     p.dbg = out.dbg;
     p.dbg_cap = out.dbg_cap;
     return p;

@@ -54,6 +54,7 @@ struct CcWarpSmem {
                                                       // of the queries, slot << 4 | query
     int2 stage[kStage];
     double sdist[EMIT ? kStage : 1];
+    double scq[DP >= 16 ? kQMax : 1];  // short-circuit: each query's w
 };
 
 // Maybe-in bitmasks of TC candidates against all queries of the item, d <= 8:
@@ -246,6 +247,12 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
         const int nr = I.r1 - I.r0;
         const ItemRoute R = item_route(st, P, it, lane);
         const uint32_t C = load_item_warp<T, DP>(S, P, I, lane);
+        if constexpr (std::is_same<T, double>::value && DP >= 16) {
+            if (P.sc_w) {  // each query's remainder bound
+                if (lane < kQMax) W.scq[lane] = lane < Q ? P.sc_w[I.q0 + lane] : 0.0;
+                __syncwarp();
+            }
+        }
 
         for (uint32_t base = 0; base < C; base += (uint32_t)SLOTS) {
             int32_t j[TC];
@@ -287,6 +294,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                 for (int q = 0; q < kQMax; ++q)
 #pragma unroll
                     for (int t = 0; t < TC; ++t) acc[t][q] = S.qh[q];
+                bool all_out = false;  // short-circuit taken: every pair of the tile is out
 #pragma unroll
                 for (int kc = 0; kc < DP; kc += KC) {
                     T c[TC][KC];
@@ -304,14 +312,43 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                             for (int t = 0; t < TC; ++t) acc[t][q] = fma_t(qv, c[t][kk], acc[t][q]);
                         }
                     }
+                    if constexpr (std::is_same<T, double>::value && DP >= 16) {
+                        // short-circuit (Sec. III-B) at the checkpoint, after the
+                        // first sc_b dims: with w bounding half the remaining norm
+                        // of each point (plus the rounding margins),
+                        // acc + w_q + w_c below thr_out means the full filter value
+                        // is below it too, i.e. the pair is certainly out; when that
+                        // holds for every pair of the warp's tile the remaining
+                        // dims are skipped
+                        // (a one-pair-per-lane pre-test first: the full test runs
+                        // only when that already holds for the whole warp)
+                        if (P.sc_w && kc + KC == P.sc_b &&
+                            __all_sync(0xffffffffu,
+                                       !valid[0] || order_key(__dadd_ru(acc[0][0], W.scq[0])) <
+                                                        order_key(__dsub_rd(to[0], P.sc_w[j[0]])))) {
+                            bool out = true;
+#pragma unroll
+                            for (int t = 0; t < TC; ++t) {
+                                if (!valid[t]) continue;
+                                const long long kr = order_key(__dsub_rd(to[t], P.sc_w[j[t]]));
+#pragma unroll
+                                for (int q = 0; q < kQMax; ++q)
+                                    if (q < Q) out = out && order_key(__dadd_ru(acc[t][q], W.scq[q])) < kr;
+                            }
+                            if (__all_sync(0xffffffffu, out)) {
+                                all_out = true;
+                                break;
+                            }
+                        }
+                    }
                 }
 #pragma unroll
                 for (int t = 0; t < TC; ++t) {
                     uint32_t b = 0, cb = 0;
 #pragma unroll
                     for (int q = 0; q < kQMax; ++q) {
-                        if (q < Q && ge_threshold(acc[t][q], to[t])) b |= 1u << q;
-                        if (q < Q && ge_threshold(acc[t][q], ti[t])) cb |= 1u << q;
+                        if (!all_out && q < Q && ge_threshold(acc[t][q], to[t])) b |= 1u << q;
+                        if (!all_out && q < Q && ge_threshold(acc[t][q], ti[t])) cb |= 1u << q;
                     }
                     bits[t] = b;
                     cbits[t] = cb;

@@ -38,6 +38,11 @@ struct JoinParams {
     unsigned long long band_cap;
     const BatchJoin* batch;  // null for a single join
     const float4* aux;       // small-d FP32 filter: per point (thr_out, thr_in, input index bits, 0)
+    // short-circuit of the FP64 tile (sj_options.short_circuit): per point, an
+    // upper bound of half its norm over the dims after the checkpoint (the
+    // first sc_b kernel dims) plus the error margin; null when off
+    const double* sc_w;
+    int sc_b;
     // test aid (sj_debug_filter_dump): when set, the FP32 filters record
     // every evaluated (query, candidate) pair with their filter value a as
     // (query sorted position, candidate sorted position, bits of a, 0);

@@ -11,6 +11,7 @@
   sj_index_perm, must list the points by non-decreasing cell key, where the
   keys are computed on the host from the oracle's grid coordinates and sorted
   by torch.sort.
+* Tracing of the build phases (sj_set_tracing / sj_index_phase_ms).
 """
 import numpy as np
 import pytest
@@ -148,3 +149,32 @@ def test_cell_order_matches_independent_sort(d, eps_scale):
     assert torch.equal(got, want)  # same multiset, non-decreasing
     # cells are the runs of equal keys: as many as the independent count
     assert info["n_cells"] == np.unique(key).size
+
+
+def test_phase_tracing():
+    """Tracing on: the four build phases get device and host times (the
+    device times sum to at most the build's device time); off: -1."""
+    w = workloads.uniform4d(n=200000, seed=8)
+    pts = torch.from_numpy(w.points).cuda()
+    binding.sj_set_tracing(True)
+    try:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h = binding.sj_build_index(pts, w.eps, binding.sj_default_options(kernel="filter_f32"))
+        e1.record()
+        torch.cuda.synchronize()
+        try:
+            dev, host = binding.sj_index_phase_ms(h)
+        finally:
+            binding.sj_destroy(h)
+    finally:
+        binding.sj_set_tracing(False)
+    assert np.all(dev >= 0) and np.all(host >= 0)
+    assert dev.sum() <= e0.elapsed_time(e1) * 1.05 + 0.05
+    h = binding.sj_build_index(pts, w.eps, binding.sj_default_options(kernel="filter_f32"))
+    try:
+        dev, host = binding.sj_index_phase_ms(h)
+    finally:
+        binding.sj_destroy(h)
+    assert np.all(dev == -1) and np.all(host == -1)

@@ -70,12 +70,13 @@ def _shard_rank(rank, world, port, q):
     # build is deterministic); heavy-tailed like dense cells
     g = np.random.Generator(np.random.PCG64(77))
     work = (g.pareto(1.5, size=50000) * 1000).astype(np.int64) + 1
+    work[g.random(50000) < 0.2] = 0  # items that continue their cell
     i0, i1 = bench.shard_of(work, rank, world)
     mine = int(work[i0:i1].sum())
     counts = bench.gather_counts(mine, world, torch.device("cpu"))
     dist.barrier()
     dist.destroy_process_group()
-    q.put((rank, i0, i1, mine, counts, int(work.sum()), int(work.max())))
+    q.put((rank, i0, i1, mine, counts, int(work.sum()), int(work.max()), i0 == 50000 or work[i0] > 0))
 
 
 @pytest.mark.parametrize("world", [2, 3])
@@ -98,8 +99,10 @@ def test_gloo_ranks_shard_the_items_and_gather_counts(world):
     # contiguous, disjoint, covering [0, n_items)
     assert out[0][1] == 0 and out[-1][2] == 50000
     assert all(out[k][2] == out[k + 1][1] for k in range(world - 1))
-    # balanced to within one item's work of an equal share
+    # balanced to within one item's work of an equal share, never starting
+    # inside a cell (an item of no work)
     assert all(abs(o[3] - total / world) <= wmax for o in out)
+    assert all(o[7] for o in out)
     # every rank gathered the same counts, rank order, summing to the whole
     for o in out:
         assert o[4] == [x[3] for x in out]
