@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
 FP64_DFMA_TFLOPS = 1.255                                  # measured, profiles/fp64_peaks_gb300.txt
 FP64_DMMA_TFLOPS = 1.102                                  # measured, profiles/fp64_peaks_gb300.txt
-KERNEL_NAMES = {"filter_f32": "k_join_cc<float>", "fp64_fma": "k_join_cc<double>",
+KERNEL_NAMES = {"filter_f32": "k_join_f32s (d <= 8) | k_join_cc<float>", "fp64_fma": "k_join_cc<double>",
                 "fp64_fma_sc": "k_join_cc<double> (short-circuit)", "fp64_dmma": "k_join_dmma",
                 "filter_bf16x3": "k_join_tc", "filter_bf16x2": "k_join_tc"}
 DTYPES = {"auto": "bf16x2|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64",
@@ -393,8 +393,8 @@ def kernel_source_sha(kname):
     tile header), to tie committed counters to the code they were taken on."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2209_11287_gb300", "csrc")
-    main = {"fp64_dmma": "sj_join_dmma.cu", "filter_bf16x3": "sj_join_tc.cu",
-            "filter_bf16x2": "sj_join_tc.cu"}.get(kname, "sj_join_cc.cu")
+    main = {"fp64_dmma": "sj_join_dmma.cu", "filter_bf16x3": "sj_join_tc.cu", "filter_bf16x2": "sj_join_tc.cu",
+            "filter_f32": "sj_join_f32s.cu"}.get(kname, "sj_join_cc.cuh")
     files = [main, "sj_join_common.cuh"]
     h = hashlib.sha256()
     for f in files:

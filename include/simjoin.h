@@ -500,6 +500,32 @@ SJ_API int sj_index_perm(sj_handle h, int32_t* perm_out);
  */
 SJ_API int sj_dbscan(const sj_result* r, int64_t n, int32_t min_pts, int32_t* labels_out, int64_t* n_clusters);
 
+/* ---- the distance tile alone; kNN from the join ------------------------- */
+/*
+ * sj_sqdist_tile: out[i * nb + j] = the squared distance of A's row i and
+ * B's row j, for all i < m, j < nb (the brute-force distance tile of the
+ * paper's Fig. 3 experiment, Sec. IV, as an operation of its own), in the
+ * decision rule's arithmetic (binary64, dimension order, subtraction, product
+ * and sum each rounded): exactly the s the join decides with.  A: m x d, B:
+ * nb x d row-major binary64, out: m x nb binary64, all device pointers owned
+ * by the caller; m <= 65535 * 64.  Asynchronous on `stream`.  Errors:
+ * SJ_ERR_ARG, SJ_ERR_CUDA.
+ *
+ * sj_knn_from_join: for every point of a single join's result with
+ * distances (sj_options.emit_distances = 1) over n points, its k nearest
+ * eps-neighbours other than itself, by (distance, index) ascending (the reuse
+ * of the join for kNN the paper names as future work, Sec. V): idx_out and
+ * dist_out n x k (row-major; -1 and +inf past the found ones), found_out n
+ * (neighbours found, at most k: fewer when the point has fewer than k other
+ * points within eps); host or device memory.  Synchronous.  Errors:
+ * SJ_ERR_ARG (no distances, a batched result, k outside 1 .. 1024),
+ * SJ_ERR_RESULT_OVERFLOW, SJ_ERR_OOM, SJ_ERR_CUDA.
+ */
+SJ_API int sj_sqdist_tile(const double* A, int64_t m, const double* B, int64_t nb, int32_t d, double* out,
+                          void* stream);
+SJ_API int sj_knn_from_join(const sj_result* r, int64_t n, int32_t k, int32_t* idx_out, double* dist_out,
+                            int32_t* found_out);
+
 /* ---- tracing ------------------------------------------------------------ */
 /*
  * No counterpart in the paper (which reports response times only).

@@ -107,7 +107,9 @@ _i32 = ctypes.c_int32
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library to load: SJ_LIBRARY when set (the bounds-checking build in
+    its test), else the regular build."""
+    return os.environ.get("SJ_LIBRARY") or _build.LIB
 
 
 def load():
@@ -187,6 +189,10 @@ def load():
         lib.sj_self_join_range.restype = ctypes.c_int
         lib.sj_dbscan.argtypes = [ctypes.POINTER(sj_result), _i64, _i32, _vp, ctypes.POINTER(_i64)]
         lib.sj_dbscan.restype = ctypes.c_int
+        lib.sj_sqdist_tile.argtypes = [_vp, _i64, _vp, _i64, _i32, _vp, _vp]
+        lib.sj_sqdist_tile.restype = ctypes.c_int
+        lib.sj_knn_from_join.argtypes = [ctypes.POINTER(sj_result), _i64, _i32, _vp, _vp, _vp]
+        lib.sj_knn_from_join.restype = ctypes.c_int
         lib.sj_set_tracing.argtypes = [_i32]
         lib.sj_set_tracing.restype = None
         lib.sj_index_phase_ms.argtypes = [_vp, _vp, _vp]
@@ -609,3 +615,29 @@ def sj_dbscan(result: sj_result, n: int, min_pts: int):
     k = _i64(0)
     _check(load().sj_dbscan(ctypes.byref(result), int(n), int(min_pts), labels.ctypes.data, ctypes.byref(k)))
     return labels, int(k.value)
+
+
+def sj_sqdist_tile(a, b, out=None, stream=None):
+    """All squared distances between the rows of two float64 CUDA tensors
+    (m x d, nb x d) in the decision rule's arithmetic; returns the m x nb
+    float64 CUDA tensor."""
+    import torch
+    if a.dtype != torch.float64 or b.dtype != torch.float64 or not a.is_cuda or not b.is_cuda:
+        raise ValueError("a and b must be float64 CUDA tensors")
+    a, b = a.contiguous(), b.contiguous()
+    if out is None:
+        out = torch.empty((a.shape[0], b.shape[0]), dtype=torch.float64, device=a.device)
+    _check(load().sj_sqdist_tile(a.data_ptr(), a.shape[0], b.data_ptr(), b.shape[0], a.shape[1], out.data_ptr(),
+                                 _stream_ptr(stream)))
+    return out
+
+
+def sj_knn_from_join(result: sj_result, n: int, k: int):
+    """(indices n x k int32, distances n x k float64, found n int32) of every
+    point's k nearest other eps-neighbours from a result with distances."""
+    idx = np.empty((int(n), int(k)), dtype=np.int32)
+    dist = np.empty((int(n), int(k)), dtype=np.float64)
+    found = np.empty(int(n), dtype=np.int32)
+    _check(load().sj_knn_from_join(ctypes.byref(result), int(n), int(k), idx.ctypes.data, dist.ctypes.data,
+                                   found.ctypes.data))
+    return idx, dist, found

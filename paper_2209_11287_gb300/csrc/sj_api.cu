@@ -134,6 +134,19 @@ bool is_device_pointer(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int side_stream(int device, cudaStream_t* out) {
+    static std::mutex mu;
+    static cudaStream_t streams[64];
+    if (device < 0 || device >= 64) {
+        set_error("device ordinal %d out of range", device);
+        return SJ_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[device]) SJ_CK(cudaStreamCreateWithFlags(&streams[device], cudaStreamNonBlocking));
+    *out = streams[device];
+    return SJ_OK;
+}
+
 int device_sm_count(int device) {
     static int cache[64];
     if (device < 0 || device >= 64) return 1;
@@ -165,6 +178,8 @@ static void release_index(Index* ix) {
     dev_free(ix->counters, s);
     if (ix->ev_tile[0]) cudaEventDestroy(ix->ev_tile[0]);
     if (ix->ev_tile[1]) cudaEventDestroy(ix->ev_tile[1]);
+    if (ix->ev_side[0]) cudaEventDestroy(ix->ev_side[0]);
+    if (ix->ev_side[1]) cudaEventDestroy(ix->ev_side[1]);
 }
 
 // AUTO: the certified filters always beat the plain FP64 kernels on this part
@@ -454,6 +469,9 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
         } else if ((int)c[4] != 0) {
             set_error("a bounded wait in the tensor-core kernel expired");
             st = SJ_ERR_TIMEOUT;
+        } else if (c[7] != 0) {
+            set_error("bounds check at site %llu failed (debug build)", c[7]);
+            st = SJ_ERR_CUDA;
         }
     }
     ix->last_tile_ms = 0.0;

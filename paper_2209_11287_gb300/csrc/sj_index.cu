@@ -284,6 +284,10 @@ int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_
     return scan_exclusive<uint32_t, LoadU32>(LoadU32{in}, out, n, false, s);
 }
 
+int scan_exclusive_u32_total(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
+    return scan_exclusive<uint32_t, LoadU32>(LoadU32{in}, out, n, true, s);
+}
+
 // ---------------------------------------------------------------------------
 // LSD radix sort of (uint64 key, int32 value), 8-bit digits, stable passes
 // ---------------------------------------------------------------------------
@@ -429,6 +433,8 @@ struct PackParams {
     double lo[SJ_MAX_D];
     // thresholds as affine functions of the computed norm pc (see below)
     double a_out, b_out, a_in, b_in;
+    // the same coefficients rounded outward to binary32 once (FP32 kernels)
+    float af_out, bf_out, af_in, bf_in;
     int has_in;
     int d, dp;
     // kernel coordinate k is input dim order[k] (identity unless the
@@ -481,7 +487,36 @@ void pack_coefficients(double eps, double pbound, double delta, double u_t, int 
     // thr_in = pc (1/2 + c1/2 + m (1 + c1)) + ((c1 P - si)/2 + m (si + c1 P))
     pp->a_in = nextafter(0.5 + 0.5 * c1 + m * (1.0 + c1), INFINITY);
     pp->b_in = nextafter((c1 * pbound - si) * 0.5 + m * (si + c1 * pbound), INFINITY);
+    // binary32 copies, rounded down (a_out) or up (the others), as the
+    // device's __double2float_rd / _ru would round them
+    auto down = [](double v) {
+        float f = (float)v;
+        if ((double)f > v) f = nextafterf(f, -INFINITY);
+        return f;
+    };
+    auto up = [](double v) {
+        float f = (float)v;
+        if ((double)f < v) f = nextafterf(f, INFINITY);
+        return f;
+    };
+    pp->af_out = down(pp->a_out);
+    pp->bf_out = up(pp->b_out);
+    pp->af_in = up(pp->a_in);
+    pp->bf_in = up(pp->b_in);
 }
+
+// The two thresholds of a point with computed norm pc, one fma each, rounded
+// outward (see pack_coefficients).
+__device__ __forceinline__ float pack_thr_out(const PackParams& pp, float pc) {
+    return __fmaf_rd(pp.af_out, pc, -pp.bf_out);
+}
+__device__ __forceinline__ double pack_thr_out(const PackParams& pp, double pc) {
+    return __fma_rd(pp.a_out, pc, -pp.b_out);
+}
+__device__ __forceinline__ float pack_thr_in(const PackParams& pp, float pc) {
+    return __fmaf_ru(pp.af_in, pc, pp.bf_in);
+}
+__device__ __forceinline__ double pack_thr_in(const PackParams& pp, double pc) { return __fma_ru(pp.a_in, pc, pp.b_in); }
 
 __device__ __forceinline__ float fma_pack(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_pack(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -529,8 +564,8 @@ __device__ __forceinline__ void pack_one(const double* __restrict__ xr, int32_t 
         if (k + 1 == pp.sc_b) nrm_b = nrm;  // the partial norm at the short-circuit checkpoint
     }
     o.h[p] = -nrm * T(0.5);
-    const T to = thr_down(pp.a_out, nrm, pp.b_out);
-    const T ti = pp.has_in ? thr_up(pp.a_in, nrm, pp.b_in) : T(INFINITY);
+    const T to = pack_thr_out(pp, nrm);
+    const T ti = pp.has_in ? pack_thr_in(pp, nrm) : T(INFINITY);
     o.thr_out[p] = to;
     o.thr_in[p] = ti;
     if (o.aux) o.aux[p] = make_float4((float)to, (float)ti, __int_as_float(src_i), 0.f);
@@ -1183,11 +1218,65 @@ double tc_c1(int dp, int kernel) {
     return norms + acc + split;
 }
 
+// The dense path's enumeration: its parameters, the totals, and the item
+// array (upper bound: at most q / qmax + 1 items per non-empty cell, at most
+// min(n, K) cells); with fixed run slots (K (3^(m-1) + 1) runs in at most
+// 512 MB) also the run array, so one pass fills both.
+struct DensePlan {
+    DenseEnum de;
+    DenseTotals* dtot;
+    unsigned eb;
+    int64_t slots, cells_max, items_cap, runs_cap;
+    bool fixed;
+};
+
+static int dense_enum_prepare(Index* ix, int64_t K, int qmax, Scratch& tmp, DensePlan* dp) {
+    cudaStream_t s = ix->stream;
+    const int64_t n = ix->n;
+    DenseEnum& de = dp->de;
+    de = DenseEnum{};
+    de.m = ix->m;
+    for (int i = 0; i < ix->m; ++i) {
+        de.ncell[i] = (uint32_t)ix->ncell[i];
+        de.stride[i] = (uint32_t)ix->stride[i];
+    }
+    de.symmetric = ix->opt.symmetric ? 1 : 0;
+    de.qmax = (uint32_t)qmax;
+    de.K = K;
+    SJ_TRY(tmp.alloc(&dp->dtot, 1));
+    SJ_CK(cudaMemsetAsync(dp->dtot, 0, sizeof(DenseTotals), s));
+    dp->eb = (unsigned)((K + 127) / 128);
+    // runs of a cell: at most 3^(m-1), one more when the self offset splits
+    // (symmetric joins)
+    int mm = ix->m > 0 ? ix->m - 1 : 0, per = 1;
+    for (int k = 0; k < mm; ++k) per *= 3;
+    dp->slots = per + 1;
+    dp->cells_max = std::min<int64_t>(n, K);
+    dp->items_cap = dp->cells_max + n / qmax + 1;
+    SJ_TRY(dev_alloc_t(&ix->items, (size_t)std::max<int64_t>(dp->items_cap, 1), s));
+    dp->fixed = K * dp->slots * (int64_t)sizeof(Run) <= (int64_t(512) << 20);
+    dp->runs_cap = 0;
+    if (dp->fixed) {
+        dp->runs_cap = K * dp->slots;
+        SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(dp->runs_cap, 1), s));
+    }
+    return SJ_OK;
+}
+
 int build_index(Index* ix, const double* pts) {
     cudaStream_t s = ix->stream;
     const int64_t n = ix->n;
     const int d = ix->d;
     Scratch tmp(s);  // temporaries, released on every return
+    // side-stream work (below) is joined back into s on every return, before
+    // the temporaries above or the index's arrays are released
+    struct SideJoin {
+        cudaStream_t s;
+        cudaEvent_t ev = nullptr;
+        ~SideJoin() {
+            if (ev) cudaStreamWaitEvent(s, ev, 0);
+        }
+    } side_join{s};
     PhaseClock clock(s);
     clock.mark();
     // ---- extent and finiteness check (one sync) ----
@@ -1300,6 +1389,7 @@ int build_index(Index* ix, const double* pts) {
                        kspace < (long double)0x7FFFFFFF;
     const int qmax = item_qmax(ix);
     const int64_t K = dense ? (int64_t)kspace : 0;
+    DensePlan dp{};  // dense path: the enumeration's parameters and arrays
     unsigned long long* off64 = nullptr;     // dense: K + 1 of (first position << 32 | first item)
     unsigned long long* ckey_tmp = nullptr;  // sparse: cell table before the cell count is known
     int32_t* cstart_tmp = nullptr;
@@ -1318,6 +1408,24 @@ int build_index(Index* ix, const double* pts) {
         SJ_CK(cudaGetLastError());
         SJ_TRY((scan_exclusive<unsigned long long, LoadCountItems>(LoadCountItems{cnt, (uint32_t)qmax}, off64, K,
                                                                    true, s)));
+        // the runs and items depend on the keys' first positions only, the
+        // scatter and the packing on the order: with fixed run slots the
+        // enumeration runs on a side stream beside them
+        SJ_TRY(dense_enum_prepare(ix, K, qmax, tmp, &dp));
+        if (dp.fixed) {
+            cudaStream_t side = nullptr;
+            SJ_TRY(side_stream(ix->device, &side));
+            for (int e = 0; e < 2; ++e)
+                if (!ix->ev_side[e]) SJ_CK(cudaEventCreateWithFlags(&ix->ev_side[e], cudaEventDisableTiming));
+            SJ_CK(cudaEventRecord(ix->ev_side[0], s));
+            SJ_CK(cudaStreamWaitEvent(side, ix->ev_side[0], 0));
+            k_denum<2><<<dp.eb, 128, 0, side>>>(dp.de, off64, nullptr, nullptr, ix->runs, ix->items, dp.dtot,
+                                                (uint32_t)dp.slots);
+            note_launch();
+            SJ_CK(cudaGetLastError());
+            SJ_CK(cudaEventRecord(ix->ev_side[1], side));
+            side_join.ev = ix->ev_side[1];
+        }
         k_key_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(key32, n, off64, fill, ix->perm);
         note_launch();
         SJ_CK(cudaGetLastError());
@@ -1358,36 +1466,16 @@ int build_index(Index* ix, const double* pts) {
     if (dense) {
         // ---- neighbour runs and work items, per key; one read-back at the
         // end of the build ----
-        DenseEnum de{};
-        de.m = ix->m;
-        for (int i = 0; i < ix->m; ++i) {
-            de.ncell[i] = (uint32_t)ix->ncell[i];
-            de.stride[i] = (uint32_t)ix->stride[i];
-        }
-        de.symmetric = ix->opt.symmetric ? 1 : 0;
-        de.qmax = (uint32_t)qmax;
-        de.K = K;
-        DenseTotals* dtot = nullptr;
-        SJ_TRY(tmp.alloc(&dtot, 1));
-        SJ_CK(cudaMemsetAsync(dtot, 0, sizeof(DenseTotals), s));
-        const unsigned eb = (unsigned)((K + 127) / 128);
-        // runs of a cell: at most 3^(m-1), one more when the self offset
-        // splits (symmetric joins); items: at most q / qmax + 1 per cell
-        int mm = ix->m > 0 ? ix->m - 1 : 0, per = 1;
-        for (int k = 0; k < mm; ++k) per *= 3;
-        const int64_t slots = per + 1;
-        const int64_t cells_max = std::min<int64_t>(n, K);
-        const int64_t items_cap = cells_max + n / qmax + 1;
-        int64_t runs_cap = 0;
+        const DenseEnum& de = dp.de;
+        DenseTotals* dtot = dp.dtot;
+        const unsigned eb = dp.eb;
+        const int64_t slots = dp.slots, cells_max = dp.cells_max, items_cap = dp.items_cap;
+        int64_t runs_cap = dp.runs_cap;
         uint32_t* run_off = nullptr;  // count pass: K + 1 run offsets
-        SJ_TRY(dev_alloc_t(&ix->items, (size_t)std::max<int64_t>(items_cap, 1), s));
-        if (K * slots * (int64_t)sizeof(Run) <= (int64_t(512) << 20)) {
-            // one pass: the runs of key k in the fixed slots k * slots ..
-            runs_cap = K * slots;
-            SJ_TRY(dev_alloc_t(&ix->runs, (size_t)std::max<int64_t>(runs_cap, 1), s));
-            k_denum<2><<<eb, 128, 0, s>>>(de, off64, nullptr, nullptr, ix->runs, ix->items, dtot, (uint32_t)slots);
-            note_launch();
-            SJ_CK(cudaGetLastError());
+        if (dp.fixed) {
+            // one pass (launched on the side stream above): the runs of key k
+            // in the fixed slots k * slots ..
+            SJ_CK(cudaStreamWaitEvent(s, ix->ev_side[1], 0));
         } else {
             // count pass, scan, fill pass; the run array sized by the upper
             // bound (non-empty cells <= min(n, K)) when that is moderate, else

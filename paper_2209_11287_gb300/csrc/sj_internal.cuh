@@ -132,6 +132,7 @@ struct Index {
     unsigned long long* counters = nullptr;
     // events around the distance-tile kernel and its last duration
     cudaEvent_t ev_tile[2] = {nullptr, nullptr};
+    cudaEvent_t ev_side[2] = {nullptr, nullptr};  // fork / join of the build's side-stream work
     double last_tile_ms = 0.0;
     // build phases (sj_set_tracing): device and host milliseconds of
     // extent + grid, sort, packing, runs + items; -1 when not traced
@@ -302,8 +303,13 @@ int round_dim(int d);
 // ---- radix sort / scan (sj_index.cu) ------------------------------------------
 int radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cudaStream_t s);
 int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+// As scan_exclusive_u32, also writing the total to out[n].
+int scan_exclusive_u32_total(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
 
 int device_sm_count(int device);
+// A second stream per device owned by the library (created on first use,
+// non-blocking), for build work that can overlap the caller's stream.
+int side_stream(int device, cudaStream_t* out);
 
 // Kernels launched by the library in this process (reported by
 // sj_kernel_launches); every launch site calls note_launch().

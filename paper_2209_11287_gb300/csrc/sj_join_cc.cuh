@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(NW * 32, cc_min_blocks<T, DP>()) k_join_cc(Joi
                 if (valid[t]) {
                     uint8_t fl;
                     j[t] = map_candidate_flag<T, DP>(S, nr, v, fl);
+                    if (!SJ_BOUND(P, j[t] >= 0 && j[t] < P.n_points, 21)) j[t] = 0;
                     to[t] = TO[j[t]];
                     ti[t] = TI[j[t]];
                     if constexpr (EMIT) W.cj[slot] = j[t];

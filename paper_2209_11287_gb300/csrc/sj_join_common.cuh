@@ -58,6 +58,18 @@ __device__ __forceinline__ void dbg_record(const JoinParams& P, int32_t qs, int3
 }
 
 JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist);
+
+// Bounds checks of the debug build (compiled with -DSJ_DEBUG_BOUNDS): a
+// failed check records its site number in counters[7] (the first one wins),
+// evaluates to false so the caller skips the access it guards, and the host
+// reports SJ_ERR_CUDA naming the site.  In the regular build they are no
+// code at all.
+#ifdef SJ_DEBUG_BOUNDS
+#define SJ_BOUND(P, cond, site) \
+    ((cond) ? true : (atomicCAS(&(P).counters[7], 0ull, (unsigned long long)(site)), false))
+#else
+#define SJ_BOUND(P, cond, site) true
+#endif
 // CUDA-core tile launch for padded dimension DP (sj_join_cc.cuh; explicit
 // instantiations in sj_cc_d*.cu).
 template <typename T, int DP>

@@ -110,7 +110,8 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
         float to = INFINITY, ti = INFINITY;
         if (v < C) {
             while (W.rpre[r + 1] <= v) ++r;
-            const int32_t jj = W.rstart[r] + (int32_t)(v - W.rpre[r]);
+            int32_t jj = W.rstart[r] + (int32_t)(v - W.rpre[r]);
+            if (!SJ_BOUND(P, jj >= 0 && jj < P.n_points && r < RUNS, 11)) jj = 0;
             const uint32_t f = W.rmir[r];
             load_coords<DP>(Y, jj, c);
             const float4 ax = AUX[jj];
@@ -198,6 +199,12 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
         if (st.cnt + total <= st.cap) {
             // the common case: the chunk's output fits the stage
             int pos = st.cnt + off;
+            if (!SJ_BOUND(P, pos >= 0 && pos + nout <= st.cap, 12)) {
+                pos = 0;
+                nout = 0;
+#pragma unroll
+                for (int t = 0; t < TC; ++t) cin[t] = 0u;  // (the debug build skips this lane's pairs)
+            }
 #pragma unroll
             for (int t = 0; t < TC; ++t) {
                 uint32_t b = cin[t];
@@ -322,6 +329,8 @@ __global__ void __launch_bounds__(kF32sWarps * 32, f32s_min_blocks<DP>()) k_join
         const Item I = P.items[it];
         const int Q = I.q1 - I.q0;
         const int nr = I.r1 - I.r0;
+        if (!SJ_BOUND(P, I.q0 >= 0 && Q >= 1 && Q <= kQMax && I.q1 <= P.n_points && nr >= 0 && nr <= RUNS, 13))
+            continue;
         const ItemRoute R = item_route(st, P, it, lane);
         // the item's queries (duplicated coordinates) and runs
         for (int i = lane; i < kQMax * DP; i += 32) {

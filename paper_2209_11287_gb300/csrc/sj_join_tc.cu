@@ -513,6 +513,7 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                 const int gi = row >> 3;
                 const int32_t g = M.g[gi];
                 p = g * 8 + (row & 7);
+                if (g >= 0 && !SJ_BOUND(P, p < P.n_points + kTcPadRows, 31)) p = 0;
                 valid = g >= 0 && p >= M.lo[gi] && p < M.hi[gi];
                 fl = M.fl[gi];
                 __syncwarp();
