@@ -43,9 +43,9 @@ FP64_DFMA_TFLOPS = 1.255                                  # measured, profiles/f
 FP64_DMMA_TFLOPS = 1.102                                  # measured, profiles/fp64_peaks_gb300.txt
 KERNEL_NAMES = {"filter_f32": "k_join_f32s (d <= 8) | k_join_cc<float>", "fp64_fma": "k_join_cc<double>",
                 "fp64_fma_sc": "k_join_cc<double> (short-circuit)", "fp64_dmma": "k_join_dmma",
-                "filter_bf16x3": "k_join_tc", "filter_bf16x2": "k_join_tc"}
+                "filter_bf16x3": "k_join_tc", "filter_bf16x2": "k_join_tc", "filter_fp16x2": "k_join_tc"}
 DTYPES = {"auto": "bf16x2|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64",
-          "filter_bf16x2": "bf16x2+f64", "fp64_fma": "f64",
+          "filter_bf16x2": "bf16x2+f64", "filter_fp16x2": "fp16x2+f64", "fp64_fma": "f64",
           "fp64_dmma": "f64", "fp64_fma_sc": "f64", "tuned": "bf16x2|bf16x3|f32+f64", "tuned_graph": "bf16x2|bf16x3|f32+f64",
           "auto_graph": "bf16x2|f32+f64"}
 
@@ -133,9 +133,11 @@ METRICS = {
 DEFAULT_VARIANTS = {
     "uniform4d": ["filter_f32", "tuned", "fp64_fma", "fp64_dmma"],
     "uniform2d": ["filter_f32", "fp64_fma", "fp64_dmma", "filter_bf16x2"],
-    "mixture16d": ["filter_bf16x2", "tuned", "filter_bf16x3", "filter_f32", "fp64_fma", "fp64_fma_sc"],
-    "expo64d": ["filter_bf16x2", "filter_bf16x3", "filter_f32"],
-    "brute16d": ["filter_bf16x2", "filter_bf16x3", "filter_f32", "fp64_fma", "fp64_fma_sc", "fp64_dmma"],
+    "mixture16d": ["filter_bf16x2", "tuned", "filter_bf16x3", "filter_fp16x2", "filter_f32", "fp64_fma",
+                   "fp64_fma_sc"],
+    "expo64d": ["filter_bf16x2", "filter_bf16x3", "filter_fp16x2", "filter_f32"],
+    "brute16d": ["filter_bf16x2", "filter_bf16x3", "filter_fp16x2", "filter_f32", "fp64_fma", "fp64_fma_sc",
+                 "fp64_dmma"],
 }
 
 
@@ -394,7 +396,7 @@ def kernel_source_sha(kname):
     import hashlib
     csrc = os.path.join(ROOT, "paper_2209_11287_gb300", "csrc")
     main = {"fp64_dmma": "sj_join_dmma.cu", "filter_bf16x3": "sj_join_tc.cu", "filter_bf16x2": "sj_join_tc.cu",
-            "filter_f32": "sj_join_f32s.cu"}.get(kname, "sj_join_cc.cuh")
+            "filter_fp16x2": "sj_join_tc.cu", "filter_f32": "sj_join_f32s.cu"}.get(kname, "sj_join_cc.cuh")
     files = [main, "sj_join_common.cuh"]
     h = hashlib.sha256()
     for f in files:
@@ -445,9 +447,10 @@ def roofline(kname, w, r, kern_ms):
     dp = 2
     while dp < w.d:
         dp *= 2
-    if kname in ("filter_bf16x3", "filter_bf16x2"):
+    if kname in ("filter_bf16x3", "filter_bf16x2", "filter_fp16x2"):
         kp = ((6 if kname == "filter_bf16x3" else 3) * dp + 3 + 15) // 16 * 16
         flops = 2.0 * kp * r["n_evaluated"]
+        # (fp16 and bf16 have the same dense tensor rate: the bf16 peak serves both)
         fp_peak, unit_bound = float(peaks.get("bf16_tflops", 1900.0)), "tensor"
     else:
         flops = 2.0 * w.d * r["n_evaluated"]

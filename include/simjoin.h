@@ -82,6 +82,11 @@ extern "C" {
 #define SJ_KERNEL_FILTER_BF16X2 5 /* as BF16X3 with a 2-term split (3 products
                                      per dim: half the K, a slightly wider
                                      certified band); d <= 64 */
+#define SJ_KERNEL_FILTER_FP16X2 6 /* as BF16X2 with fp16 terms (11 significant
+                                     bits each) of the kernel coordinates
+                                     scaled by a power of two into fp16's
+                                     range: the same K, a narrower certified
+                                     band; single joins, d <= 64 */
 
 /* ---- options ----------------------------------------------------------- */
 #define SJ_NO_INDEX (-1)        /* sj_options.indexed_dims: brute force */

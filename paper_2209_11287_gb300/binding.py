@@ -35,6 +35,7 @@ SJ_KERNEL_FP64_DMMA = 2
 SJ_KERNEL_FILTER_F32 = 3
 SJ_KERNEL_FILTER_BF16X3 = 4
 SJ_KERNEL_FILTER_BF16X2 = 5
+SJ_KERNEL_FILTER_FP16X2 = 6
 
 KERNELS = {
     "auto": SJ_KERNEL_AUTO,
@@ -43,6 +44,7 @@ KERNELS = {
     "filter_f32": SJ_KERNEL_FILTER_F32,
     "filter_bf16x3": SJ_KERNEL_FILTER_BF16X3,
     "filter_bf16x2": SJ_KERNEL_FILTER_BF16X2,
+    "filter_fp16x2": SJ_KERNEL_FILTER_FP16X2,
 }
 
 

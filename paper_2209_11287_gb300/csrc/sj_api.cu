@@ -287,7 +287,7 @@ int sj_build_index(const double* pts, int64_t n, int32_t d, double eps, const sj
     sj_options o;
     sj_default_options(&o);
     if (opt) o = *opt;
-    if (o.kernel < SJ_KERNEL_AUTO || o.kernel > SJ_KERNEL_FILTER_BF16X2 || o.indexed_dims < SJ_NO_INDEX ||
+    if (o.kernel < SJ_KERNEL_AUTO || o.kernel > SJ_KERNEL_FILTER_FP16X2 || o.indexed_dims < SJ_NO_INDEX ||
         o.queries_per_item < 0 || o.page_pairs < 0 || o.max_pairs_hint < 0) {
         set_error("invalid options");
         return SJ_ERR_ARG;
@@ -1019,7 +1019,9 @@ int join_batch_impl(const double* const* pts, const int64_t* n, const int32_t* d
     auto group_entry = [&](int dp) -> const TuneEntry* {
         const TuneEntry* e = forced ? tune_find_group(*forced, dp) : nullptr;
         if (!e && !tuned.empty()) e = tune_find_group(tuned, dp);
-        if (!e || e->kernel == SJ_KERNEL_AUTO || e->kernel == SJ_KERNEL_FP64_DMMA) return nullptr;
+        if (!e || e->kernel == SJ_KERNEL_AUTO || e->kernel == SJ_KERNEL_FP64_DMMA ||
+            e->kernel == SJ_KERNEL_FILTER_FP16X2)
+            return nullptr;
         if (is_tensor_kernel(e->kernel) && dp > 64) return nullptr;
         return e;
     };

@@ -5,10 +5,12 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <cmath>
 #include <numeric>
 #include <type_traits>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "sj_internal.cuh"
 
@@ -444,6 +446,9 @@ struct PackParams {
     // margin coefficient (see pack_one)
     int sc_b;
     double sc_coef, sc_p;
+    // kernel coordinates y = (x - lo) * scale, a power of two (1 except for
+    // the FP16x2 filter, whose fp16 terms need |y_k| <= 2^15)
+    double scale = 1.0;
 };
 
 __host__ __device__ inline double gamma_n(double u, int k) { return k * u / (1.0 - k * u); }
@@ -558,7 +563,7 @@ __device__ __forceinline__ void pack_one(const double* __restrict__ xr, int32_t 
     T nrm = T(0), nrm_b = T(0);
     for (int k = 0; k < dp; ++k) {
         const int ok = k < d ? pp.order[k] : k;
-        const T yk = k < d ? T(xr[ok] - pp.lo[ok]) : T(0);
+        const T yk = k < d ? T((xr[ok] - pp.lo[ok]) * pp.scale) : T(0);
         o.y[p * dp + k] = yk;
         nrm = fma_pack(yk, yk, nrm);
         if (k + 1 == pp.sc_b) nrm_b = nrm;  // the partial norm at the short-circuit checkpoint
@@ -1097,15 +1102,23 @@ static int pack_points(Index* ix, const double* pts, const PackParams& hp) {
     return SJ_OK;
 }
 
-// Exact split of an FP32 value into three bf16 terms (8 significant bits
-// each; y has 24, so y = t1 + t2 + t3 with no rounding error, for normal
-// values): each term is the round-to-nearest bf16 of what is left.
-__device__ __forceinline__ void split3(float y, __nv_bfloat16& t1, __nv_bfloat16& t2, __nv_bfloat16& t3) {
-    t1 = __float2bfloat16_rn(y);
-    const float r1 = y - __bfloat162float(t1);
-    t2 = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(t2);
-    t3 = __float2bfloat16_rn(r2);
+// Split of an FP32 value into three 16-bit terms, each the round-to-nearest
+// term of what is left (each difference is exact in FP32).  bf16 (8
+// significant bits, FP32's exponent range): y = t1 + t2 + t3 exactly.  fp16
+// (11 significant bits, normal down to 2^-14, subnormal spacing 2^-24): the
+// terms keep 33 bits, and each remainder is at most 2^-11 of what it splits
+// plus 2^-25 (a subnormal term's rounding).
+__device__ __forceinline__ __nv_bfloat16 to_term(float v, __nv_bfloat16) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ __half to_term(float v, __half) { return __float2half_rn(v); }
+__device__ __forceinline__ float from_term(__nv_bfloat16 t) { return __bfloat162float(t); }
+__device__ __forceinline__ float from_term(__half t) { return __half2float(t); }
+template <typename H>
+__device__ __forceinline__ void split3(float y, H& t1, H& t2, H& t3) {
+    t1 = to_term(y, H());
+    const float r1 = y - from_term(t1);
+    t2 = to_term(r1, H());
+    const float r2 = r1 - from_term(t2);
+    t3 = to_term(r2, H());
 }
 
 // Operand rows of the tensor-core filter for every packed point: K slot
@@ -1128,24 +1141,28 @@ __device__ __forceinline__ int64_t split_at(int64_t p, int k, int kp, int64_t nr
 
 // One thread per 16-byte chunk (8 K slots of one row): consecutive threads
 // write consecutive rows of a chunk, so a warp stores whole 128-byte lines.
-// prod = 6 (BF16x3) or 3 (BF16x2: per dim candidate (c1, c2, c1), query
-// (q1, q1, q2) of the first two split terms, which t1 and t2 of split3 are).
+// prod = 6 (BF16x3) or 3 (BF16x2 and FP16x2: per dim candidate (c1, c2, c1),
+// query (q1, q1, q2) of the first two split terms, which t1 and t2 of split3
+// are).  H: the term type (bf16, or fp16 for FP16x2).  The three h slots hold
+// hs in the candidate row and the split of h / hs in the query row (hs a
+// power of two: 1 for bf16, 2^15 for fp16, whose range stops at 65504).
+template <typename H>
 __global__ void k_pack_split(const float* __restrict__ y, const float* __restrict__ h, int64_t n, int dp, int kp,
-                             int prod, int64_t nrows, __nv_bfloat16* rows_a, __nv_bfloat16* rows_b) {
+                             int prod, int64_t nrows, float hs, H* rows_a, H* rows_b) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int ch = kp >> 3;
     const int64_t grp = t / (8 * ch);
     const int c = (int)((t >> 3) % ch);
     const int64_t p = grp * 8 + (t & 7);
     if (p >= n) return;  // padding rows stay zero
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
-    __align__(16) __nv_bfloat16 av[8], bv[8];
+    const H zero = to_term(0.f, H()), hterm = to_term(hs, H());
+    __align__(16) H av[8], bv[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int k = c * 8 + u;
-        __nv_bfloat16 a = zero, b = zero;
+        H a = zero, b = zero;
         if (k < prod * dp) {
-            __nv_bfloat16 t1, t2, t3;
+            H t1, t2, t3;
             split3(y[p * dp + k / prod], t1, t2, t3);
             if (prod == 6) {
                 switch (k % 6) {  // candidate (c1, c2, c1, c3, c2, c1), query (q1, q1, q2, q1, q2, q3)
@@ -1164,9 +1181,9 @@ __global__ void k_pack_split(const float* __restrict__ y, const float* __restric
                 }
             }
         } else if (k < prod * dp + 3) {
-            __nv_bfloat16 h1, h2, h3;
-            split3(h[p], h1, h2, h3);
-            a = one;
+            H h1, h2, h3;
+            split3(h[p] / hs, h1, h2, h3);  // (exact: hs is a power of two)
+            a = hterm;
             b = k == prod * dp ? h1 : (k == prod * dp + 1 ? h2 : h3);
         }
         av[u] = a;
@@ -1183,17 +1200,25 @@ static int pack_split_rows(Index* ix) {
     ix->kp = tc_kp(ix->dp, ix->kernel);
     const int64_t nrows = ((n + 7) & ~int64_t(7)) + kTcPadRows;
     const size_t elems = (size_t)nrows * ix->kp;
-    __nv_bfloat16 *ra = nullptr, *rb = nullptr;
+    uint16_t *ra = nullptr, *rb = nullptr;  // 16-bit terms (bf16 or fp16)
     SJ_TRY(dev_alloc_t(&ra, elems, s));
     ix->rows_a = ra;
     SJ_TRY(dev_alloc_t(&rb, elems, s));
     ix->rows_b = rb;
-    SJ_CK(cudaMemsetAsync(ra, 0, elems * sizeof(__nv_bfloat16), s));
-    SJ_CK(cudaMemsetAsync(rb, 0, elems * sizeof(__nv_bfloat16), s));
+    SJ_CK(cudaMemsetAsync(ra, 0, elems * sizeof(uint16_t), s));
+    SJ_CK(cudaMemsetAsync(rb, 0, elems * sizeof(uint16_t), s));
     const int64_t threads = ((n + 7) / 8) * 8 * (ix->kp / 8);
-    k_pack_split<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(static_cast<const float*>(ix->y),
-                                                            static_cast<const float*>(ix->h), n, ix->dp, ix->kp,
-                                                            tc_products(ix->kernel), nrows, ra, rb);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    const float* y = static_cast<const float*>(ix->y);
+    const float* hn = static_cast<const float*>(ix->h);
+    if (ix->kernel == SJ_KERNEL_FILTER_FP16X2)
+        k_pack_split<__half><<<blocks, 256, 0, s>>>(y, hn, n, ix->dp, ix->kp, tc_products(ix->kernel), nrows,
+                                                    32768.f, reinterpret_cast<__half*>(ra),
+                                                    reinterpret_cast<__half*>(rb));
+    else
+        k_pack_split<__nv_bfloat16><<<blocks, 256, 0, s>>>(y, hn, n, ix->dp, ix->kp, tc_products(ix->kernel), nrows,
+                                                           1.f, reinterpret_cast<__nv_bfloat16*>(ra),
+                                                           reinterpret_cast<__nv_bfloat16*>(rb));
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
@@ -1208,13 +1233,27 @@ static int pack_split_rows(Index* ix) {
 // products whose term indices sum to 5 or 6) below 2^-23 in all, so at most
 // 2^-23 (Pq + Pc); BF16x2 (y = t1 + t2 + r, |t2| <= 2^-8 |y|, |r| <= 2^-16 |y|;
 // t2 t2', r (t1' + t2') and r' (t1 + t2) left out) at most 3.01 2^-16, so
-// 1.51 2^-16 (Pq + Pc).  The sum is doubled (for 2a) and doubled again for
-// safety.
+// 1.51 2^-16 (Pq + Pc).  FP16x2 (the same three products of fp16 terms of the
+// scaled coordinates v = y S, with S^2 P in (2^28, 2^30]): a term in fp16's
+// subnormal range is off by at most a = 2^-14 whether the tensor core keeps
+// it (2^-25) or flushes it to zero, so |v - t1| <= 2^-11 |v| + a,
+// |r| <= 2^-22 |v| + 1.001 a and |t2| <= 2^-11 (1 + 2^-11) |v| + 2.001 a; the
+// left-out products are at most 3.01 2^-22 |v| |v'| per dim
+// (1.51 2^-22 (Pq + Pc) in all) plus an absolute part below
+// 1.01 a sum_k (|v_k| + |v'_k|) + 5 a^2 dp <= 1.01 2^-13 sqrt(dp P) + 5 dp 2^-28
+// <= 1.02 sqrt(dp) 2^-27 P (as P > 2^28); the query's -||v||^2 / 2 goes in as
+// 2^15 times the 3 fp16 terms of its 2^-15 part (33 bits, each off by at most
+// a), which miss at most 2^-33 of it plus 3 a 2^15 < 2^-25 P.  The sum is
+// doubled (for 2a) and doubled again for safety.
 double tc_c1(int dp, int kernel) {
     const int kp = tc_kp(dp, kernel);
     const double norms = 2.0 * gamma_n(ldexp(1.0, -24), dp);
     const double acc = 4.1 * kp * ldexp(1.0, -22);
-    const double split = kernel == SJ_KERNEL_FILTER_BF16X2 ? 6.1 * ldexp(1.0, -16) : 2.0 * ldexp(1.0, -22);
+    double split = 2.0 * ldexp(1.0, -22);  // BF16x3
+    if (kernel == SJ_KERNEL_FILTER_BF16X2) split = 6.1 * ldexp(1.0, -16);
+    if (kernel == SJ_KERNEL_FILTER_FP16X2)
+        split = 4.0 * (1.51 * ldexp(1.0, -22) + 1.02 * std::sqrt((double)dp) * ldexp(1.0, -27) + ldexp(1.0, -25) +
+                       ldexp(1.0, -33));
     return norms + acc + split;
 }
 
@@ -1368,7 +1407,26 @@ int build_index(Index* ix, const double* pts) {
     const double delta = 1.01 * u_t * rmax;
     double c1 = -1.0;  // (the tensor-core filter's bound: tc_c1)
     if (tensor) c1 = tc_c1(ix->dp, ix->kernel);
-    pack_coefficients(ix->eps, pbound, delta, u_t, d, ix->dp, &hp, c1);
+    // FP16x2: the filter runs on kernel coordinates scaled by S = 2^e, the
+    // largest power of two with S^2 P <= 2^30 (so every coordinate, below
+    // 2^15, is an fp16 value's range, and the terms lost to underflow are
+    // small against P: see tc_c1); eps, P and delta scale with it, every
+    // threshold relation is unchanged (exact scaling)
+    double scale = 1.0;
+    if (ix->kernel == SJ_KERNEL_FILTER_FP16X2 && pbound > 0) {
+        int e = (int)std::floor(0.5 * (30.0 - std::log2(pbound)));
+        e = std::min(200, std::max(-200, e));
+        while (e > -200 && ldexp(pbound, 2 * e) > ldexp(1.0, 30)) --e;
+        while (e < 200 && ldexp(pbound, 2 * (e + 1)) <= ldexp(1.0, 30)) ++e;
+        scale = ldexp(1.0, e);
+        if (ldexp(pbound, 2 * e) <= ldexp(1.0, 28)) {  // (tc_c1 assumes S^2 P > 2^28)
+            set_error("the FP16x2 filter cannot scale an extent this small (P = %g)", pbound);
+            return SJ_ERR_UNSUPPORTED;
+        }
+    }
+    hp.scale = scale;
+    ix->kscale = scale;
+    pack_coefficients(ix->eps * scale, pbound * scale * scale, delta * scale, u_t, d, ix->dp, &hp, c1);
 
     // ---- cell keys, sort and packing ----
     SJ_TRY(dev_alloc_t(&ix->perm, (size_t)n, s));
@@ -1460,7 +1518,7 @@ int build_index(Index* ix, const double* pts) {
     if (tensor) SJ_TRY(pack_split_rows(ix));
     ix->filter_band_rel = 2.0 * (c1 > 0 ? c1 : 6.2 * gamma_n(u_t, ix->dp + 1)) * 2.0 * pbound / ix->e2;
     ix->bound_c1 = c1 > 0 ? c1 : 6.2 * gamma_n(u_t, ix->dp + 1);
-    ix->bound_p = pbound;
+    ix->bound_p = pbound * scale * scale;  // in kernel coordinates
     clock.mark();
 
     if (dense) {
@@ -1601,7 +1659,7 @@ size_t pack_params_size() { return sizeof(PackParams); }
 
 int pack_params_fill(void* host_pp, const double* lo, int d, int dp, double eps, double pbound, double delta) {
     PackParams* pp = static_cast<PackParams*>(host_pp);
-    memset(pp, 0, sizeof *pp);
+    *pp = PackParams{};  // zeros, scale 1
     for (int k = 0; k < d; ++k) {
         pp->lo[k] = lo[k];
         pp->order[k] = (uint8_t)k;

@@ -126,6 +126,7 @@ struct Index {
     int64_t n_cells = 0, n_runs = 0, n_items = 0, n_candidates = 0, n_evaluated = 0;
     double filter_band_rel = 0;  // predicted certified band (relative to eps^2)
     double bound_c1 = 0, bound_p = 0;  // certified bound E = c1 (P + pc) of the filter
+    double kscale = 1.0;        // kernel coordinates = (x - centre) * kscale (a power of two)
 
     // per-join scratch: counters (item queue, result cursor, recheck count,
     // recheck queue fill)
@@ -210,7 +211,9 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
 // joins on the CUDA-core and tensor-core filter kernels): a work item's
 // self-cell candidates start at its own first query and pairs below the
 // diagonal are skipped.
-inline bool is_tensor_kernel(int k) { return k == SJ_KERNEL_FILTER_BF16X3 || k == SJ_KERNEL_FILTER_BF16X2; }
+inline bool is_tensor_kernel(int k) {
+    return k == SJ_KERNEL_FILTER_BF16X3 || k == SJ_KERNEL_FILTER_BF16X2 || k == SJ_KERNEL_FILTER_FP16X2;
+}
 inline bool uses_triangle(const Index* ix) {
     return ix->opt.symmetric &&
            (ix->kernel == SJ_KERNEL_FILTER_F32 || ix->kernel == SJ_KERNEL_FP64_FMA || is_tensor_kernel(ix->kernel));
@@ -245,8 +248,9 @@ int launch_join_tc(Index* ix, const JoinOut& out, int emit_dist);
 int selftest_bounded_wait(cudaStream_t s);
 int launch_recheck(Index* ix, const JoinOut& out, int emit_dist);
 
-// Split products per dim of a tensor-core filter: BF16x3 keeps 6, BF16x2 3.
-constexpr int tc_products(int kernel) { return kernel == SJ_KERNEL_FILTER_BF16X2 ? 3 : 6; }
+// Split products per dim of a tensor-core filter: BF16x3 keeps 6, BF16x2 and
+// FP16x2 3.
+constexpr int tc_products(int kernel) { return kernel == SJ_KERNEL_FILTER_BF16X3 ? 6 : 3; }
 // Padded K of the tensor-core filter for padded dimension dp: the products
 // per dim plus 3 slots for the query term, rounded up to the MMA K of 16.
 constexpr int tc_kp(int dp, int kernel) { return (tc_products(kernel) * dp + 3 + 15) / 16 * 16; }

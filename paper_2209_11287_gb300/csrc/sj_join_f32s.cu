@@ -53,7 +53,7 @@ static_assert(kF32sStage <= kStageMax, "a stage flush resolves at most 32 pages"
 
 template <int DP, int RUNS>
 struct F32sWarp {
-    float2 qd[kQMax][DP];  // query coordinates, each as (v, v)
+    __align__(16) float2 qd[kQMax][DP];  // query coordinates, each as (v, v)
     float2 qh2[kQMax];     // (h, h), h = -||y_q||^2 / 2
     int32_t qid[kQMax];    // output index of each query (batched: instance-local)
     int32_t rstart[RUNS];  // first sorted position of each run
@@ -151,8 +151,18 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
         if (qq >= Q) break;
         const float2 h2 = qh[-qq];
         float2 qv[DP];
+        if constexpr (DP % 2 == 0) {  // rows of DP float2 are 16-byte aligned
+            const float4* q4 = reinterpret_cast<const float4*>(qrow - qq * DP);
 #pragma unroll
-        for (int k = 0; k < DP; ++k) qv[k] = qrow[k - qq * DP];
+            for (int k = 0; k < DP / 2; ++k) {
+                const float4 u = q4[k];
+                qv[2 * k] = make_float2(u.x, u.y);
+                qv[2 * k + 1] = make_float2(u.z, u.w);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < DP; ++k) qv[k] = qrow[k - qq * DP];
+        }
 #pragma unroll
         for (int p = 0; p < TC / 2; ++p) {
             float2 a = h2;
@@ -205,19 +215,45 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
 #pragma unroll
                 for (int t = 0; t < TC; ++t) cin[t] = 0u;  // (the debug build skips this lane's pairs)
             }
+            if constexpr (TC == 2) {
+                // both slots' pairs in one loop (Q <= 16: slot t's queries
+                // at bits 16 t ..), so the warp runs max over lanes of the
+                // lane's pairs, not the sum over slots of the maxima
+                uint32_t b = cin[0] | (cin[1] << 16);
+                if (b) {
+                    uint32_t two = 0;  // bit set: the pair is also written mirrored
 #pragma unroll
-            for (int t = 0; t < TC; ++t) {
-                uint32_t b = cin[t];
-                if (!b) continue;
-                const bool two = ((meta >> (8 * t)) & 3u) != 0u;
-                const int dg = (int)((meta >> (8 * t + 2)) & 63u) - 1;
-                const int32_t ci = W.cid[t * 32 + lane];
-                while (b) {
-                    const int q = __ffs(b) - 1;
-                    b &= b - 1u;
-                    const int32_t qi = W.qid[q];
-                    st.pairs[pos++] = make_int2(qi, ci);
-                    if (two && q != dg) st.pairs[pos++] = make_int2(ci, qi);
+                    for (int t = 0; t < 2; ++t) {
+                        const uint32_t f = (meta >> (8 * t)) & 3u;
+                        const uint32_t dg1 = (meta >> (8 * t + 2)) & 63u;
+                        const uint32_t tw = f ? (dg1 ? ~(1u << (dg1 - 1u)) : 0xFFFFu) & 0xFFFFu : 0u;
+                        two |= tw << (16 * t);
+                    }
+                    const int32_t ci0 = W.cid[lane], ci1 = W.cid[32 + lane];
+                    while (b) {
+                        const int bit = __ffs(b) - 1;
+                        b &= b - 1u;
+                        const int32_t ci = bit >= 16 ? ci1 : ci0;
+                        const int32_t qi = W.qid[bit & 15];
+                        st.pairs[pos++] = make_int2(qi, ci);
+                        if ((two >> bit) & 1u) st.pairs[pos++] = make_int2(ci, qi);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < TC; ++t) {
+                    uint32_t b = cin[t];
+                    if (!b) continue;
+                    const bool two = ((meta >> (8 * t)) & 3u) != 0u;
+                    const int dg = (int)((meta >> (8 * t + 2)) & 63u) - 1;
+                    const int32_t ci = W.cid[t * 32 + lane];
+                    while (b) {
+                        const int q = __ffs(b) - 1;
+                        b &= b - 1u;
+                        const int32_t qi = W.qid[q];
+                        st.pairs[pos++] = make_int2(qi, ci);
+                        if (two && q != dg) st.pairs[pos++] = make_int2(ci, qi);
+                    }
                 }
             }
             st.cnt += total;

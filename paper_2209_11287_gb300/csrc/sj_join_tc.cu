@@ -1,12 +1,14 @@
 // Certified low-precision filter on the 5th-generation tensor cores
-// (tcgen05.mma kind::f16, bf16 operands, FP32 accumulation in TMEM).
+// (tcgen05.mma kind::f16, bf16 or fp16 operands, FP32 accumulation in TMEM).
 //
 // The dot products of Eq. 3 (the tensor-core part of Eq. 4) are formed from a
 // bf16 split of every FP32 kernel coordinate, y = y1 + y2 + y3 exactly (8
 // significant bits each).  BF16x3 keeps the six products whose term indices
 // sum to at most 4: for dim k the candidate row holds (c1, c2, c1, c3, c2, c1)
 // and the query row (q1, q1, q2, q1, q2, q3); BF16x2 keeps three, (c1, c2, c1)
-// against (q1, q1, q2), for half the K.  Three more K slots carry the
+// against (q1, q1, q2), for half the K; FP16x2 keeps the same three products
+// of fp16 terms (11 significant bits) of the coordinates scaled by a power of
+// two into fp16's range, for a narrower band.  Three more K slots carry the
 // query's -||y_q||^2 / 2, split the same way, against ones, so the
 // accumulator ends as a = -||y_q||^2/2 + y_q . y_c, the quantity every other
 // kernel computes.  Each value is compared with per-candidate thresholds
@@ -53,10 +55,11 @@ constexpr int tc_threads(int kp, bool emit) { return 64 + 32 * tc_epi(kp, emit);
 constexpr long long kTcSpin = 1 << 22;  // bound on barrier polls per wait
 
 struct TcParams {
-    const __nv_bfloat16* rows_a;  // candidate role, slice-major 8-row groups
+    const __nv_bfloat16* rows_a;  // candidate role, slice-major 8-row groups (16-bit terms)
     const __nv_bfloat16* rows_b;  // query role, same layout
     long long nrows;              // rows per slice (packed points, padded)
     int* error;                   // set to 1 when a bounded wait expires
+    uint32_t ab_bf16;             // 1: A and B are bf16, 0: both fp16
 };
 
 template <int KP>
@@ -136,9 +139,11 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
-// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major.
-__host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// Instruction descriptor of kind::f16: D f32, A and B of one type (bf16 when
+// ab_bf16 = 1, else fp16), both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc(int m, int n, uint32_t ab_bf16) {
+    return (1u << 4) | ((ab_bf16 & 1u) << 7) | ((ab_bf16 & 1u) << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
@@ -435,7 +440,7 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                 if (X.it < 0) break;
                 if (!bar_wait(&S.b_full, b_ph, abort)) break;
                 b_ph ^= 1u;
-                const uint32_t idesc = umma_idesc(kTcM, X.ncol);
+                const uint32_t idesc = umma_idesc(kTcM, X.ncol, T.ab_bf16);
                 bool fail = false;
                 for (int t = 0; t < X.ntiles && !fail; ++t) {
                     if (!bar_wait(&S.acc_empty[acc], acc_ph ^ 1u, abort)) {
@@ -725,6 +730,7 @@ int launch_join_tc(Index* ix, const JoinOut& out, int emit_dist) {
     t.rows_b = static_cast<const __nv_bfloat16*>(ix->rows_b);
     t.nrows = ((ix->n + 7) & ~int64_t(7)) + kTcPadRows;
     t.error = reinterpret_cast<int*>(ix->counters + 4);
+    t.ab_bf16 = ix->kernel == SJ_KERNEL_FILTER_FP16X2 ? 0u : 1u;
     switch (ix->kp) {
         case 16: return launch_k<16>(ix, p, t);
         case 32: return launch_k<32>(ix, p, t);

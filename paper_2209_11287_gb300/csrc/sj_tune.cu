@@ -32,7 +32,7 @@ struct CachedFile {
 std::mutex g_tune_mu;
 std::map<std::string, CachedFile> g_tune_files;
 
-bool valid_kernel(long k) { return k >= SJ_KERNEL_AUTO && k <= SJ_KERNEL_FILTER_BF16X2; }
+bool valid_kernel(long k) { return k >= SJ_KERNEL_AUTO && k <= SJ_KERNEL_FILTER_FP16X2; }
 
 // Parses one line; *has gets whether it held an entry (blank and comment
 // lines hold none).  Returns false for a malformed line.

@@ -127,6 +127,8 @@ def test_unsupported_kernel_rejected():
         binding.join_batch([np.random.default_rng(0).random((10, 4))], [0.1], kernel="fp64_dmma")
     with pytest.raises(RuntimeError):  # the tensor-core filter stops at d = 64
         binding.join_batch([np.random.default_rng(0).random((10, 65))], [0.1], kernel="filter_bf16x3")
+    with pytest.raises(RuntimeError):  # the FP16x2 filter serves single joins
+        binding.join_batch([np.random.default_rng(0).random((10, 16))], [0.1], kernel="filter_fp16x2")
 
 
 def test_bad_instance_rejected():

@@ -155,7 +155,7 @@ def _check(name, x, eps, kernel):
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
-@pytest.mark.parametrize("kernel", ["filter_f32", "filter_bf16x2", "filter_bf16x3"])
+@pytest.mark.parametrize("kernel", ["filter_f32", "filter_bf16x2", "filter_bf16x3", "filter_fp16x2"])
 def test_certified_bound_per_pair(kernel, case):
     name, x, eps = case
     dp = 1 << max(1, (x.shape[1] - 1).bit_length())

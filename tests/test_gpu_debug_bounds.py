@@ -30,7 +30,7 @@ SCRIPT = textwrap.dedent("""
     for w in cases + [(dense, 0.01)]:
         x, eps = (w.points, w.eps) if hasattr(w, "points") else w
         ref = oracle.join(x, eps)
-        for kernel in ("fp64_fma", "fp64_dmma", "filter_f32", "filter_bf16x3", "filter_bf16x2"):
+        for kernel in ("fp64_fma", "fp64_dmma", "filter_f32", "filter_bf16x3", "filter_bf16x2", "filter_fp16x2"):
             for sym in (1, 0):
                 pairs, _, _ = binding.self_join(torch.from_numpy(x).cuda(), eps, kernel=kernel, symmetric=sym)
                 assert np.array_equal(binding.pairs_to_keys(pairs), ref), (kernel, sym)

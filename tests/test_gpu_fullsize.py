@@ -67,7 +67,7 @@ def _check_whole(pairs, n):
     assert diag.numel() == n and torch.equal(torch.sort(diag).values.cpu(), torch.arange(n, dtype=torch.int32))
 
 
-@pytest.mark.parametrize("kernel", ["filter_bf16x2", "filter_bf16x3", "filter_f32"])
+@pytest.mark.parametrize("kernel", ["filter_bf16x2", "filter_bf16x3", "filter_fp16x2", "filter_f32"])
 def test_mixture16d_full_size(kernel):
     """1M points in 16-D (32 Gaussians), the calibrated eps of the benchmark."""
     w = workloads.mixture16d()
@@ -77,7 +77,7 @@ def test_mixture16d_full_size(kernel):
     assert pairs.shape[0] > 5e7
 
 
-@pytest.mark.parametrize("kernel", ["filter_bf16x2", "filter_bf16x3"])
+@pytest.mark.parametrize("kernel", ["filter_bf16x2", "filter_bf16x3", "filter_fp16x2"])
 def test_expo64d_full_size(kernel):
     """500k points in 64-D (clipped exponential), the calibrated eps."""
     w = workloads.expo64d()

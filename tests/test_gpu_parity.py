@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-KERNELS = ["fp64_fma", "fp64_dmma", "filter_f32", "filter_bf16x3", "filter_bf16x2"]
+KERNELS = ["fp64_fma", "fp64_dmma", "filter_f32", "filter_bf16x3", "filter_bf16x2", "filter_fp16x2"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -295,7 +295,7 @@ def test_no_index_brute_force(kernel):
     assert w.n * (w.n + 1) // 2 <= st["n_evaluated"] <= w.n * w.n
 
 
-@pytest.mark.parametrize("kernel", ["filter_f32", "filter_bf16x2"])
+@pytest.mark.parametrize("kernel", ["filter_f32", "filter_bf16x2", "filter_fp16x2"])
 @pytest.mark.parametrize("emit", [False, True], ids=["pairs", "distances"])
 def test_recheck_queue_overflow(kernel, emit):
     """One point far from the rest makes the kernel coordinates' norms huge,
