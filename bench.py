@@ -44,9 +44,9 @@ FP64_DMMA_TFLOPS = 1.102                                  # measured, profiles/f
 KERNEL_NAMES = {"filter_f32": "k_join_f32s (d <= 8) | k_join_cc<float>", "fp64_fma": "k_join_cc<double>",
                 "fp64_fma_sc": "k_join_cc<double> (short-circuit)", "fp64_dmma": "k_join_dmma",
                 "filter_bf16x3": "k_join_tc", "filter_bf16x2": "k_join_tc", "filter_fp16x2": "k_join_tc"}
-DTYPES = {"auto": "bf16x2|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64",
+DTYPES = {"auto": "fp16x2|bf16x2|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64",
           "filter_bf16x2": "bf16x2+f64", "filter_fp16x2": "fp16x2+f64", "fp64_fma": "f64",
-          "fp64_dmma": "f64", "fp64_fma_sc": "f64", "tuned": "bf16x2|bf16x3|f32+f64", "tuned_graph": "bf16x2|bf16x3|f32+f64",
+          "fp64_dmma": "f64", "fp64_fma_sc": "f64", "tuned": "fp16x2|bf16x2|bf16x3|f32+f64", "tuned_graph": "bf16x2|bf16x3|f32+f64",
           "auto_graph": "bf16x2|f32+f64"}
 
 
@@ -133,10 +133,10 @@ METRICS = {
 DEFAULT_VARIANTS = {
     "uniform4d": ["filter_f32", "tuned", "fp64_fma", "fp64_dmma"],
     "uniform2d": ["filter_f32", "fp64_fma", "fp64_dmma", "filter_bf16x2"],
-    "mixture16d": ["filter_bf16x2", "tuned", "filter_bf16x3", "filter_fp16x2", "filter_f32", "fp64_fma",
+    "mixture16d": ["filter_fp16x2", "tuned", "filter_bf16x2", "filter_bf16x3", "filter_f32", "fp64_fma",
                    "fp64_fma_sc"],
-    "expo64d": ["filter_bf16x2", "filter_bf16x3", "filter_fp16x2", "filter_f32"],
-    "brute16d": ["filter_bf16x2", "filter_bf16x3", "filter_fp16x2", "filter_f32", "fp64_fma", "fp64_fma_sc",
+    "expo64d": ["filter_fp16x2", "filter_bf16x2", "filter_bf16x3", "filter_f32"],
+    "brute16d": ["filter_fp16x2", "filter_bf16x2", "filter_bf16x3", "filter_f32", "fp64_fma", "fp64_fma_sc",
                  "fp64_dmma"],
 }
 

@@ -66,15 +66,22 @@ extern "C" {
 #define SJ_MAX_D 128
 
 /* ---- distance kernels -------------------------------------------------- */
-#define SJ_KERNEL_AUTO 0        /* single joins: SJ_KERNEL_FILTER_BF16X2 for
+#define SJ_KERNEL_AUTO 0        /* single joins: SJ_KERNEL_FILTER_FP16X2 for
                                    16 <= d <= 64, else SJ_KERNEL_FILTER_F32
+                                   (SJ_KERNEL_FP64_FMA for an extent that
+                                   scaled binary32 coordinates cannot hold)
                                    (batched joins: see sj_join_batch) */
 #define SJ_KERNEL_FP64_FMA 1    /* FP64 CUDA-core FMA tiles (expanded form,
                                    Eq. 3) + direct-form recheck of the band */
 #define SJ_KERNEL_FP64_DMMA 2   /* FP64 tensor-core tiles, mma.sync m8n8k4
                                    f64 (the paper's FP64 MMA, Fig. 2) */
 #define SJ_KERNEL_FILTER_F32 3  /* FP32 CUDA-core filter with certified bound,
-                                   FP64 direct recheck of the band */
+                                   FP64 direct recheck of the band.  The
+                                   binary32 filters (this and the tensor-core
+                                   ones) work on coordinates scaled by a power
+                                   of two into binary32's range; an extent
+                                   outside it (squared half-extent below about
+                                   2^-970) gives SJ_ERR_UNSUPPORTED */
 #define SJ_KERNEL_FILTER_BF16X3 4 /* tcgen05 kind::f16 with 3-term bf16 split
                                      operands (6 products per dim), FP32
                                      accumulation in TMEM, certified bound,
@@ -307,8 +314,7 @@ SJ_API int sj_selftest_bounded_wait(void* stream);
  * (kernels SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_BF16X3 / _BF16X2 (padded
  * d <= 64) or SJ_KERNEL_FP64_FMA; AUTO takes SJ_KERNEL_FILTER_BF16X2 for
  * groups of padded dimension 8 .. 64 and the FP32 filter for the others;
- * SJ_KERNEL_FP64_DMMA
- * gives SJ_ERR_UNSUPPORTED).  Pairs carry instance-local indices and
+ * SJ_KERNEL_FP64_DMMA and SJ_KERNEL_FILTER_FP16X2 give SJ_ERR_UNSUPPORTED).  Pairs carry instance-local indices and
  * satisfy the same decision rule as sj_self_join.  The device takes each
  * instance's result pages from one shared pool (opt->page_pairs rounded up
  * to a power of two of at least 64, default 65536 pairs a page); when the
@@ -328,7 +334,7 @@ SJ_API int sj_join_batch(const double* const* pts, const int64_t* n, const int32
  * No counterpart in the paper, which fixes one kernel design for its GPU.
  * The tunable choices of a join here are the distance kernel (which also
  * fixes the split count of the tensor-core operands: none for the FP32
- * filter, 2 terms for BF16X2, 3 for BF16X3), the queries per work item (the
+ * filter, 2 terms for BF16X2 and FP16X2, 3 for BF16X3), the queries per work item (the
  * query tile of a work item, Sec. III-B's shared candidate set) and the
  * number of indexed dims (Sec. II-D).  The autotuner times each candidate
  * configuration on the caller's data with CUDA events on `stream` and keeps
@@ -344,7 +350,7 @@ SJ_API int sj_join_batch(const double* const* pts, const int64_t* n, const int32
 
 /*
  * Tunes a single join of (pts, n, d, eps) (pts host or device, as for
- * sj_build_index).  Candidates: kernel in {FILTER_F32, FILTER_BF16X2 and
+ * sj_build_index).  Candidates: kernel in {FILTER_F32, FILTER_FP16X2 and
  * FILTER_BF16X3 when d <= 64} x queries per item in {the kernel's maximum,
  * half of it, a quarter} (at least 4) x indexed dims in {automatic, one less
  * than the automatic choice}; the FP64 kernels are never candidates (FP64 runs

@@ -186,10 +186,14 @@ static void release_index(Index* ix) {
 // (FP64 runs at ~1/60 of FP32); the tensor-core filter wins once the dot
 // product is long enough to amortise its tiles (measured: d = 64 12x and
 // d = 16 1.3x faster than the FP32 filter), the FP32 CUDA-core filter below.
+// Of the tensor-core filters FP16x2 (the K of BF16x2, a narrower band: fewer
+// binary64 rechecks) is never slower (measured on the 16-D and 64-D
+// workloads).  (build_index turns AUTO into the FP64 tile for an extent that
+// scaled binary32 coordinates cannot hold.)
 static int pick_kernel(const Index* ix) {
     int k = ix->opt.kernel;
     if (k != SJ_KERNEL_AUTO) return k;
-    return (ix->d >= 16 && ix->d <= 64) ? SJ_KERNEL_FILTER_BF16X2 : SJ_KERNEL_FILTER_F32;
+    return (ix->d >= 16 && ix->d <= 64) ? SJ_KERNEL_FILTER_FP16X2 : SJ_KERNEL_FILTER_F32;
 }
 
 int round_dim(int d) {

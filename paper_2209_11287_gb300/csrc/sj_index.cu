@@ -453,6 +453,29 @@ struct PackParams {
 
 __host__ __device__ inline double gamma_n(double u, int k) { return k * u / (1.0 - k * u); }
 
+// Scale of binary32 kernel coordinates: S = 2^e, the largest power of two
+// with S^2 P <= 2^30, so S^2 P is in (2^28, 2^30] (1 when P = 0).  Then no
+// norm, product, threshold or accumulator overflows binary32 (all below
+// 2^31), every coordinate is below 2^15 (an fp16 value: FP16x2), and a
+// coordinate or partial product that underflows is off by at most 2^-149
+// absolute, far below the bound c1 (P + pc) with P > 2^28; eps, P and delta
+// scale with S and every threshold relation of pack_coefficients is
+// unchanged (scaling by a power of two is exact).  False when no such e in
+// [-500, 500] exists (P below about 2^-970 or not finite).
+bool binary32_scale(double pbound, double* scale) {
+    *scale = 1.0;
+    if (pbound == 0.0) return true;
+    if (!(pbound > 0.0) || !std::isfinite(pbound)) return false;
+    int e = (int)std::floor(0.5 * (30.0 - std::log2(pbound)));
+    e = std::min(500, std::max(-500, e));
+    while (e > -500 && ldexp(pbound, 2 * e) > ldexp(1.0, 30)) --e;
+    while (e < 500 && ldexp(pbound, 2 * (e + 1)) <= ldexp(1.0, 30)) ++e;
+    const double ps = ldexp(pbound, 2 * e);
+    if (!(ps > ldexp(1.0, 28) && ps <= ldexp(1.0, 30))) return false;
+    *scale = ldexp(1.0, e);
+    return true;
+}
+
 // Thresholds on a = y_q.y_c - ||y_q||^2/2 computed in T (fma chain over the
 // padded dims, started at -||y_q||^2/2) for candidate c with computed norm
 // pc.  With s_y = ||y_q - y_c||^2 = ||y_c||^2 - 2 a_exact, the evaluation
@@ -1401,29 +1424,23 @@ int build_index(Index* ix, const double* pts) {
     }
     for (int k = 0; k < d; ++k) hp.order[k] = (uint8_t)order[k];
     ix->dim_order = order;
+    // binary32 kernel coordinates (the FP32 and tensor-core filters) are
+    // scaled into binary32's range (binary32_scale); an extent that cannot be
+    // scaled runs the binary64 tile under AUTO and is refused otherwise
+    double scale = 1.0;
+    if ((ix->kernel == SJ_KERNEL_FILTER_F32 || is_tensor_kernel(ix->kernel)) && !binary32_scale(pbound, &scale)) {
+        if (ix->opt.kernel != SJ_KERNEL_AUTO) {
+            set_error("binary32 kernel coordinates cannot hold an extent with P = %g (take an FP64 kernel)", pbound);
+            return SJ_ERR_UNSUPPORTED;
+        }
+        ix->kernel = SJ_KERNEL_FP64_FMA;
+    }
     const bool tensor = is_tensor_kernel(ix->kernel);
     const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32 || tensor;
     const double u_t = use_f32 ? ldexp(1.0, -24) : ldexp(1.0, -53);
     const double delta = 1.01 * u_t * rmax;
     double c1 = -1.0;  // (the tensor-core filter's bound: tc_c1)
     if (tensor) c1 = tc_c1(ix->dp, ix->kernel);
-    // FP16x2: the filter runs on kernel coordinates scaled by S = 2^e, the
-    // largest power of two with S^2 P <= 2^30 (so every coordinate, below
-    // 2^15, is an fp16 value's range, and the terms lost to underflow are
-    // small against P: see tc_c1); eps, P and delta scale with it, every
-    // threshold relation is unchanged (exact scaling)
-    double scale = 1.0;
-    if (ix->kernel == SJ_KERNEL_FILTER_FP16X2 && pbound > 0) {
-        int e = (int)std::floor(0.5 * (30.0 - std::log2(pbound)));
-        e = std::min(200, std::max(-200, e));
-        while (e > -200 && ldexp(pbound, 2 * e) > ldexp(1.0, 30)) --e;
-        while (e < 200 && ldexp(pbound, 2 * (e + 1)) <= ldexp(1.0, 30)) ++e;
-        scale = ldexp(1.0, e);
-        if (ldexp(pbound, 2 * e) <= ldexp(1.0, 28)) {  // (tc_c1 assumes S^2 P > 2^28)
-            set_error("the FP16x2 filter cannot scale an extent this small (P = %g)", pbound);
-            return SJ_ERR_UNSUPPORTED;
-        }
-    }
     hp.scale = scale;
     ix->kscale = scale;
     pack_coefficients(ix->eps * scale, pbound * scale * scale, delta * scale, u_t, d, ix->dp, &hp, c1);
@@ -1699,6 +1716,7 @@ struct BInst {
     double inv_w;
     double a_out, b_out, a_in, b_in;
     int has_in;
+    double scale;  // kernel coordinates (x - centre) * scale (binary32_scale; 1 for binary64)
 };
 
 __device__ __forceinline__ int inst_of_position(const long long* __restrict__ off, int n_inst, long long p) {
@@ -1822,7 +1840,7 @@ __global__ void k_bpack(const double* const* __restrict__ srcp, const int32_t* _
     for (int c = 0; c < dp; ++c) {
         const double v = bcoord(srcp, d_of, off, k, src, c);
         xs[p * dp + c] = v;
-        const T yc = T(v - centre[(int64_t)k * dp + c]);
+        const T yc = T((v - centre[(int64_t)k * dp + c]) * g.scale);
         y[p * dp + c] = yc;
         nrm = fma_pack(yc, yc, nrm);
     }
@@ -1852,7 +1870,7 @@ __global__ void k_bpack_lanes(const double* const* __restrict__ srcp, const int3
         k = inst_of[src];
         const double v = bcoord(srcp, d_of, off, k, src, c);
         xs[p * dp + c] = v;
-        const T yc = T(v - centre[(int64_t)k * dp + c]);
+        const T yc = T((v - centre[(int64_t)k * dp + c]) * P[k].scale);
         y[p * dp + c] = yc;
         sq = yc * yc;
     }
@@ -2096,8 +2114,16 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
             pb += r * r;
             rmax = std::max(rmax, r);
         }
+        const double pbk = pb * (1.0 + ldexp(1.0, -20));
+        double sk = 1.0;  // binary32 kernels: the instance's scale (binary32_scale)
+        if (use_f32 && !binary32_scale(pbk, &sk)) {
+            set_error("batch instance %d: binary32 kernel coordinates cannot hold its extent (P = %g; take "
+                      "SJ_KERNEL_FP64_FMA)", g->gids[k], pbk);
+            return SJ_ERR_UNSUPPORTED;
+        }
+        b.scale = sk;
         PackParams pp{};
-        pack_coefficients(t.eps, pb * (1.0 + ldexp(1.0, -20)), 1.01 * u_t * rmax, u_t, dp, dp, &pp, c1);
+        pack_coefficients(t.eps * sk, pbk * sk * sk, 1.01 * u_t * rmax * sk, u_t, dp, dp, &pp, c1);
         b.a_out = pp.a_out;
         b.b_out = pp.b_out;
         b.a_in = pp.a_in;

@@ -221,7 +221,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
         : "r"(taddr));
 }
 
-template <int KP, bool EMIT>
+// DBG: the recording instantiation of the filter dump (a test aid; the join
+// kernels proper carry none of its code).
+template <int KP, bool EMIT, bool DBG>
 __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams P, TcParams T) {
     using SH = TcShape<KP>;
     using SM = TcSmem<KP, EMIT>;
@@ -567,10 +569,12 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                         tmem_ld32(taddr + (uint32_t)c0, v);
                     }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (P.dbg && cvalid && has_cols) {  // the filter dump (test aid)
-                        for (int k = 0; k < 32 && c0 + k < X.ncol; ++k) {
+                    if (DBG && cvalid && has_cols) {  // the filter dump (test aid)
+                        // (constant indices: v stays in registers)
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
                             const int col = c0 + k;
-                            if ((uint32_t)(col - col_lo) <= col_span)
+                            if (col < X.ncol && (uint32_t)(col - col_lo) <= col_span)
                                 dbg_record(P, X.qa + col, cp, __uint_as_float(v[k]));
                         }
                     }
@@ -693,9 +697,9 @@ int selftest_bounded_wait(cudaStream_t s) {
     return SJ_ERR_CUDA;
 }
 
-template <int KP, bool EMIT>
+template <int KP, bool EMIT, bool DBG = false>
 static int launch_kp(Index* ix, const JoinParams& p, const TcParams& t) {
-    auto kern = k_join_tc<KP, EMIT>;
+    auto kern = k_join_tc<KP, EMIT, DBG>;
     const size_t smem = tc_smem_bytes<KP, EMIT>();
     if (smem > kSmemMax) {
         set_error("tensor-core tile does not fit in shared memory (K = %d)", KP);
@@ -720,6 +724,7 @@ static int launch_kp(Index* ix, const JoinParams& p, const TcParams& t) {
 
 template <int KP>
 static int launch_k(Index* ix, const JoinParams& p, const TcParams& t) {
+    if (p.dbg) return launch_kp<KP, false, true>(ix, p, t);  // the filter dump (no distances)
     return p.emit_dist ? launch_kp<KP, true>(ix, p, t) : launch_kp<KP, false>(ix, p, t);
 }
 

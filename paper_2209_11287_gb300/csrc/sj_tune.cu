@@ -272,9 +272,9 @@ int sj_autotune(const double* pts, int64_t n, int32_t d, double eps, const sj_op
     };
     std::vector<int> kernels;
     // the automatic choice first, so slow candidates meet a good time early
-    const int auto_k = (d >= 16 && d <= 64) ? SJ_KERNEL_FILTER_BF16X2 : SJ_KERNEL_FILTER_F32;
+    const int auto_k = (d >= 16 && d <= 64) ? SJ_KERNEL_FILTER_FP16X2 : SJ_KERNEL_FILTER_F32;
     kernels.push_back(auto_k);
-    for (int k : {SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_BF16X2, SJ_KERNEL_FILTER_BF16X3})
+    for (int k : {SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_FP16X2, SJ_KERNEL_FILTER_BF16X3})
         if (k != auto_k && (!is_tensor_kernel(k) || dp <= 64)) kernels.push_back(k);
 
     int first_err = SJ_OK;

@@ -122,6 +122,21 @@ def test_candidate_counts_per_instance():
         assert st["n_candidates"] == oracle.grid_candidate_count(x, e * (1.0 + 2.0 ** -20))
 
 
+@pytest.mark.parametrize("kernel", ["filter_f32", "filter_bf16x2", "auto"])
+def test_extreme_coordinate_scales(kernel):
+    """Instances whose coordinate spread underflows (1e-30) or overflows (1e25)
+    binary32, beside an ordinary one: each instance's coordinates are scaled
+    by its own power of two, and every instance's set is the oracle's."""
+    g = np.random.Generator(np.random.PCG64(78))
+    pts, eps = [], []
+    for scale in (1e-30, 1.0, 1e25, 1e-100):
+        c = g.random((10, 8))
+        pts.append((c[g.integers(0, 10, 1500)] + 0.03 * g.standard_normal((1500, 8))) * scale)
+        eps.append(0.1 * scale)
+    out = binding.join_batch(pts, eps, kernel=kernel)
+    _check(pts, eps, out, with_dist=False)
+
+
 def test_unsupported_kernel_rejected():
     with pytest.raises(RuntimeError):
         binding.join_batch([np.random.default_rng(0).random((10, 4))], [0.1], kernel="fp64_dmma")

@@ -338,3 +338,21 @@ def test_join_to_host_in_rounds(kernel):
         assert np.all(np.isin(part, ref)) and np.unique(part).size == 1000
     finally:
         binding.sj_destroy(h)
+
+
+@pytest.mark.parametrize("kernel", KERNELS + ["auto"])
+@pytest.mark.parametrize("scale", [1e-100, 1e-30, 1e25, 1e100], ids=lambda s: f"{s:g}")
+def test_extreme_coordinate_scales(kernel, scale):
+    """Coordinates whose spread underflows binary32 (1e-30: squared
+    distances near 1e-60) or overflows it (1e25: squares near 1e50), and far
+    beyond (1e-100, 1e100): the binary32 filters scale their coordinates by a
+    power of two into range, so every kernel returns the oracle's set."""
+    g = np.random.Generator(np.random.PCG64(77))
+    d = 16 if kernel in ("filter_bf16x3", "filter_bf16x2", "filter_fp16x2", "auto") else 3
+    centres = g.random((20, d))
+    x = (centres[g.integers(0, 20, 3000)] + 0.03 * g.standard_normal((3000, d))) * scale
+    eps = (0.15 if d == 16 else 0.05) * scale
+    ref = oracle.join(x, eps)
+    assert ref.size > 30 * 3000  # about 45 neighbours a point
+    got, _, _ = gpu_join(x, eps, kernel)
+    assert_same_set(x, eps, ref, got)

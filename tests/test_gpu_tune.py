@@ -26,7 +26,8 @@ def _keys(pairs):
     return binding.pairs_to_keys(pairs) if len(pairs) else np.zeros(0, dtype=np.int64)
 
 
-TUNABLE = {binding.SJ_KERNEL_FILTER_F32, binding.SJ_KERNEL_FILTER_BF16X2, binding.SJ_KERNEL_FILTER_BF16X3}
+TUNABLE = {binding.SJ_KERNEL_FILTER_F32, binding.SJ_KERNEL_FILTER_BF16X2, binding.SJ_KERNEL_FILTER_FP16X2,
+           binding.SJ_KERNEL_FILTER_BF16X3}
 
 
 @pytest.mark.parametrize("make", [lambda: workloads.uniform4d(n=20000, seed=5),
