@@ -526,9 +526,14 @@ __global__ void __launch_bounds__(tc_threads(KP, EMIT), 1) k_join_tc(JoinParams 
                 __syncwarp();
                 if (lane == 0) bar_arrive(&S.meta_empty[m_i]);
                 if (++m_i == kMetaDepth) m_i = 0, m_ph ^= 1u;
-                to = valid ? TO[p] : INFINITY;
-                ti = valid ? TI[p] : INFINITY;
-                pid = valid ? P.perm[p] : 0;
+                // unconditional loads from an in-bounds row (selecting the
+                // loaded values here would wait for them; every use below
+                // is guarded by `valid`), so their latency overlaps the
+                // current tile's chunks
+                const int32_t pl = valid ? p : 0;
+                to = TO[pl];
+                ti = TI[pl];
+                pid = P.perm[pl];
                 return true;
             };
             if (X.ntiles > 0 && !read_meta()) fail = true;
