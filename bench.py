@@ -46,8 +46,8 @@ KERNEL_NAMES = {"filter_f32": "k_join_f32s (d <= 8) | k_join_cc<float>", "fp64_f
                 "filter_bf16x3": "k_join_tc", "filter_bf16x2": "k_join_tc", "filter_fp16x2": "k_join_tc"}
 DTYPES = {"auto": "fp16x2|bf16x2|f32+f64", "filter_f32": "f32+f64", "filter_bf16x3": "bf16x3+f64",
           "filter_bf16x2": "bf16x2+f64", "filter_fp16x2": "fp16x2+f64", "fp64_fma": "f64",
-          "fp64_dmma": "f64", "fp64_fma_sc": "f64", "tuned": "fp16x2|bf16x2|bf16x3|f32+f64", "tuned_graph": "bf16x2|bf16x3|f32+f64",
-          "auto_graph": "bf16x2|f32+f64"}
+          "fp64_dmma": "f64", "fp64_fma_sc": "f64", "tuned": "fp16x2|bf16x2|bf16x3|f32+f64", "tuned_graph": "fp16x2|bf16x2|bf16x3|f32+f64",
+          "auto_graph": "fp16x2|bf16x2|f32+f64"}
 
 
 def parse():
@@ -652,7 +652,7 @@ def run_batched(args):
     # variants: a kernel name; "tuned" = AUTO with the tuning cache the
     # autotuner writes before the variant's warm-up (untimed); "*_graph" = the
     # join phase as one CUDA graph
-    allowed = ("tuned_graph", "tuned", "auto_graph", "auto", "filter_f32", "filter_bf16x3", "filter_bf16x2",
+    allowed = ("tuned_graph", "tuned", "auto_graph", "auto", "filter_f32", "filter_bf16x3", "filter_bf16x2", "filter_fp16x2",
                "fp64_fma")
     asked = (args.variants.split(",") if args.variants != ",".join(VARIANTS)
              else ["tuned_graph", "tuned", "auto", "filter_f32", "fp64_fma"])
@@ -797,7 +797,7 @@ def batch_rooflines(r):
     out = {}
     for dp, g in sorted(r["groups"].items()):
         sec = max(g["ms"], 1e-6) * 1e-3
-        if g["kernel"] in ("filter_bf16x3", "filter_bf16x2"):
+        if g["kernel"] in ("filter_bf16x3", "filter_bf16x2", "filter_fp16x2"):
             kp = ((6 if g["kernel"] == "filter_bf16x3" else 3) * dp + 3 + 15) // 16 * 16
             flops, peak, kern = 2.0 * kp * g["evaluated"], bf16, "k_join_tc<" + g["kernel"][7:] + ">"
             bound = "tensor"

@@ -67,7 +67,7 @@ extern "C" {
 
 /* ---- distance kernels -------------------------------------------------- */
 #define SJ_KERNEL_AUTO 0        /* single joins: SJ_KERNEL_FILTER_FP16X2 for
-                                   16 <= d <= 64, else SJ_KERNEL_FILTER_F32
+                                   9 <= d <= 64, else SJ_KERNEL_FILTER_F32
                                    (SJ_KERNEL_FP64_FMA for an extent that
                                    scaled binary32 coordinates cannot hold)
                                    (batched joins: see sj_join_batch) */
@@ -93,7 +93,7 @@ extern "C" {
                                      bits each) of the kernel coordinates
                                      scaled by a power of two into fp16's
                                      range: the same K, a narrower certified
-                                     band; single joins, d <= 64 */
+                                     band; d <= 64 */
 
 /* ---- options ----------------------------------------------------------- */
 #define SJ_NO_INDEX (-1)        /* sj_options.indexed_dims: brute force */
@@ -311,10 +311,10 @@ SJ_API int sj_selftest_bounded_wait(void* stream);
  * group's index is built by segmented kernels over composite cell keys
  * (instance << S | cell key of the instance's own grid, Sec. III-A) and all
  * of the group's work items run in one persistent distance-tile launch
- * (kernels SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_BF16X3 / _BF16X2 (padded
- * d <= 64) or SJ_KERNEL_FP64_FMA; AUTO takes SJ_KERNEL_FILTER_BF16X2 for
+ * (kernels SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_BF16X3 / _BF16X2 / _FP16X2
+ * (padded d <= 64) or SJ_KERNEL_FP64_FMA; AUTO takes SJ_KERNEL_FILTER_FP16X2 for
  * groups of padded dimension 8 .. 64 and the FP32 filter for the others;
- * SJ_KERNEL_FP64_DMMA and SJ_KERNEL_FILTER_FP16X2 give SJ_ERR_UNSUPPORTED).  Pairs carry instance-local indices and
+ * SJ_KERNEL_FP64_DMMA gives SJ_ERR_UNSUPPORTED).  Pairs carry instance-local indices and
  * satisfy the same decision rule as sj_self_join.  The device takes each
  * instance's result pages from one shared pool (opt->page_pairs rounded up
  * to a power of two of at least 64, default 65536 pairs a page); when the
@@ -373,7 +373,7 @@ SJ_API int sj_autotune(const double* pts, int64_t n, int32_t d, double eps, cons
 /*
  * Tunes a batched join (arguments as for sj_join_batch) per group of padded
  * dimension.  Candidates, each applied to every group it supports: FILTER_F32
- * with 16 and 8 queries per item; FILTER_BF16X2 with its maximum, half and a
+ * with 16 and 8 queries per item; FILTER_FP16X2 with its maximum, half and a
  * quarter; FILTER_BF16X3 with its maximum (tensor-core candidates only for
  * padded d <= 64).  Each candidate runs the whole batch once untimed and
  * `reps` times timed (reps < 1 means 2); a group's time for a candidate is the

@@ -183,9 +183,12 @@ static void release_index(Index* ix) {
 }
 
 // AUTO: the certified filters always beat the plain FP64 kernels on this part
-// (FP64 runs at ~1/60 of FP32); the tensor-core filter wins once the dot
-// product is long enough to amortise its tiles (measured: d = 64 12x and
-// d = 16 1.3x faster than the FP32 filter), the FP32 CUDA-core filter below.
+// (FP64 runs at ~1/60 of FP32); the tensor-core filter wins from padded
+// dimension 16 on (measured, 1M points, step times FP32 filter / FP16x2:
+// d = 12 clustered 37.1 / 19.4 ms, uniform 1128 / 109 ms; d = 16 clustered
+// 39.6 / 19.1 ms), the FP32 CUDA-core filter below (d = 6: 7.1 / 33.8 ms
+// clustered; d = 8 depends on the data: clustered 10.3 / 22.2, uniform
+// 36.5 / 14.9 ms).
 // Of the tensor-core filters FP16x2 (the K of BF16x2, a narrower band: fewer
 // binary64 rechecks) is never slower (measured on the 16-D and 64-D
 // workloads).  (build_index turns AUTO into the FP64 tile for an extent that
@@ -193,7 +196,7 @@ static void release_index(Index* ix) {
 static int pick_kernel(const Index* ix) {
     int k = ix->opt.kernel;
     if (k != SJ_KERNEL_AUTO) return k;
-    return (ix->d >= 16 && ix->d <= 64) ? SJ_KERNEL_FILTER_FP16X2 : SJ_KERNEL_FILTER_F32;
+    return (ix->d >= 9 && ix->d <= 64) ? SJ_KERNEL_FILTER_FP16X2 : SJ_KERNEL_FILTER_F32;
 }
 
 int round_dim(int d) {
@@ -1005,14 +1008,17 @@ int join_batch_impl(const double* const* pts, const int64_t* n, const int32_t* d
     sj_default_options(&o);
     if (opt) o = *opt;
     if (o.kernel != SJ_KERNEL_AUTO && o.kernel != SJ_KERNEL_FILTER_F32 && o.kernel != SJ_KERNEL_FP64_FMA &&
-        o.kernel != SJ_KERNEL_FILTER_BF16X3 && o.kernel != SJ_KERNEL_FILTER_BF16X2) {
+        o.kernel != SJ_KERNEL_FILTER_BF16X3 && o.kernel != SJ_KERNEL_FILTER_BF16X2 &&
+        o.kernel != SJ_KERNEL_FILTER_FP16X2) {
         set_error("batched joins run the FP32 filter, the tensor-core filter or the FP64 CUDA-core kernel (got "
                   "kernel %d)", o.kernel);
         return SJ_ERR_UNSUPPORTED;
     }
-    // AUTO: the tensor-core filter for padded dimensions 8 .. 64 (measured on
-    // uniform instances with the batched grid choice: d 8 1.7x, d 16 4x, d 32
-    // 12x faster than the FP32 filter), else the FP32 CUDA-core filter
+    // AUTO: the tensor-core filter (FP16x2: each instance's coordinates are
+    // scaled by its own power of two) for padded dimensions 8 .. 64
+    // (measured on uniform instances with the batched grid choice: d 8 1.7x,
+    // d 16 4x, d 32 12x faster than the FP32 filter), else the FP32 CUDA-core
+    // filter
     std::vector<TuneEntry> tuned;
     if (o.kernel == SJ_KERNEL_AUTO && o.tune_cache && o.tune_cache[0]) {
         const int ts = tune_load(o.tune_cache, &tuned);
@@ -1023,16 +1029,14 @@ int join_batch_impl(const double* const* pts, const int64_t* n, const int32_t* d
     auto group_entry = [&](int dp) -> const TuneEntry* {
         const TuneEntry* e = forced ? tune_find_group(*forced, dp) : nullptr;
         if (!e && !tuned.empty()) e = tune_find_group(tuned, dp);
-        if (!e || e->kernel == SJ_KERNEL_AUTO || e->kernel == SJ_KERNEL_FP64_DMMA ||
-            e->kernel == SJ_KERNEL_FILTER_FP16X2)
-            return nullptr;
+        if (!e || e->kernel == SJ_KERNEL_AUTO || e->kernel == SJ_KERNEL_FP64_DMMA) return nullptr;
         if (is_tensor_kernel(e->kernel) && dp > 64) return nullptr;
         return e;
     };
     auto group_kernel = [&](int dp) {
         if (const TuneEntry* e = group_entry(dp)) return e->kernel;
         if (o.kernel != SJ_KERNEL_AUTO) return o.kernel;
-        return (dp >= 8 && dp <= 64) ? SJ_KERNEL_FILTER_BF16X2 : SJ_KERNEL_FILTER_F32;
+        return (dp >= 8 && dp <= 64) ? SJ_KERNEL_FILTER_FP16X2 : SJ_KERNEL_FILTER_F32;
     };
     for (int32_t k = 0; k < count; ++k)
         if (is_tensor_kernel(group_kernel(round_dim(d[k]))) && round_dim(d[k]) > 64) {

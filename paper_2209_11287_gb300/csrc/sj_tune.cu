@@ -272,7 +272,7 @@ int sj_autotune(const double* pts, int64_t n, int32_t d, double eps, const sj_op
     };
     std::vector<int> kernels;
     // the automatic choice first, so slow candidates meet a good time early
-    const int auto_k = (d >= 16 && d <= 64) ? SJ_KERNEL_FILTER_FP16X2 : SJ_KERNEL_FILTER_F32;
+    const int auto_k = (d >= 9 && d <= 64) ? SJ_KERNEL_FILTER_FP16X2 : SJ_KERNEL_FILTER_F32;
     kernels.push_back(auto_k);
     for (int k : {SJ_KERNEL_FILTER_F32, SJ_KERNEL_FILTER_FP16X2, SJ_KERNEL_FILTER_BF16X3})
         if (k != auto_k && (!is_tensor_kernel(k) || dp <= 64)) kernels.push_back(k);
@@ -383,8 +383,8 @@ int sj_autotune_batch(const double* const* pts, const int64_t* n, const int32_t*
     struct Cand {
         int kernel, div;  // div: queries per item = capacity / div (1: the capacity, written as 0)
     };
-    const Cand cands[] = {{SJ_KERNEL_FILTER_BF16X2, 1}, {SJ_KERNEL_FILTER_F32, 1}, {SJ_KERNEL_FILTER_F32, 2},
-                          {SJ_KERNEL_FILTER_BF16X2, 2}, {SJ_KERNEL_FILTER_BF16X2, 4}, {SJ_KERNEL_FILTER_BF16X3, 1}};
+    const Cand cands[] = {{SJ_KERNEL_FILTER_FP16X2, 1}, {SJ_KERNEL_FILTER_F32, 1}, {SJ_KERNEL_FILTER_F32, 2},
+                          {SJ_KERNEL_FILTER_FP16X2, 2}, {SJ_KERNEL_FILTER_FP16X2, 4}, {SJ_KERNEL_FILTER_BF16X3, 1}};
     std::vector<double> best(G, 0.0);
     std::vector<int> best_k(G, SJ_KERNEL_AUTO), best_q(G, 0);
     std::vector<bool> have(G, false);

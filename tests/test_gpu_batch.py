@@ -77,7 +77,8 @@ def _check(pts, eps, out, with_dist):
             assert np.array_equal(dists[order], rd), f"instance {k}: distances differ"
 
 
-@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3", "filter_bf16x2", "auto"])
+@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3", "filter_bf16x2", "filter_fp16x2",
+                                    "auto"])
 @pytest.mark.parametrize("symmetric", [1, 0])
 def test_mixed_batch(kernel, symmetric):
     pts, eps = _mixed_batch()
@@ -93,7 +94,7 @@ def test_mixed_batch_indexed_dims(indexed_dims):
     _check(pts, eps, out, with_dist=False)
 
 
-@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3", "filter_bf16x2"])
+@pytest.mark.parametrize("kernel", ["filter_f32", "fp64_fma", "filter_bf16x3", "filter_bf16x2", "filter_fp16x2"])
 def test_mixed_batch_distances_host_input(kernel):
     pts, eps = _mixed_batch(seed=1)
     out = binding.join_batch(pts, eps, kernel=kernel, emit_distances=True)
@@ -122,7 +123,7 @@ def test_candidate_counts_per_instance():
         assert st["n_candidates"] == oracle.grid_candidate_count(x, e * (1.0 + 2.0 ** -20))
 
 
-@pytest.mark.parametrize("kernel", ["filter_f32", "filter_bf16x2", "auto"])
+@pytest.mark.parametrize("kernel", ["filter_f32", "filter_bf16x2", "filter_fp16x2", "auto"])
 def test_extreme_coordinate_scales(kernel):
     """Instances whose coordinate spread underflows (1e-30) or overflows (1e25)
     binary32, beside an ordinary one: each instance's coordinates are scaled
@@ -142,8 +143,6 @@ def test_unsupported_kernel_rejected():
         binding.join_batch([np.random.default_rng(0).random((10, 4))], [0.1], kernel="fp64_dmma")
     with pytest.raises(RuntimeError):  # the tensor-core filter stops at d = 64
         binding.join_batch([np.random.default_rng(0).random((10, 65))], [0.1], kernel="filter_bf16x3")
-    with pytest.raises(RuntimeError):  # the FP16x2 filter serves single joins
-        binding.join_batch([np.random.default_rng(0).random((10, 16))], [0.1], kernel="filter_fp16x2")
 
 
 def test_bad_instance_rejected():
