@@ -98,6 +98,26 @@ def shard_of(item_work, rank: int, world: int):
     return int(b[rank]), int(b[rank + 1])
 
 
+def instance_shard(sizes, rank: int, world: int):
+    """The contiguous range of batch instances rank `rank` joins: shards of
+    about equal sum of n_i^2 (the grid-independent work of an instance), by
+    the library's host-side partition, the same on every rank."""
+    import numpy as np
+    return shard_of(np.asarray(sizes, dtype=np.int64) ** 2, rank, world)
+
+
+def gather_sums(values, world: int, dev) -> list:
+    """Element-wise sums over the ranks of a few int64 values (counts of a
+    sharded batch), on every rank."""
+    if world == 1:
+        return [int(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([int(v) for v in values], dtype=torch.int64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [int(v) for v in t.tolist()]
+
+
 def gather_counts(count: int, world: int, dev) -> list:
     """Every rank's result count (int64), gathered on every rank: the one
     exchange of a sharded join (|R| is their sum)."""
@@ -592,9 +612,12 @@ def run_batched(args):
     step."""
     from paper_2209_11287_gb300 import workloads
     rank, world, local = dist_env()
-    insts = [workloads.batch_instance(i) for i in range(args.batch_count)]
-    total_n = sum(w.n for w in insts)
-    eps = [w.eps for w in insts]
+    sizes = [workloads.batch_instance_params(i)[0] for i in range(args.batch_count)]
+    total_n = sum(sizes)
+    nsq = float(sum(n * n for n in sizes))  # the grid-independent unit of work of the whole batch
+    # several ranks: each joins a contiguous range of instances of about equal
+    # sum of n^2 (the batch shards by instance, no data-path exchange)
+    i0, i1 = (0, args.batch_count) if world == 1 else instance_shard(sizes, rank, world)
     if args.impl == "reference":
         if rank != 0:
             return
@@ -611,6 +634,8 @@ def run_batched(args):
     torch.cuda.set_device(local)
     build.build()
     binding.load()
+    insts = [workloads.batch_instance(i) for i in range(i0, i1)]
+    eps = [w.eps for w in insts]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     pts = [torch.from_numpy(w.points).to(dev) for w in insts]
@@ -694,13 +719,18 @@ def run_batched(args):
         launches = (binding.sj_kernel_launches() - l0) // args.steps
         clocks = sampler.stop() if vi == len(variants) - 1 else None
         times = [a.elapsed_time(b) for a, b in ev]
-        results[kname] = {"ms_per_step": statistics.mean(times), "count": info[0], "n_candidates": info[1],
-                          "n_evaluated": info[2], "reruns": info[3], "tile_ms": statistics.mean(tiles),
-                          "groups": info[5], "max_count": info[6], "launches": launches, "clocks": clocks}
+        # the whole batch: the slowest rank's time, the sums of the ranks' counts
+        count, n_cand, n_eval = gather_sums(info[:3], world, dev)
+        results[kname] = {"ms_per_step": max_over_ranks(statistics.mean(times), world, dev), "count": count,
+                          "n_candidates": n_cand, "n_evaluated": n_eval, "reruns": info[3],
+                          "tile_ms": max_over_ranks(statistics.mean(tiles), world, dev),
+                          "groups": info[5], "max_count": info[6], "launches": launches, "clocks": clocks,
+                          "local_count": info[0]}
     head = results[variants[0]]
     # end to end: host inputs (pinned), every instance's pairs copied back to pinned host memory
     host_pts = binding.BatchInputs([torch.from_numpy(w.points).pin_memory() for w in insts], eps)
     host_out = torch.empty((head["max_count"] + 16, 2), dtype=torch.int32).pin_memory()
+    sync_all()
     opt = make_opt(variants[0])
     t_e2e = []
     for k in range(max(2, min(args.steps, 4))):
@@ -710,7 +740,7 @@ def run_batched(args):
         one_step(opt, host_pts, host_out)
         torch.cuda.synchronize(dev)
         t_e2e.append(time.perf_counter() - t0)
-    e2e_s = statistics.mean(t_e2e)
+    e2e_s = max_over_ranks(statistics.mean(t_e2e), world, dev)
     shutil.rmtree(tune_dir, ignore_errors=True)
     if rank != 0:
         return
@@ -718,20 +748,20 @@ def run_batched(args):
     for k in variants:
         r = results[k]
         var[k] = {"ms_per_step": round(r["ms_per_step"], 3),
-                  "pair_equivalents_per_s": world * float(sum(w.n * w.n for w in insts)) / (r["ms_per_step"] * 1e-3),
+                  "pair_equivalents_per_s": nsq / (r["ms_per_step"] * 1e-3),
                   "candidate_pairs": r["n_candidates"],
-                  "instances_per_s": world * len(insts) / (r["ms_per_step"] * 1e-3),
+                  "instances_per_s": args.batch_count / (r["ms_per_step"] * 1e-3),
                   "result_pairs": r["count"], "evaluated_pairs": r["n_evaluated"], "reruns": r["reruns"],
                   "tile_kernel_ms": round(r["tile_ms"], 3), "launches_per_step": r["launches"],
                   "groups": batch_rooflines(r)}
-    nsq = float(sum(w.n * w.n for w in insts))  # the grid-independent unit of work
-    line = {"metric": BATCH_METRIC, "value": world * nsq / (head["ms_per_step"] * 1e-3),
+    line = {"metric": BATCH_METRIC, "value": nsq / (head["ms_per_step"] * 1e-3),
             "unit": BATCH_UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(head["ms_per_step"], 3), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": round(head["ms_per_step"], 3), "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": DTYPES.get(variants[0], "f64"),
             "data": "synthetic",
-            "config": batch_config(len(insts), total_n, {"kernel": variants[0], "symmetric": 1,
-                                                          "parallelism": f"replicas x{world}",
+            "config": batch_config(args.batch_count, total_n, {"kernel": variants[0], "symmetric": 1,
+                                                          "parallelism": "1 GPU" if world == 1 else
+                                                          f"instance shards x{world} (equal sum of n^2)",
                                                           "l2": "inputs (4.7 GB) larger than L2; 256 MB flush too",
                                                           "candidate_pairs": head["n_candidates"],
                                                           "result_pairs": head["count"]}),
@@ -740,11 +770,12 @@ def run_batched(args):
                 "seconds": tuned["seconds"],
                 "groups": {str(g["dp"]): {"kernel": knames.get(g["kernel"], "?"), "queries_per_item": g["qpi"],
                                           "tile_ms": round(g["ms"], 3)} for g in tuned["groups"]}},
-            "e2e": {"value": world * nsq / e2e_s, "unit": BATCH_UNIT,
-                    "h2d_bytes_per_step": sum(w.n * w.d * 8 for w in insts),
+            "e2e": {"value": nsq / e2e_s, "unit": BATCH_UNIT,
+                    "h2d_bytes_per_step": sum(n * workloads.batch_instance_params(i)[1] * 8
+                                              for i, n in enumerate(sizes)),
                     "d2h_bytes_per_step": head["count"] * 8, "ms_per_step": round(e2e_s * 1e3, 1)},
             "roofline": max(batch_rooflines(head).values(), key=lambda g: g["kernel_ms"]),
-            "cpu_baseline": None if args.no_cpu_baseline else batch_cpu_baseline(insts, nsq),
+            "cpu_baseline": None if (args.no_cpu_baseline or world > 1) else batch_cpu_baseline(insts, nsq),
             "gpu_launches": int(head["launches"]),
             "clocks": results[variants[-1]]["clocks"]}
     print(json.dumps(line), flush=True)

@@ -107,3 +107,50 @@ def test_gloo_ranks_shard_the_items_and_gather_counts(world):
     for o in out:
         assert o[4] == [x[3] for x in out]
         assert sum(o[4]) == total
+
+
+def _batch_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    from paper_2209_11287_gb300 import workloads
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sizes = [workloads.batch_instance_params(i)[0] for i in range(4096)]
+    i0, i1 = bench.instance_shard(sizes, rank, world)
+    mine = sum(n * n for n in sizes[i0:i1])
+    sums = bench.gather_sums([i1 - i0, mine], world, torch.device("cpu"))
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, i0, i1, mine, sums))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_batch_shards_by_instance(world):
+    """The batched workload on several ranks: contiguous ranges of instances
+    covering the batch once, of about equal sum of n^2, the same partition on
+    every rank, and the ranks' counts summed by the one exchange."""
+    import torch.multiprocessing as mp
+    sys.path.insert(0, ROOT)
+    from paper_2209_11287_gb300 import workloads
+    sizes = [workloads.batch_instance_params(i)[0] for i in range(4096)]
+    total = sum(n * n for n in sizes)
+    biggest = max(n * n for n in sizes)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out[0][1] == 0 and out[-1][2] == 4096
+    for a, b in zip(out, out[1:]):
+        assert a[2] == b[1]  # contiguous, disjoint
+    for o in out:
+        assert abs(o[3] - total / world) <= biggest  # balanced to within one instance
+        assert o[4] == [4096, total]  # every rank holds the sums
