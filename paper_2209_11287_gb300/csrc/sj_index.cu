@@ -102,8 +102,8 @@ struct GridParams {
 // grid.  (1 / w is rounded once; the relative margin of w over eps absorbs
 // the three roundings, see choose_grid.)
 __device__ __forceinline__ int64_t cell_coord(double v, double lo, double inv_w, int64_t ncell) {
-    double t = floor(__dmul_rn(__dsub_rn(v, lo), inv_w));
-    int64_t c = (int64_t)t;
+    // floor and conversion in one instruction (binary64 work is scarce here)
+    const int64_t c = __double2ll_rd(__dmul_rn(__dsub_rn(v, lo), inv_w));
     return c < 0 ? 0 : (c >= ncell ? ncell - 1 : c);
 }
 
@@ -1169,26 +1169,33 @@ __device__ __forceinline__ int64_t split_at(int64_t p, int k, int kp, int64_t nr
 // are).  H: the term type (bf16, or fp16 for FP16x2).  The three h slots hold
 // hs in the candidate row and the split of h / hs in the query row (hs a
 // power of two: 1 for bf16, 2^15 for fp16, whose range stops at 65504).
-template <typename H>
-__global__ void k_pack_split(const float* __restrict__ y, const float* __restrict__ h, int64_t n, int dp, int kp,
-                             int prod, int64_t nrows, float hs, H* rows_a, H* rows_b) {
+template <typename H, int PROD, int KP>
+__global__ void k_pack_split(const float* __restrict__ y, const float* __restrict__ h, int64_t n, int dp,
+                             int64_t nrows, float hs, H* rows_a, H* rows_b) {
+    constexpr int CH = KP / 8;  // 16-byte chunks per row (compile-time: no run-time division)
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int ch = kp >> 3;
-    const int64_t grp = t / (8 * ch);
-    const int c = (int)((t >> 3) % ch);
+    const int64_t grp = t / (8 * CH);
+    const int c = (int)((t >> 3) % CH);
     const int64_t p = grp * 8 + (t & 7);
-    if (p >= n) return;  // padding rows stay zero
+    if (p >= nrows) return;
+    const bool live = p < n;  // padding rows (p >= n) are written as zeros
     const H zero = to_term(0.f, H()), hterm = to_term(hs, H());
     __align__(16) H av[8], bv[8];
+    int last = -1;  // the coordinate whose split t1 .. t3 hold
+    H t1 = zero, t2 = zero, t3 = zero;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int k = c * 8 + u;
         H a = zero, b = zero;
-        if (k < prod * dp) {
-            H t1, t2, t3;
-            split3(y[p * dp + k / prod], t1, t2, t3);
-            if (prod == 6) {
-                switch (k % 6) {  // candidate (c1, c2, c1, c3, c2, c1), query (q1, q1, q2, q1, q2, q3)
+        if (!live) {
+        } else if (k < PROD * dp) {
+            const int j = k / PROD, r = k - j * PROD;
+            if (j != last) {  // each coordinate split once per thread
+                split3(y[p * dp + j], t1, t2, t3);
+                last = j;
+            }
+            if (PROD == 6) {
+                switch (r) {  // candidate (c1, c2, c1, c3, c2, c1), query (q1, q1, q2, q1, q2, q3)
                     case 0: a = t1; b = t1; break;
                     case 1: a = t2; b = t1; break;
                     case 2: a = t1; b = t2; break;
@@ -1197,24 +1204,48 @@ __global__ void k_pack_split(const float* __restrict__ y, const float* __restric
                     default: a = t1; b = t3; break;
                 }
             } else {
-                switch (k % 3) {  // candidate (c1, c2, c1), query (q1, q1, q2)
+                switch (r) {  // candidate (c1, c2, c1), query (q1, q1, q2)
                     case 0: a = t1; b = t1; break;
                     case 1: a = t2; b = t1; break;
                     default: a = t1; b = t2; break;
                 }
             }
-        } else if (k < prod * dp + 3) {
+        } else if (k < PROD * dp + 3) {
             H h1, h2, h3;
             split3(h[p] / hs, h1, h2, h3);  // (exact: hs is a power of two)
             a = hterm;
-            b = k == prod * dp ? h1 : (k == prod * dp + 1 ? h2 : h3);
+            b = k == PROD * dp ? h1 : (k == PROD * dp + 1 ? h2 : h3);
         }
         av[u] = a;
         bv[u] = b;
     }
-    const int64_t o = split_at(p, c * 8, kp, nrows);
+    const int64_t o = split_at(p, c * 8, KP, nrows);
     *reinterpret_cast<uint4*>(rows_a + o) = *reinterpret_cast<const uint4*>(av);
     *reinterpret_cast<uint4*>(rows_b + o) = *reinterpret_cast<const uint4*>(bv);
+}
+
+template <typename H, int PROD, int KP>
+static void launch_pack_split(const Index* ix, int64_t nrows, float hs, void* ra, void* rb, cudaStream_t s) {
+    const int64_t threads = nrows * (KP / 8);
+    k_pack_split<H, PROD, KP><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        static_cast<const float*>(ix->y), static_cast<const float*>(ix->h), ix->n, ix->dp, nrows, hs,
+        static_cast<H*>(ra), static_cast<H*>(rb));
+}
+
+template <typename H, int PROD>
+static int launch_pack_split_k(const Index* ix, int64_t nrows, float hs, void* ra, void* rb, cudaStream_t s) {
+    switch (ix->kp) {
+        case 16: launch_pack_split<H, PROD, 16>(ix, nrows, hs, ra, rb, s); break;
+        case 32: launch_pack_split<H, PROD, 32>(ix, nrows, hs, ra, rb, s); break;
+        case 64: launch_pack_split<H, PROD, 64>(ix, nrows, hs, ra, rb, s); break;
+        case 112: launch_pack_split<H, PROD, 112>(ix, nrows, hs, ra, rb, s); break;
+        case 208: launch_pack_split<H, PROD, 208>(ix, nrows, hs, ra, rb, s); break;
+        case 400: launch_pack_split<H, PROD, 400>(ix, nrows, hs, ra, rb, s); break;
+        default:
+            set_error("no split-row packing for K = %d", ix->kp);
+            return SJ_ERR_UNSUPPORTED;
+    }
+    return SJ_OK;
 }
 
 static int pack_split_rows(Index* ix) {
@@ -1228,20 +1259,13 @@ static int pack_split_rows(Index* ix) {
     ix->rows_a = ra;
     SJ_TRY(dev_alloc_t(&rb, elems, s));
     ix->rows_b = rb;
-    SJ_CK(cudaMemsetAsync(ra, 0, elems * sizeof(uint16_t), s));
-    SJ_CK(cudaMemsetAsync(rb, 0, elems * sizeof(uint16_t), s));
-    const int64_t threads = ((n + 7) / 8) * 8 * (ix->kp / 8);
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
-    const float* y = static_cast<const float*>(ix->y);
-    const float* hn = static_cast<const float*>(ix->h);
+    // every slot of every row is written (padding rows as zeros): no memset
     if (ix->kernel == SJ_KERNEL_FILTER_FP16X2)
-        k_pack_split<__half><<<blocks, 256, 0, s>>>(y, hn, n, ix->dp, ix->kp, tc_products(ix->kernel), nrows,
-                                                    32768.f, reinterpret_cast<__half*>(ra),
-                                                    reinterpret_cast<__half*>(rb));
+        SJ_TRY((launch_pack_split_k<__half, 3>(ix, nrows, 32768.f, ra, rb, s)));
+    else if (tc_products(ix->kernel) == 3)
+        SJ_TRY((launch_pack_split_k<__nv_bfloat16, 3>(ix, nrows, 1.f, ra, rb, s)));
     else
-        k_pack_split<__nv_bfloat16><<<blocks, 256, 0, s>>>(y, hn, n, ix->dp, ix->kp, tc_products(ix->kernel), nrows,
-                                                           1.f, reinterpret_cast<__nv_bfloat16*>(ra),
-                                                           reinterpret_cast<__nv_bfloat16*>(rb));
+        SJ_TRY((launch_pack_split_k<__nv_bfloat16, 6>(ix, nrows, 1.f, ra, rb, s)));
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
