@@ -93,6 +93,30 @@ static int pool_for(int dev, cudaMemPool_t* out) {
 static std::atomic<long long> g_fail_after{-1};
 static std::atomic<long long> g_live_blocks{0};
 
+void* host_staging(size_t bytes) {
+    struct Buf {
+        void* p = nullptr;
+        size_t n = 0;
+        ~Buf() {
+            if (p) cudaFreeHost(p);
+        }
+    };
+    thread_local Buf b;
+    if (b.n < bytes) {
+        if (b.p) cudaFreeHost(b.p);
+        b.p = nullptr;
+        b.n = 0;
+        const size_t want = bytes < 4096 ? 4096 : bytes;
+        if (cudaMallocHost(&b.p, want) != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return nullptr;
+        }
+        b.n = want;
+    }
+    return b.p;
+}
+
 int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (g_fail_after.load(std::memory_order_relaxed) >= 0 &&
@@ -383,21 +407,39 @@ int sj_index_info(sj_handle h, int64_t* n_cells, int64_t* n_items, int32_t* m, i
 
 // The page pool is one allocation sliced into pages (one pool call per join
 // instead of one per page); growing it replaces the allocation.
+// The pool of a single join's result: one block of pages_needed pages (the
+// page tables are filled after the join, with the pages that hold pairs).
 static int alloc_pages(ResultImpl* ri, int64_t pages_needed, int64_t page_pairs, bool dist, cudaStream_t s) {
-    if ((int64_t)ri->pair_pages.size() >= pages_needed) return SJ_OK;
+    if (ri->pages_alloc >= pages_needed) return SJ_OK;
     dev_free(ri->block, s);
     dev_free(ri->dblock, s);
     ri->block = nullptr;
     ri->dblock = nullptr;
-    ri->pair_pages.clear();
-    ri->dist_pages.clear();
+    ri->pages_alloc = 0;
     SJ_TRY(dev_alloc_t(&ri->block, (size_t)pages_needed * page_pairs * 2, s));
     if (dist) SJ_TRY(dev_alloc_t(&ri->dblock, (size_t)pages_needed * page_pairs, s));
-    for (int64_t p = 0; p < pages_needed; ++p) {
-        ri->pair_pages.push_back(ri->block + p * page_pairs * 2);
-        if (dist) ri->dist_pages.push_back(ri->dblock + p * page_pairs);
-    }
+    ri->pages_alloc = pages_needed;
     return SJ_OK;
+}
+
+// Free device memory of `dev`, queried at most every 64 calls (a query
+// costs ~10 us on the join's critical path); `fresh` forces a query.
+static size_t free_memory(int dev, bool fresh) {
+    static std::mutex mu;
+    static size_t cached[64] = {};
+    static int age[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    const int i = dev & 63;
+    if (fresh || cached[i] == 0 || ++age[i] >= 64) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            fr = 0;
+        }
+        cached[i] = fr;
+        age[i] = 0;
+    }
+    return cached[i];
 }
 
 // The page pool shared by the results of one batched join, freed with the
@@ -423,7 +465,7 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
                     unsigned long long* rechecked_out, int4* dbg = nullptr, unsigned long long dbg_cap = 0,
                     unsigned long long* dbg_count = nullptr, int64_t item_begin = 0, int64_t item_end = -1) {
     cudaStream_t s = ix->stream;
-    const int64_t np = (int64_t)ri->pair_pages.size();
+    const int64_t np = ri->pages_alloc;
     SJ_CK(cudaMemsetAsync(ix->counters, 0, kCounters * sizeof(unsigned long long), s));
     const int64_t all_items = ix->n_items;
     if (item_end < 0 || item_end > all_items) item_end = all_items;
@@ -468,8 +510,11 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
     }
     unsigned long long c[kCounters] = {};
     if (st == SJ_OK) {
-        cudaError_t e = cudaMemcpyAsync(c, ix->counters, sizeof c, cudaMemcpyDeviceToHost, s);
+        tmp.release();  // (stream-ordered: after the kernels that use the queue)
+        void* hs = host_staging(sizeof c);  // pinned: a direct copy
+        cudaError_t e = cudaMemcpyAsync(hs ? hs : c, ix->counters, sizeof c, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && hs) memcpy(c, hs, sizeof c);
         if (e != cudaSuccess) {
             set_error("join: %s", cudaGetErrorString(e));
             st = SJ_ERR_CUDA;
@@ -647,23 +692,28 @@ static int self_join_impl(sj_handle h, int64_t item_begin, int64_t item_end, sj_
     // initial pool: the hint, else the candidate count capped by a share of
     // free memory (the result never exceeds the candidate count)
     int64_t want = h->opt.max_pairs_hint;
-    if (want <= 0) {
-        size_t fr = 0, tot = 0;
-        cudaMemGetInfo(&fr, &tot);
+    const bool from_free = want <= 0;
+    auto budget_pairs = [&](bool fresh) {
         const int64_t per_pair = dist ? 16 : 8;
-        const int64_t budget = (int64_t)(fr / 4) / per_pair;
-        want = std::min<int64_t>(h->n_candidates, std::max<int64_t>(budget, 16 * h->n));
-    }
+        const int64_t budget = (int64_t)(free_memory(h->device, fresh) / 4) / per_pair;
+        return std::min<int64_t>(h->n_candidates, std::max<int64_t>(budget, 16 * h->n));
+    };
+    if (from_free) want = budget_pairs(false);
     ResultImpl* ri = new (std::nothrow) ResultImpl();
     if (!ri) return SJ_ERR_OOM;
     ri->stream = h->stream;
     int64_t np = (want + page_pairs - 1) / page_pairs;
     if (np < 1) np = 1;
     int st = alloc_pages(ri, np, page_pairs, dist, h->stream);
+    if (st == SJ_ERR_OOM && from_free) {  // the remembered free memory was stale: ask again
+        np = std::max<int64_t>(1, (budget_pairs(true) + page_pairs - 1) / page_pairs);
+        clear_error();
+        st = alloc_pages(ri, np, page_pairs, dist, h->stream);
+    }
     unsigned long long count = 0, rechecked = 0;
     int reruns = 0;
     if (st == SJ_OK) st = run_join(h, ri, page_pairs, dist, &count, &rechecked, nullptr, 0, nullptr, item_begin, item_end);
-    if (st == SJ_OK && count > (unsigned long long)ri->pair_pages.size() * (unsigned long long)page_pairs) {
+    if (st == SJ_OK && count > (unsigned long long)ri->pages_alloc * (unsigned long long)page_pairs) {
         // overflow: grow the pool to the exact count and run again
         int64_t need = (int64_t)((count + page_pairs - 1) / page_pairs);
         st = alloc_pages(ri, need, page_pairs, dist, h->stream);
@@ -671,7 +721,7 @@ static int self_join_impl(sj_handle h, int64_t item_begin, int64_t item_end, sj_
             reruns = 1;
             st = run_join(h, ri, page_pairs, dist, &count, &rechecked, nullptr, 0, nullptr, item_begin, item_end);
         }
-        if (st == SJ_OK && count > (unsigned long long)ri->pair_pages.size() * (unsigned long long)page_pairs) {
+        if (st == SJ_OK && count > (unsigned long long)ri->pages_alloc * (unsigned long long)page_pairs) {
             set_error("result of %llu pairs still exceeds the page pool", count);
             st = SJ_ERR_RESULT_OVERFLOW;
         }
@@ -682,9 +732,13 @@ static int self_join_impl(sj_handle h, int64_t item_begin, int64_t item_end, sj_
     }
     // report only the pages that hold pairs (the allocation stays whole)
     int64_t used = (int64_t)((count + page_pairs - 1) / page_pairs);
-    used = std::min<int64_t>(used, (int64_t)ri->pair_pages.size());
+    used = std::min<int64_t>(used, ri->pages_alloc);
     ri->pair_pages.resize((size_t)used);
     if (dist) ri->dist_pages.resize((size_t)used);
+    for (int64_t p = 0; p < used; ++p) {
+        ri->pair_pages[(size_t)p] = ri->block + p * page_pairs * 2;
+        if (dist) ri->dist_pages[(size_t)p] = ri->dblock + p * page_pairs;
+    }
     out->count = (int64_t)count;
     out->page_pairs = page_pairs;
     out->n_pages = (int32_t)ri->pair_pages.size();

@@ -1368,13 +1368,9 @@ int build_index(Index* ix, const double* pts) {
     // ---- extent and finiteness check (one sync) ----
     unsigned long long* ext = nullptr;
     SJ_TRY(tmp.alloc(&ext, (size_t)2 * d + 1));
-    std::vector<unsigned long long> init(2 * d + 1);
-    for (int k = 0; k < d; ++k) {
-        init[k] = ~0ull;
-        init[d + k] = 0ull;
-    }
-    init[2 * d] = 0;
-    SJ_CK(cudaMemcpyAsync(ext, init.data(), init.size() * 8, cudaMemcpyHostToDevice, s));
+    // minima start at all ones, maxima and the non-finite flag at zero
+    SJ_CK(cudaMemsetAsync(ext, 0xFF, (size_t)d * 8, s));
+    SJ_CK(cudaMemsetAsync(ext + d, 0, (size_t)(d + 1) * 8, s));
     {
         const int64_t total = n * d;
         const int bs = 256 - (256 % d);  // a multiple of d (d <= 128)
@@ -1400,8 +1396,12 @@ int build_index(Index* ix, const double* pts) {
         SJ_CK(cudaMemcpyAsync(mom.data(), dmom, 2 * d * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     std::vector<unsigned long long> got(2 * d + 1);
-    SJ_CK(cudaMemcpyAsync(got.data(), ext, got.size() * 8, cudaMemcpyDeviceToHost, s));
-    SJ_CK(cudaStreamSynchronize(s));
+    {
+        void* hs = host_staging(got.size() * 8);  // pinned: a direct copy
+        SJ_CK(cudaMemcpyAsync(hs ? hs : got.data(), ext, got.size() * 8, cudaMemcpyDeviceToHost, s));
+        SJ_CK(cudaStreamSynchronize(s));
+        if (hs) memcpy(got.data(), hs, got.size() * 8);
+    }
     if (*reinterpret_cast<int*>(&got[2 * d]) != 0) {
         set_error("non-finite coordinate in the input points");
         return SJ_ERR_ARG;
@@ -1598,13 +1598,21 @@ int build_index(Index* ix, const double* pts) {
             note_launch();
             SJ_CK(cudaGetLastError());
         }
-        struct {
+        struct Got {
             DenseTotals t;
             unsigned long long last_off;
         } got{};
-        SJ_CK(cudaMemcpyAsync(&got.t, dtot, sizeof(DenseTotals), cudaMemcpyDeviceToHost, s));
-        SJ_CK(cudaMemcpyAsync(&got.last_off, off64 + K, 8, cudaMemcpyDeviceToHost, s));
+        // everything the join needs that does not depend on the totals is set
+        // up before waiting for them: the counters, and the release of the
+        // build's temporaries (stream-ordered, after the copies below)
+        SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
+        Got* hg = static_cast<Got*>(host_staging(sizeof(Got)));  // pinned: direct copies
+        Got* dst = hg ? hg : &got;
+        SJ_CK(cudaMemcpyAsync(&dst->t, dtot, sizeof(DenseTotals), cudaMemcpyDeviceToHost, s));
+        SJ_CK(cudaMemcpyAsync(&dst->last_off, off64 + K, 8, cudaMemcpyDeviceToHost, s));
+        tmp.release();
         SJ_CK(cudaStreamSynchronize(s));
+        if (hg) got = *hg;
         ix->n_cells = (int64_t)got.t.n_cells;
         ix->n_runs = (int64_t)got.t.n_runs;
         ix->n_items = (int64_t)(got.last_off & 0xFFFFFFFFull);
@@ -1616,7 +1624,6 @@ int build_index(Index* ix, const double* pts) {
                       (long long)(got.last_off >> 32), (long long)ix->n_runs, (long long)ix->n_items);
             return SJ_ERR_CUDA;
         }
-        SJ_TRY(dev_alloc_t(&ix->counters, kCounters, s));
         clock.mark();
         clock.finish(ix);
         return SJ_OK;

@@ -53,14 +53,24 @@ bool is_device_pointer(const void* p);
 // Device temporaries of one host routine: every block taken through it is
 // freed (stream-ordered) when it goes out of scope, on success and on every
 // error return alike.
+// A pinned host buffer of at least `bytes` for small device-to-host reads
+// (sizes, totals, counts) of the calling thread, kept for the thread's life;
+// null when pinned memory cannot be had (the caller reads into its own
+// memory then).
+void* host_staging(size_t bytes);
+
 struct Scratch {
     cudaStream_t s;
     std::vector<void*> ptrs;
     explicit Scratch(cudaStream_t st) : s(st) {}
     Scratch(const Scratch&) = delete;
     Scratch& operator=(const Scratch&) = delete;
-    ~Scratch() {
+    ~Scratch() { release(); }
+    // frees every temporary now (stream-ordered: after the work already
+    // enqueued on s that uses them)
+    void release() {
         for (void* p : ptrs) dev_free(p, s);
+        ptrs.clear();
     }
     template <typename T>
     int alloc(T** p, size_t count) {
@@ -162,6 +172,7 @@ struct ResultImpl {
     cudaStream_t stream = nullptr;
     int32_t* block = nullptr;   // the page pool: pages are slices of it
     double* dblock = nullptr;
+    int64_t pages_alloc = 0;    // pages the pool holds (single joins; the tables list the used ones)
     std::vector<int32_t*> pair_pages;
     std::vector<double*> dist_pages;
     std::shared_ptr<void> shared_pool;  // batched results: the pool shared by all instances

@@ -32,6 +32,8 @@
 //    orders for pairs of adjacent cells and for the self-cell triangle); a
 //    chunk whose output would not fit the stage takes a general path that
 //    emits one pair per lane per round.
+#include <atomic>
+
 #include "sj_join_common.cuh"
 
 namespace sj {
@@ -424,9 +426,13 @@ __global__ void __launch_bounds__(kF32sWarps * 32, f32s_min_blocks<DP>()) k_join
 template <int DP, int RUNS, bool DBG>
 static int launch_f32s_dr(Index* ix, const JoinParams& p) {
     auto kern = k_join_f32s<DP, RUNS, DBG>;
-    int per_sm = 0;
-    SJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32sWarps * 32, 0));
-    if (per_sm < 1) per_sm = 1;
+    static std::atomic<int> cached{0};  // resident CTAs per SM (a property of the kernel)
+    int per_sm = cached.load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        SJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32sWarps * 32, 0));
+        if (per_sm < 1) per_sm = 1;
+        cached.store(per_sm, std::memory_order_relaxed);
+    }
     long long blocks = (long long)device_sm_count(ix->device) * per_sm;
     const long long need = (ix->n_items + kF32sWarps - 1) / kF32sWarps;
     if (blocks > need) blocks = need > 0 ? need : 1;
