@@ -188,7 +188,11 @@ typedef struct sj_result {
     double* const* dist_pages;  /* NULL, or host array of n_pages device
                                    pointers to the matching FP64 distances */
     int64_t n_candidates;     /* candidate pairs of the full neighbourhoods */
-    int64_t n_evaluated;      /* pair evaluations performed by the kernel */
+    int64_t n_evaluated;      /* pair evaluations performed by the kernel: the
+                                 index's scheduled evaluations less those the
+                                 FP32 filter's bounding-box prune (padded
+                                 d <= 8) removed; batched results report the
+                                 scheduled evaluations */
     int64_t n_rechecked;      /* pairs re-decided by the FP64 direct form */
     int32_t reruns;           /* reruns after the page pool overflowed */
     int32_t kernel;           /* SJ_KERNEL_* actually used */
@@ -460,11 +464,16 @@ SJ_API int sj_self_join_noalloc(const double* pts, int64_t n, int32_t d, double 
  *                                     coordinates, -||y||^2 / 2, thresholds
  *   records    host array of 4 * capacity int32: per evaluated pair (query
  *              position, candidate position, bits of a as float, 0), positions
- *              in cell order; pairs past capacity are counted, not stored
+ *              in cell order; the FP32 filter also records each pair its
+ *              bounding-box prune decided out unevaluated as (query position,
+ *              candidate position, 0, 1); pairs past capacity are counted, not
+ *              stored
  *   info       sizes and the bound: n, dp, kernel, c1, P, e2, records (pairs
- *              evaluated, exact), count (|R| of the join); with every array
- *              NULL and capacity 0 only the sizes and the bound are filled
- *              (records = count = -1) and nothing runs
+ *              recorded, exact), count (|R| of the join), prune_r2 (the FP32
+ *              filter's prune radius^2 in kernel units: a recorded pruned pair
+ *              has s_y above it; +inf for the tensor-core filters); with every
+ *              array NULL and capacity 0 only the sizes and the bound are
+ *              filled (records = count = -1) and nothing runs
  * Errors: SJ_ERR_ARG, SJ_ERR_UNSUPPORTED (another kernel), SJ_ERR_OOM,
  * SJ_ERR_CUDA.
  */
@@ -477,6 +486,7 @@ typedef struct sj_filter_dump {
     double e2;
     int64_t records;
     int64_t count;
+    double prune_r2;
 } sj_filter_dump;
 SJ_API int sj_debug_filter_dump(sj_handle h, int32_t* perm, float* y, float* hnorm, float* thr_out, float* thr_in,
                                 int32_t* records, int64_t capacity, sj_filter_dump* info);

@@ -97,6 +97,7 @@ class sj_filter_dump(ctypes.Structure):
         ("e2", ctypes.c_double),
         ("records", ctypes.c_int64),
         ("count", ctypes.c_int64),
+        ("prune_r2", ctypes.c_double),
     ]
 
 
@@ -484,7 +485,9 @@ def sj_kernel_launches() -> int:
 def self_join(points, eps: float, kernel="auto", emit_distances=False, symmetric=True, indexed_dims=0,
               max_pairs_hint=0, queries_per_item=0, tune_cache=None, short_circuit=0, stream=None):
     """Build, join and copy out in one call: returns (pairs int32 n x 2 numpy,
-    distances or None, stats dict)."""
+    distances or None, stats dict: the index's sizes (n_evaluated: the
+    scheduled pair evaluations), count, n_rechecked, reruns, kernel and
+    n_performed, the evaluations the tile kernel performed)."""
     opt = sj_default_options(kernel=kernel, emit_distances=int(emit_distances), symmetric=int(symmetric),
                              indexed_dims=indexed_dims, max_pairs_hint=max_pairs_hint,
                              queries_per_item=queries_per_item, tune_cache=tune_cache,
@@ -496,7 +499,7 @@ def self_join(points, eps: float, kernel="auto", emit_distances=False, symmetric
         try:
             pairs, dists = sj_result_copy(r)
             stats = dict(info, count=int(r.count), n_rechecked=int(r.n_rechecked), reruns=int(r.reruns),
-                         kernel=int(r.kernel))
+                         kernel=int(r.kernel), n_performed=int(r.n_evaluated))
         finally:
             sj_result_free(r)
     finally:
@@ -533,10 +536,12 @@ def pairs_to_keys(pairs: np.ndarray) -> np.ndarray:
 
 def sj_debug_filter_dump(handle, capacity: int):
     """The filter's own value for every evaluated pair of a built index
-    (test aid): returns (info, records, arrays) with records an (m, 3) int64
-    array of (query position, candidate position, float32 bits of a) in cell
-    order (m = min(info.records, capacity)) and arrays a dict of the index's
-    perm, y (n x dp float32), h, thr_out, thr_in in cell order."""
+    (test aid): returns (info, records, arrays) with records an (m, 4) int64
+    array of (query position, candidate position, float32 bits of a, pruned)
+    in cell order (m = min(info.records, capacity); pruned = 1 marks a pair
+    the FP32 filter's bounding-box prune decided out without evaluating it,
+    with no value of a) and arrays a dict of the index's perm, y (n x dp
+    float32), h, thr_out, thr_in in cell order."""
     lib = load()
     info = sj_filter_dump()
     # sizes first (no arrays, no records: nothing runs), then the dump
@@ -551,7 +556,7 @@ def sj_debug_filter_dump(handle, capacity: int):
     _check(lib.sj_debug_filter_dump(handle, perm.ctypes.data, y.ctypes.data, h.ctypes.data, to.ctypes.data,
                                     ti.ctypes.data, rec.ctypes.data, int(capacity), ctypes.byref(info)))
     m = min(int(info.records), int(capacity))
-    return info, rec[:m, :3].astype(np.int64), {"perm": perm, "y": y, "h": h, "thr_out": to, "thr_in": ti}
+    return info, rec[:m, :4].astype(np.int64), {"perm": perm, "y": y, "h": h, "thr_out": to, "thr_in": ti}
 
 
 def sj_index_perm(handle, n: int) -> np.ndarray:

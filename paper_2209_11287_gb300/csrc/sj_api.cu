@@ -533,6 +533,7 @@ static int run_join(sj_index* ix, ResultImpl* ri, int64_t page_pairs, bool dist,
     }
     *count_out = c[1];
     *rechecked_out = c[2];
+    ix->last_pruned = c[6];
     if (dbg_count) *dbg_count = c[5];
     return st;
 }
@@ -746,7 +747,7 @@ static int self_join_impl(sj_handle h, int64_t item_begin, int64_t item_end, sj_
     out->pair_pages = ri->pair_pages.data();
     out->dist_pages = dist ? ri->dist_pages.data() : nullptr;
     out->n_candidates = h->n_candidates;
-    out->n_evaluated = h->n_evaluated;
+    out->n_evaluated = h->n_evaluated - (int64_t)h->last_pruned;
     out->n_rechecked = (int64_t)rechecked;
     out->reruns = reruns;
     out->kernel = h->kernel;
@@ -773,6 +774,7 @@ int sj_debug_filter_dump(sj_handle h, int32_t* perm, float* y, float* hnorm, flo
     info->c1 = h->bound_c1;
     info->pbound = h->bound_p;
     info->e2 = h->e2;
+    info->prune_r2 = f32s ? (double)h->prune_r2 : INFINITY;
     info->records = -1;
     info->count = -1;
     if (!perm && !y && !hnorm && !thr_out && !thr_in && capacity == 0) return SJ_OK;  // sizes only
@@ -1113,6 +1115,7 @@ int join_batch_impl(const double* const* pts, const int64_t* n, const int32_t* d
             dev_free(g->d_off, s);
             dev_free(g->d_gid, s);
             dev_free(g->d_e2, s);
+            dev_free(g->d_r2, s);
             dev_free(g->d_inst_of_sorted, s);
             dev_free(g->d_item_inst, s);
         }
@@ -1257,6 +1260,7 @@ int join_batch_impl(const double* const* pts, const int64_t* n, const int32_t* d
             bj.inst_off = g.d_off;
             bj.inst_gid = g.d_gid;
             bj.inst_e2 = g.d_e2;
+            bj.inst_r2 = g.d_r2;
             bj.pool = reinterpret_cast<int2*>(pool->block);
             bj.dpool = pool->dblock;
             bj.page_log2 = page_log2;

@@ -449,6 +449,11 @@ struct PackParams {
     // kernel coordinates y = (x - lo) * scale, a power of two (1 except for
     // the FP16x2 filter, whose fp16 terms need |y_k| <= 2^15)
     double scale = 1.0;
+    // (eps (1 + g) + eta)^2 rounded up, and its binary32 copy rounded up: a
+    // squared distance of kernel coordinates above it is out for the decision
+    // rule (the small-d FP32 filter's bounding-box prune)
+    double prune_r2 = INFINITY;
+    float prune_r2f = INFINITY;
 };
 
 __host__ __device__ inline double gamma_n(double u, int k) { return k * u / (1.0 - k * u); }
@@ -531,6 +536,8 @@ void pack_coefficients(double eps, double pbound, double delta, double u_t, int 
     pp->bf_out = up(pp->b_out);
     pp->af_in = up(pp->a_in);
     pp->bf_in = up(pp->b_in);
+    pp->prune_r2 = so;
+    pp->prune_r2f = up(so);
 }
 
 // The two thresholds of a point with computed norm pc, one fma each, rounded
@@ -1468,6 +1475,7 @@ int build_index(Index* ix, const double* pts) {
     hp.scale = scale;
     ix->kscale = scale;
     pack_coefficients(ix->eps * scale, pbound * scale * scale, delta * scale, u_t, d, ix->dp, &hp, c1);
+    ix->prune_r2 = hp.prune_r2f;
 
     // ---- cell keys, sort and packing ----
     SJ_TRY(dev_alloc_t(&ix->perm, (size_t)n, s));
@@ -2098,6 +2106,7 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     std::vector<BInst> hp((size_t)K);
     std::vector<double> centre((size_t)K * dp, 0.0);
     std::vector<double> e2((size_t)K);
+    std::vector<float> r2((size_t)K);
     int shift = 0;
     const bool tensor = is_tensor_kernel(ix->kernel);
     const bool use_f32 = ix->kernel == SJ_KERNEL_FILTER_F32 || tensor;
@@ -2155,6 +2164,7 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
         b.scale = sk;
         PackParams pp{};
         pack_coefficients(t.eps * sk, pbk * sk * sk, 1.01 * u_t * rmax * sk, u_t, dp, dp, &pp, c1);
+        r2[k] = pp.prune_r2f;
         b.a_out = pp.a_out;
         b.b_out = pp.b_out;
         b.a_in = pp.a_in;
@@ -2174,6 +2184,8 @@ int build_batch_group(BatchGroup* g, const double* const* src_dev_ptrs, const in
     SJ_CK(cudaMemcpyAsync(dP, hp.data(), K * sizeof(BInst), cudaMemcpyHostToDevice, s));
     SJ_CK(cudaMemcpyAsync(dcentre, centre.data(), centre.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     SJ_CK(cudaMemcpyAsync(g->d_e2, e2.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
+    SJ_TRY(dev_alloc_t(&g->d_r2, (size_t)K, s));
+    SJ_CK(cudaMemcpyAsync(g->d_r2, r2.data(), K * sizeof(float), cudaMemcpyHostToDevice, s));
     // ---- keys, sort, cells ----
     unsigned long long* keys = nullptr;
     SJ_TRY(tmp.alloc(&keys, (size_t)n));

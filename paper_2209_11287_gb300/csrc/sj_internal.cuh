@@ -137,6 +137,11 @@ struct Index {
     double filter_band_rel = 0;  // predicted certified band (relative to eps^2)
     double bound_c1 = 0, bound_p = 0;  // certified bound E = c1 (P + pc) of the filter
     double kscale = 1.0;        // kernel coordinates = (x - centre) * kscale (a power of two)
+    // binary32 kernels: (eps (1 + g) + eta)^2 in kernel units rounded up; a
+    // squared distance of kernel coordinates above it is certified out (the
+    // radius of the thresholds, see pack_coefficients)
+    float prune_r2 = INFINITY;
+    unsigned long long last_pruned = 0;  // pair evaluations the last join's prune removed
 
     // per-join scratch: counters (item queue, result cursor, recheck count,
     // recheck queue fill)
@@ -190,6 +195,7 @@ struct BatchGroup {
     long long* d_off = nullptr;
     int32_t* d_gid = nullptr;
     double* d_e2 = nullptr;
+    float* d_r2 = nullptr;          // per instance: the bounding-box prune radius^2
     int32_t* d_inst_of_sorted = nullptr;
     int32_t* d_item_inst = nullptr;
 };
@@ -202,6 +208,8 @@ struct BatchJoin {
     const long long* inst_off;      // group-local instance -> its first point in the group
     const int32_t* inst_gid;        // group-local instance -> instance number in the batch
     const double* inst_e2;          // group-local instance -> eps^2
+    const float* inst_r2;           // group-local instance -> the small-d FP32 filter's
+                                    // bounding-box prune radius^2 (kernel units), or null
     // output (indexed by instance number)
     int2* pool;                     // n_pages pages of 2^page_log2 pairs
     double* dpool;                  // matching distances, or null

@@ -131,6 +131,7 @@ JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist) {
     p.sc_b = ix->sc_b;
     p.dbg = out.dbg;
     p.dbg_cap = out.dbg_cap;
+    p.prune_r2 = ix->prune_r2;
     return p;
 }
 

@@ -49,12 +49,24 @@ struct JoinParams {
     // counters[5] counts records, those past dbg_cap are dropped
     int4* dbg;
     unsigned long long dbg_cap;
+    // small-d FP32 filter: a candidate whose squared distance to the bounding
+    // box of an item's queries exceeds prune_r2 (kernel units) is out for
+    // every query and is not evaluated (single joins; batched joins take the
+    // per-instance value from BatchJoin::inst_r2); counters[6] counts the
+    // pair evaluations this removes
+    float prune_r2;
 };
 
 // Records one evaluated pair for the filter dump.
 __device__ __forceinline__ void dbg_record(const JoinParams& P, int32_t qs, int32_t cs, float a) {
     const unsigned long long k = atomicAdd(&P.counters[5], 1ull);
     if (k < P.dbg_cap) P.dbg[k] = make_int4(qs, cs, __float_as_int(a), 0);
+}
+// Records one pair the bounding-box prune decided out without evaluating it
+// (fourth field 1, no filter value).
+__device__ __forceinline__ void dbg_record_pruned(const JoinParams& P, int32_t qs, int32_t cs) {
+    const unsigned long long k = atomicAdd(&P.counters[5], 1ull);
+    if (k < P.dbg_cap) P.dbg[k] = make_int4(qs, cs, 0, 1);
 }
 
 JoinParams make_join_params(Index* ix, const JoinOut& out, int emit_dist);
@@ -213,14 +225,16 @@ struct ItemRoute {
     int gid;
     long long off;
     double e2;
+    float r2;  // the bounding-box prune's radius^2 (small-d FP32 filter)
 };
 __device__ __forceinline__ ItemRoute item_route(WarpStage& st, const JoinParams& P, long long it, int lane) {
-    ItemRoute r{0, 0, P.e2};
+    ItemRoute r{0, 0, P.e2, P.prune_r2};
     if (P.batch) {
         const int li = P.batch->item_inst[it];
         r.gid = P.batch->inst_gid[li];
         r.off = P.batch->inst_off[li];
         r.e2 = P.batch->inst_e2[li];
+        r.r2 = P.batch->inst_r2 ? P.batch->inst_r2[li] : INFINITY;
         if (st.cnt > 0 && st.gid != r.gid) stage_flush(st, P, lane);
         st.gid = r.gid;
     }

@@ -23,10 +23,17 @@
 //    miss mask (queries are visited last to first, so bit q is query q);
 //  * a candidate's thresholds and input index come in one 16-byte record,
 //    its coordinates in one more load (two for d = 8);
-//  * a lane walks the item's runs with a cursor (slots only grow), instead of
-//    searching the run list for every slot;
-//  * chunks of 32 TC slots (with TC > 2: while they fill, then chunks of 64
-//    for the tail);
+//  * candidates are first pruned against the bounding box of the item's
+//    queries: a lane per candidate walks the item's runs with a cursor,
+//    bounds the candidate's squared distance to the box from below (binary32,
+//    every operation rounded down) and drops it when that bound exceeds the
+//    radius^2 (eps (1 + g) + eta)^2 of the certified "out" threshold, so the
+//    pair is out for every query of the item; the kept candidates are
+//    compacted (ballot + popc) into a per-warp ring in shared memory.  On
+//    uniform data about half of the half-neighbourhood's candidates go (a
+//    cell's neighbours reach eps beyond its corners; the grid of Sec. III-B
+//    keeps every point of the 3^m cells);
+//  * chunks of 32 TC kept candidates from the ring;
 //  * emission: one warp scan of the lanes' output counts, then each lane
 //    writes its pairs straight into the warp's shared-memory stage (both
 //    orders for pairs of adjacent cells and for the self-cell triangle); a
@@ -52,19 +59,54 @@ template <int DP>
 constexpr int f32s_tc() { return DP <= 4 ? SJ_F32S_TC_SMALL : 2; }
 constexpr int kF32sStage = SJ_F32S_STAGE;
 static_assert(kF32sStage <= kStageMax, "a stage flush resolves at most 32 pages");
+// Candidates per lane of a compaction step, and the ring of kept candidates:
+// a chunk takes 32 TC of them once that many are queued, and a compaction
+// step adds at most 32 G, so it never holds more than 32 TC - 1 + 32 G (a
+// power of two, for the index arithmetic).  Compile-time tuning constant.
+#ifndef SJ_F32S_GATHER
+#define SJ_F32S_GATHER 2
+#endif
+constexpr int kF32sGather = SJ_F32S_GATHER;
+template <int DP>
+constexpr int f32s_ring() { return 32 * f32s_tc<DP>() - 1 + 32 * kF32sGather <= 128 ? 128 : 256; }
 
 template <int DP, int RUNS>
 struct F32sWarp {
     __align__(16) float2 qd[kQMax][DP];  // query coordinates, each as (v, v)
     float2 qh2[kQMax];     // (h, h), h = -||y_q||^2 / 2
     int32_t qid[kQMax];    // output index of each query (batched: instance-local)
+    __align__(16) float blo[DP];  // bounding box of the item's queries
+    __align__(16) float bhi[DP];
     int32_t rstart[RUNS];  // first sorted position of each run
     uint32_t rpre[RUNS + 1];  // prefix of the run lengths
     uint8_t rmir[RUNS];    // 0 plain, 1 mirrored, 2 self-cell triangle
-    int32_t cj[32 * f32s_tc<DP>()];   // per slot of a chunk: sorted position
-    int32_t cid[32 * f32s_tc<DP>()];  // per slot: output index
+    int32_t cid[32 * f32s_tc<DP>()];  // per slot of a chunk: output index
+    int32_t ring_j[f32s_ring<DP>()];  // kept candidates: sorted position
+    uint8_t ring_f[f32s_ring<DP>()];  // and run flag
+    unsigned long long pruned;        // pair evaluations the prune removed (lane 0)
+    unsigned long long rechecked;     // pairs re-decided in place, queue full (lane 0)
+    float r2;                         // the item's prune radius^2
     int2 stage[kF32sStage];
 };
+
+// The bounding box of the item's queries, per dim, as two values (binary32).
+template <int DP>
+__device__ __forceinline__ void load_box(const float* b, float (&v)[DP]) {
+    if constexpr (DP == 2) {
+        const float2 u = *reinterpret_cast<const float2*>(b);
+        v[0] = u.x;
+        v[1] = u.y;
+    } else {
+#pragma unroll
+        for (int h = 0; h < DP / 4; ++h) {
+            const float4 u = reinterpret_cast<const float4*>(b)[h];
+            v[4 * h] = u.x;
+            v[4 * h + 1] = u.y;
+            v[4 * h + 2] = u.z;
+            v[4 * h + 3] = u.w;
+        }
+    }
+}
 
 // Candidate coordinates of one point as DP floats, loaded with vector loads.
 template <int DP>
@@ -90,13 +132,94 @@ __device__ __forceinline__ uint32_t push_sign(uint32_t mask, float v) {
     return __funnelshift_l(__float_as_uint(v), mask, 1);
 }
 
-// One chunk of 32 TC candidate slots [base, base + 32 TC) against the item's
-// Q queries.  `r` is the lane's run cursor (kept across chunks).
+// Compaction step: candidates [v0, v0 + 32 G) of the item (G per lane, `r`
+// the lane's run cursor, kept across steps) are tested against the queries'
+// bounding box and the kept ones appended to the ring after its `cnt`
+// entries from `head`; the G coordinate loads of a lane are issued before
+// any is used, so their latencies overlap.  The lower bound: per dim the gap
+// max(lo - c, c - hi, 0) and the sum of the squared gaps, each operation
+// rounded down, is at most the exact squared distance of the candidate to
+// every query; above W.r2 the pair is out for every query (the argument of
+// the certified "out" threshold, pack_coefficients).  Self-cell candidates
+// (flag 2) are always kept.  W.pruned counts the pair evaluations removed.
+template <int DP, int RUNS, bool DBG>
+__device__ __forceinline__ void f32s_gather(F32sWarp<DP, RUNS>& W, const JoinParams& P, const Item& I,
+                                            const ItemRoute& R, int Q, uint32_t C, uint32_t v0, int lane, int& r,
+                                            uint32_t head, uint32_t& cnt) {
+    constexpr uint32_t RING = (uint32_t)f32s_ring<DP>();
+    constexpr int G = kF32sGather;
+    const float* __restrict__ Y = static_cast<const float*>(P.y);
+    int32_t jj[G];
+    uint32_t f[G];
+    bool test[G], keep[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const uint32_t v = v0 + (uint32_t)(32 * g + lane);
+        jj[g] = 0;
+        f[g] = 0;
+        keep[g] = v < C;
+        if (v < C) {
+            while (W.rpre[r + 1] <= v) ++r;
+            jj[g] = W.rstart[r] + (int32_t)(v - W.rpre[r]);
+            if (!SJ_BOUND(P, jj[g] >= 0 && jj[g] < P.n_points && r < RUNS, 11)) jj[g] = 0;
+            f[g] = W.rmir[r];
+        }
+        test[g] = keep[g] && f[g] != 2u;
+    }
+    float c[G][DP];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (test[g]) {
+            load_coords<DP>(Y, jj[g], c[g]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < DP; ++k) c[g][k] = 0.f;
+        }
+    }
+    float lo[DP], hi[DP];
+    load_box<DP>(W.blo, lo);
+    load_box<DP>(W.bhi, hi);
+    const float r2 = W.r2;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        float lb = 0.f;
+#pragma unroll
+        for (int k = 0; k < DP; ++k) {
+            const float gap = fmaxf(fmaxf(__fsub_rd(lo[k], c[g][k]), __fsub_rd(c[g][k], hi[k])), 0.f);
+            lb = __fmaf_rd(gap, gap, lb);
+        }
+        if (test[g] && lb > r2) keep[g] = false;
+    }
+    uint32_t kept = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const unsigned m = __ballot_sync(0xffffffffu, keep[g]);
+        if (keep[g]) {
+            const uint32_t e = (head + cnt + kept + (uint32_t)__popc(m & ((1u << lane) - 1u))) & (RING - 1u);
+            W.ring_j[e] = jj[g];
+            W.ring_f[e] = (uint8_t)f[g];
+        }
+        kept += (uint32_t)__popc(m);
+    }
+    const uint32_t nv = min((uint32_t)(32 * G), C - v0);
+    if (lane == 0) W.pruned += (unsigned long long)(nv - kept) * (unsigned long long)Q;
+    cnt += kept;
+    if constexpr (DBG) {
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (test[g] && !keep[g])
+                for (int q = 0; q < Q; ++q) dbg_record_pruned(P, I.q0 + q, jj[g]);
+    }
+}
+
+// One chunk of `ns` <= 32 TC kept candidates, ring entries [head, head + ns),
+// against the item's Q queries (slot t 32 + lane is entry head + t 32 + lane).
 template <int DP, int RUNS, int TC, bool DBG>
 __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st, const JoinParams& P,
-                                           const Item& I, const ItemRoute& R, int Q, uint32_t C, uint32_t base,
-                                           int lane, int& r, unsigned long long& rechecked) {
+                                           const Item& I, const ItemRoute& R, int Q, uint32_t ns, uint32_t head,
+                                           int lane) {
     static_assert(TC % 2 == 0, "candidates go in pairs");
+    constexpr uint32_t RING = (uint32_t)f32s_ring<DP>();
     const float* __restrict__ Y = static_cast<const float*>(P.y);
     const float4* __restrict__ AUX = P.aux;
 
@@ -107,19 +230,17 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
     uint32_t meta = 0;
 #pragma unroll
     for (int t = 0; t < TC; ++t) {
-        const uint32_t v = base + (uint32_t)(t * 32 + lane);
+        const uint32_t sl = (uint32_t)(t * 32 + lane);
         float c[DP];
         float to = INFINITY, ti = INFINITY;
-        if (v < C) {
-            while (W.rpre[r + 1] <= v) ++r;
-            int32_t jj = W.rstart[r] + (int32_t)(v - W.rpre[r]);
-            if (!SJ_BOUND(P, jj >= 0 && jj < P.n_points && r < RUNS, 11)) jj = 0;
-            const uint32_t f = W.rmir[r];
+        if (sl < ns) {
+            const uint32_t e = (head + sl) & (RING - 1u);
+            const int32_t jj = W.ring_j[e];
+            const uint32_t f = W.ring_f[e];
             load_coords<DP>(Y, jj, c);
             const float4 ax = AUX[jj];
             to = ax.x;
             ti = ax.y;
-            W.cj[t * 32 + lane] = jj;
             W.cid[t * 32 + lane] = (int32_t)(__float_as_int(ax.z) - (int32_t)R.off);
             // self-cell triangle: queries q0 .. jj pair with jj
             const uint32_t dg1 = (f == 2 && jj < I.q1) ? (uint32_t)(jj - I.q0 + 1) : 0u;
@@ -178,10 +299,9 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
             mi[2 * p + 1] = push_sign(mi[2 * p + 1], din.y);
             if constexpr (DBG) {
                 const int q = Q - 1 - qq;
-                if (base + (uint32_t)(2 * p * 32 + lane) < C)
-                    dbg_record(P, I.q0 + q, W.cj[2 * p * 32 + lane], a.x);
-                if (base + (uint32_t)((2 * p + 1) * 32 + lane) < C)
-                    dbg_record(P, I.q0 + q, W.cj[(2 * p + 1) * 32 + lane], a.y);
+                const uint32_t s0 = (uint32_t)(2 * p * 32 + lane), s1 = s0 + 32u;
+                if (s0 < ns) dbg_record(P, I.q0 + q, W.ring_j[(head + s0) & (RING - 1u)], a.x);
+                if (s1 < ns) dbg_record(P, I.q0 + q, W.ring_j[(head + s1) & (RING - 1u)], a.y);
             }
         }
     }
@@ -309,15 +429,16 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
             }
         if (!__any_sync(0xffffffffu, want)) break;
         const uint32_t ms = (meta >> (8 * t_sel)) & 0xFFu;
-        const int32_t jj = want ? W.cj[t_sel * 32 + lane] : 0;
+        const int32_t jj = want ? W.ring_j[(head + (uint32_t)(t_sel * 32 + lane)) & (RING - 1u)] : 0;
         const int32_t ci = want ? W.cid[t_sel * 32 + lane] : 0;
         const bool mir = want && (ms & 3u) != 0u && q != (int)(ms >> 2) - 1;
         const bool queued = band_push(P, lane, want, I.q0 + q, jj, mir);
         int no = 0;
         int32_t qi = 0;
+        const unsigned inplace = __ballot_sync(0xffffffffu, want && !queued);
+        if (lane == 0 && inplace) W.rechecked += (unsigned long long)__popc(inplace);
         if (want && !queued) {
             const double s = direct_sq(P.xs + (int64_t)(I.q0 + q) * P.dp, P.xs + (int64_t)jj * P.dp, P.d);
-            ++rechecked;
             if (s <= R.e2) {
                 no = mir ? 2 : 1;
                 qi = W.qid[q];
@@ -348,13 +469,18 @@ template <int DP, int RUNS, bool DBG>
 __global__ void __launch_bounds__(kF32sWarps * 32, f32s_min_blocks<DP>()) k_join_f32s(JoinParams P) {
     constexpr int TC = f32s_tc<DP>();
     constexpr uint32_t SLOTS = 32u * TC;
+    constexpr uint32_t RING = (uint32_t)f32s_ring<DP>();
+    static_assert(SLOTS - 1u + 32u * kF32sGather <= RING, "the ring holds a chunk and one compaction step");
     __shared__ F32sWarp<DP, RUNS> smem[kF32sWarps];
     const float* __restrict__ Y = static_cast<const float*>(P.y);
     const float* __restrict__ H = static_cast<const float*>(P.h);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     F32sWarp<DP, RUNS>& W = smem[wid];
     WarpStage st{W.stage, nullptr, 0, 0, kF32sStage};
-    unsigned long long rechecked = 0;
+    if (lane == 0) {
+        W.pruned = 0;
+        W.rechecked = 0;
+    }
 
     long long next = 0;
     if (lane == 0) next = (long long)atomicAdd(&P.counters[0], 1ull);
@@ -370,12 +496,28 @@ __global__ void __launch_bounds__(kF32sWarps * 32, f32s_min_blocks<DP>()) k_join
         if (!SJ_BOUND(P, I.q0 >= 0 && Q >= 1 && Q <= kQMax && I.q1 <= P.n_points && nr >= 0 && nr <= RUNS, 13))
             continue;
         const ItemRoute R = item_route(st, P, it, lane);
-        // the item's queries (duplicated coordinates) and runs
+        // the item's queries (duplicated coordinates), their bounding box
+        // (lane holds dim lane % DP, as 32 is a multiple of DP) and runs
+        float bmin = INFINITY, bmax = -INFINITY;
         for (int i = lane; i < kQMax * DP; i += 32) {
             const int q = i / DP;
             const float v = q < Q ? Y[(int64_t)I.q0 * DP + i] : 0.f;
             W.qd[q][i % DP] = make_float2(v, v);
+            if (q < Q) {
+                bmin = fminf(bmin, v);
+                bmax = fmaxf(bmax, v);
+            }
         }
+#pragma unroll
+        for (int o = DP; o < 32; o <<= 1) {
+            bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+            bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        }
+        if (lane < DP) {
+            W.blo[lane] = bmin;
+            W.bhi[lane] = bmax;
+        }
+        if (lane == 0) W.r2 = R.r2;
         if (lane < kQMax) {
             const float h = lane < Q ? H[I.q0 + lane] : -INFINITY;
             W.qh2[lane] = make_float2(h, h);
@@ -405,22 +547,32 @@ __global__ void __launch_bounds__(kF32sWarps * 32, f32s_min_blocks<DP>()) k_join
         if (lane == 0) W.rpre[0] = 0;
         __syncwarp();
         const uint32_t C = carry;
+        // compaction steps of 32 G candidates into the ring, a chunk whenever
+        // SLOTS kept candidates are queued, then the rest
+        // (one call site each, so one inlined copy of the chunk's code)
         int r = 0;
-        uint32_t base = 0;
-        if constexpr (TC == 2) {  // one chunk shape (one copy of the code)
-            for (; base < C; base += SLOTS)
-                f32s_chunk<DP, RUNS, TC, DBG>(W, st, P, I, R, Q, C, base, lane, r, rechecked);
-        } else {
-            for (; base + SLOTS <= C; base += SLOTS)
-                f32s_chunk<DP, RUNS, TC, DBG>(W, st, P, I, R, Q, C, base, lane, r, rechecked);
-            for (; base < C; base += 64u)
-                f32s_chunk<DP, RUNS, 2, DBG>(W, st, P, I, R, Q, C, base, lane, r, rechecked);
+        uint32_t head = 0, cnt = 0, v0 = 0;
+        for (;;) {  // warp-uniform
+            if (v0 < C) {
+                f32s_gather<DP, RUNS, DBG>(W, P, I, R, Q, C, v0, lane, r, head, cnt);
+                v0 += 32u * kF32sGather;
+            }
+            const bool more = v0 < C;
+            if (cnt >= SLOTS || (!more && cnt > 0u)) {
+                const uint32_t ns = min(cnt, SLOTS);
+                __syncwarp();
+                f32s_chunk<DP, RUNS, TC, DBG>(W, st, P, I, R, Q, ns, head, lane);
+                head = (head + ns) & (RING - 1u);
+                cnt -= ns;
+            } else if (!more) {
+                break;
+            }
         }
         __syncwarp();
     }
     stage_flush(st, P, lane);
-    for (int o = 16; o > 0; o >>= 1) rechecked += __shfl_down_sync(0xffffffffu, rechecked, o);
-    if (lane == 0 && rechecked) atomicAdd(&P.counters[2], rechecked);
+    if (lane == 0 && W.rechecked) atomicAdd(&P.counters[2], W.rechecked);
+    if (lane == 0 && W.pruned) atomicAdd(&P.counters[6], W.pruned);
 }
 
 template <int DP, int RUNS, bool DBG>

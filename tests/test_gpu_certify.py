@@ -11,7 +11,9 @@ and check, for every pair:
     TwoSum, Knuth; TwoProduct by Dekker's split), so the bound itself holds on
     random, Gaussian-clustered, near-tie and cancellation-heavy data;
   * a >= thr_in  =>  the decision rule says in, a < thr_out => it says out,
-    the rule being the oracle's binary64 direct form (Sec. II-A, Eq. 1).
+    the rule being the oracle's binary64 direct form (Sec. II-A, Eq. 1);
+  * every pair the FP32 filter's bounding-box prune dropped unevaluated has
+    s_y above the prune radius^2 and is out under the decision rule.
 
 The largest observed |s_y - s~| / E of each case is printed (pytest -s).
 """
@@ -113,11 +115,42 @@ def _dump(x, eps, kernel):
     return info, rec, arr
 
 
+def _rule_in(x, eps, perm, qs, cs):
+    """The decision rule (oracle, input points) for pairs of cell positions."""
+    e2 = eps * eps
+    order = np.argsort(qs, kind="stable")
+    qs_s, cs_s = qs[order], cs[order]
+    bounds = np.flatnonzero(np.diff(qs_s)) + 1
+    starts = np.concatenate([[0], bounds])
+    ends = np.concatenate([bounds, [qs_s.size]])
+    out = np.empty(qs.size, dtype=bool)
+    for s0, s1 in zip(starts, ends):
+        q = int(perm[qs_s[s0]])
+        row = oracle.sqdist_row(x, q)
+        out[order[s0:s1]] = row[perm[cs_s[s0:s1]]] <= e2
+    return out
+
+
 def _check(name, x, eps, kernel):
     info, rec, arr = _dump(x, eps, kernel)
+    y = arr["y"]
+    perm = arr["perm"]
+    pruned = rec[:, 3] == 1
+    if pruned.any():
+        # the prune: s_y of each dropped pair is above the radius^2, and the
+        # decision rule says out
+        pq, pcs = rec[pruned, 0], rec[pruned, 1]
+        sy_hi, sy_lo = _sqdist_dd(y[pq], y[pcs])
+        assert np.all((sy_hi - info.prune_r2) + sy_lo > 0), f"{name}/{kernel}: a pruned pair within the radius"
+        assert not np.any(_rule_in(x, eps, perm, pq, pcs)), f"{name}/{kernel}: a pruned pair is in"
+    REPORT[(name, kernel, "pruned")] = int(pruned.sum())
+    if kernel == "filter_f32" and name in ("uniform4d", "uniform2d"):
+        # about 46% (4-D) and 20% (2-D) of the scheduled evaluations
+        floor = 0.3 if name == "uniform4d" else 0.1
+        assert pruned.sum() > floor * rec.shape[0], "the bounding-box prune removed almost nothing"
+    rec = rec[~pruned]
     qs, cs = rec[:, 0], rec[:, 1]
     a = rec[:, 2].astype(np.int32).view(np.float32).astype(np.float64)
-    y = arr["y"]
     pc = -2.0 * arr["h"].astype(np.float64)[cs]  # h = -pc / 2 exactly
     # s~ = pc - 2 a (both exact in binary64 as float values; the sum as
     # double-double), against s_y
@@ -128,26 +161,16 @@ def _check(name, x, eps, kernel):
     ratio = err / E
     worst = float(ratio.max())
     REPORT[(name, kernel)] = worst
-    print(f"\n{kernel:14s} {name:12s} pairs {rec.shape[0]:9d}  max |s_y - s~| / E = {worst:.3e}")
+    print(f"\n{kernel:14s} {name:12s} pairs {rec.shape[0]:9d}  max |s_y - s~| / E = {worst:.3e}"
+          f"  pruned {int(pruned.sum())}")
     assert worst < 1.0, (name, kernel, worst)
     # certified decisions against the decision rule (oracle, input points)
-    perm = arr["perm"]
     tin = arr["thr_in"].astype(np.float64)[cs]
     tout = arr["thr_out"].astype(np.float64)[cs]
     cert_in = a >= tin
     cert_out = a < tout
     assert not np.any(cert_in & cert_out)
-    e2 = eps * eps
-    order = np.argsort(qs, kind="stable")
-    qs_s, cs_s = qs[order], cs[order]
-    bounds = np.flatnonzero(np.diff(qs_s)) + 1
-    starts = np.concatenate([[0], bounds])
-    ends = np.concatenate([bounds, [qs_s.size]])
-    rule_in = np.empty(qs.size, dtype=bool)
-    for s0, s1 in zip(starts, ends):
-        q = int(perm[qs_s[s0]])
-        row = oracle.sqdist_row(x, q)
-        rule_in[order[s0:s1]] = row[perm[cs_s[s0:s1]]] <= e2
+    rule_in = _rule_in(x, eps, perm, qs, cs)
     assert not np.any(cert_in & ~rule_in), f"{name}/{kernel}: a certified-in pair is out"
     assert not np.any(cert_out & rule_in), f"{name}/{kernel}: a certified-out pair is in"
     # the classes are not vacuous: most pairs are certified one way or the other
