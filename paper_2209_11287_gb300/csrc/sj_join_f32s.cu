@@ -35,10 +35,12 @@
 //    keeps every point of the 3^m cells);
 //  * chunks of 32 TC kept candidates from the ring;
 //  * emission: one warp scan of the lanes' output counts, then each lane
-//    writes its pairs straight into the warp's shared-memory stage (both
-//    orders for pairs of adjacent cells and for the self-cell triangle); a
-//    chunk whose output would not fit the stage takes a general path that
-//    emits one pair per lane per round.
+//    writes its pairs straight into the warp's shared-memory stage; a pair
+//    of adjacent cells or above the self-cell triangle's diagonal, which is
+//    emitted in both orders, is staged once with a flag (bit 31 of the query
+//    index) and its mirror is written at the flush, so the stage holds twice
+//    the output and the lane stores half of it; a chunk whose entries would
+//    not fit the stage takes a general path in stage-sized windows.
 #include <atomic>
 
 #include "sj_join_common.cuh"
@@ -58,7 +60,7 @@ namespace sj {
 template <int DP>
 constexpr int f32s_tc() { return DP <= 4 ? SJ_F32S_TC_SMALL : 2; }
 constexpr int kF32sStage = SJ_F32S_STAGE;
-static_assert(kF32sStage <= kStageMax, "a stage flush resolves at most 32 pages");
+static_assert(2 * kF32sStage <= kStageMax, "a stage flush (entries and mirrors) resolves at most 32 pages");
 // Candidates per lane of a compaction step, and the ring of kept candidates:
 // a chunk takes 32 TC of them once that many are queued, and a compaction
 // step adds at most 32 G, so it never holds more than 32 TC - 1 + 32 G (a
@@ -86,6 +88,7 @@ struct F32sWarp {
     unsigned long long pruned;        // pair evaluations the prune removed (lane 0)
     unsigned long long rechecked;     // pairs re-decided in place, queue full (lane 0)
     float r2;                         // the item's prune radius^2
+    int smir;                         // staged entries flagged for a mirrored copy (lane 0)
     int2 stage[kF32sStage];
 };
 
@@ -130,6 +133,90 @@ __device__ __forceinline__ void load_coords(const float* __restrict__ Y, int32_t
 // (mask << 1) | sign bit of v: one funnel shift.
 __device__ __forceinline__ uint32_t push_sign(uint32_t mask, float v) {
     return __funnelshift_l(__float_as_uint(v), mask, 1);
+}
+
+// Stage entries: (query output index | kStageMirror if the pair is also
+// emitted mirrored, candidate output index); output indices are below 2^31.
+constexpr uint32_t kStageMirror = 0x80000000u;
+
+// Copies the warp's staged entries out: one atomic on the result cursor (the
+// instance's cursor in a batched join) reserves entries + mirrored pairs;
+// entry i goes to base + i, the mirrored pairs after them in entry order.
+// Positions past the pool's capacity (a batched instance's pages) are counted
+// but not written.
+template <int DP, int RUNS>
+__device__ __forceinline__ void f32s_flush(F32sWarp<DP, RUNS>& W, WarpStage& st, const JoinParams& P, int lane) {
+    __syncwarp();
+    const int ne = st.cnt;
+    const unsigned long long total = (unsigned long long)(ne + W.smir);
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long base = 0;
+    if (P.batch) {
+        const BatchJoin& B = *P.batch;
+        if (lane == 0 && total > 0) base = atomicAdd(&B.cursor[st.gid], total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (total > 0) {
+            // pages of at least 64 pairs: a flush of <= kStageMax pairs
+            // touches at most 32 pages, one lane resolves each
+            const unsigned long long pg0 = base >> B.page_log2;
+            const int npg = (int)(((base + total - 1ull) >> B.page_log2) - pg0) + 1;
+            const int32_t mine = lane < npg ? batch_page(B, st.gid, pg0 + (unsigned long long)lane) : -1;
+            const unsigned long long mask = (1ull << B.page_log2) - 1ull;
+            unsigned long long mb = base + (unsigned long long)ne;
+            for (int i0 = 0; i0 < ne; i0 += 32) {
+                const int i = i0 + lane;
+                const int2 e = i < ne ? st.pairs[i] : make_int2(0, 0);
+                const bool m = i < ne && ((uint32_t)e.x & kStageMirror) != 0u;
+                const int32_t qi = (int32_t)((uint32_t)e.x & ~kStageMirror);
+                const unsigned bm = __ballot_sync(0xffffffffu, m);
+                const unsigned long long p1 = base + (unsigned long long)i;
+                const unsigned long long p2 = mb + (unsigned long long)__popc(bm & lt);
+                const int32_t pa = __shfl_sync(0xffffffffu, mine, i < ne ? (int)((p1 >> B.page_log2) - pg0) : 0);
+                const int32_t pb = __shfl_sync(0xffffffffu, mine, m ? (int)((p2 >> B.page_log2) - pg0) : 0);
+                if (i < ne && pa >= 0)
+                    B.pool[((long long)pa << B.page_log2) | (long long)(p1 & mask)] = make_int2(qi, e.y);
+                if (m && pb >= 0) B.pool[((long long)pb << B.page_log2) | (long long)(p2 & mask)] = make_int2(e.y, qi);
+                mb += (unsigned long long)__popc(bm);
+            }
+        }
+    } else {
+        if (lane == 0 && total > 0) base = atomicAdd(&P.counters[1], total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        unsigned long long mb = base + (unsigned long long)ne;
+        for (int i0 = 0; i0 < ne; i0 += 32) {
+            const int i = i0 + lane;
+            const int2 e = i < ne ? st.pairs[i] : make_int2(0, 0);
+            const bool m = i < ne && ((uint32_t)e.x & kStageMirror) != 0u;
+            const int32_t qi = (int32_t)((uint32_t)e.x & ~kStageMirror);
+            const unsigned bm = __ballot_sync(0xffffffffu, m);
+            const unsigned long long p1 = base + (unsigned long long)i;
+            if (i < ne && p1 < P.capacity) P.out_pairs[p1] = make_int2(qi, e.y);
+            const unsigned long long p2 = mb + (unsigned long long)__popc(bm & lt);
+            if (m && p2 < P.capacity) P.out_pairs[p2] = make_int2(e.y, qi);
+            mb += (unsigned long long)__popc(bm);
+        }
+    }
+    __syncwarp();
+    st.cnt = 0;
+    if (lane == 0) W.smir = 0;
+}
+
+// Warp-collective: each lane offers nout in {0, 1, 2} pairs ((qid, cid) and,
+// when 2, the mirrored (cid, qid)): one stage entry each, flagged when 2.
+template <int DP, int RUNS>
+__device__ __forceinline__ void f32s_emit(F32sWarp<DP, RUNS>& W, WarpStage& st, const JoinParams& P, int lane,
+                                          int nout, int32_t qid, int32_t cid) {
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned b1 = __ballot_sync(0xffffffffu, nout >= 1);
+    const unsigned b2 = __ballot_sync(0xffffffffu, nout == 2);
+    const int ne = __popc(b1);
+    if (ne == 0) return;
+    if (st.cnt + ne > st.cap) f32s_flush(W, st, P, lane);
+    if (nout >= 1)
+        st.pairs[st.cnt + __popc(b1 & lt)] =
+            make_int2((int32_t)((uint32_t)qid | (nout == 2 ? kStageMirror : 0u)), cid);
+    st.cnt += ne;
+    if (lane == 0) W.smir += __popc(b2);
 }
 
 // Compaction step: candidates [v0, v0 + 32 G) of the item (G per lane, `r`
@@ -320,16 +407,22 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
         cin[t] = ~mi[t] & mb;
         unc[t] = mb & mi[t];
         any_unc |= unc[t];
+        // entries (low 16 bits) and mirrored copies (high 16 bits; the
+        // self-cell diagonal is emitted once)
         const int c = __popc(cin[t]);
-        nout += f ? 2 * c : c;
-        if (dg1 && ((cin[t] >> (dg1 - 1u)) & 1u)) nout -= 1;  // the diagonal once
+        const int dgin = (dg1 && ((cin[t] >> (dg1 - 1u)) & 1u)) ? 1 : 0;
+        nout += c + (f ? (c - dgin) << 16 : 0);
     }
     int total;
-    const int off = warp_excl_scan(nout, lane, &total);
+    const int off16 = warp_excl_scan(nout, lane, &total);
+    const int tmir = total >> 16;
+    total &= 0xFFFF;
+    const int off = off16 & 0xFFFF;
+    nout &= 0xFFFF;
     if (total > 0) {
-        if (st.cnt + total > st.cap) stage_flush(st, P, lane);
+        if (st.cnt + total > st.cap) f32s_flush(W, st, P, lane);
         if (st.cnt + total <= st.cap) {
-            // the common case: the chunk's output fits the stage
+            // the common case: the chunk's entries fit the stage
             int pos = st.cnt + off;
             if (!SJ_BOUND(P, pos >= 0 && pos + nout <= st.cap, 12)) {
                 pos = 0;
@@ -356,9 +449,8 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
                         const int bit = __ffs(b) - 1;
                         b &= b - 1u;
                         const int32_t ci = bit >= 16 ? ci1 : ci0;
-                        const int32_t qi = W.qid[bit & 15];
-                        st.pairs[pos++] = make_int2(qi, ci);
-                        if ((two >> bit) & 1u) st.pairs[pos++] = make_int2(ci, qi);
+                        const uint32_t qi = (uint32_t)W.qid[bit & 15] | (((two >> bit) & 1u) << 31);
+                        st.pairs[pos++] = make_int2((int32_t)qi, ci);
                     }
                 }
             } else {
@@ -372,19 +464,20 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
                     while (b) {
                         const int q = __ffs(b) - 1;
                         b &= b - 1u;
-                        const int32_t qi = W.qid[q];
-                        st.pairs[pos++] = make_int2(qi, ci);
-                        if (two && q != dg) st.pairs[pos++] = make_int2(ci, qi);
+                        const uint32_t qi = (uint32_t)W.qid[q] | (two && q != dg ? kStageMirror : 0u);
+                        st.pairs[pos++] = make_int2((int32_t)qi, ci);
                     }
                 }
             }
             st.cnt += total;
+            if (lane == 0) W.smir += tmir;
         } else {
-            // dense cells: the output in stage-sized windows; each lane
-            // writes the outputs of its range [off, off + nout) that fall in
+            // dense cells: the entries in stage-sized windows; each lane
+            // writes the entries of its range [off, off + nout) that fall in
             // the window, the stage is flushed after each window
             for (int w0 = 0; w0 < total;) {  // warp-uniform
                 const int w1 = min(total, w0 + (st.cap - st.cnt));
+                int wm = 0;  // this lane's mirrored entries in the window
                 if (off < w1 && off + nout > w0) {
                     int idx = off;
 #pragma unroll
@@ -397,19 +490,22 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
                         while (b) {
                             const int q = __ffs(b) - 1;
                             b &= b - 1u;
-                            const int32_t qi = W.qid[q];
-                            if (idx >= w0 && idx < w1) st.pairs[st.cnt + idx - w0] = make_int2(qi, ci);
-                            ++idx;
-                            if (two && q != dg) {
-                                if (idx >= w0 && idx < w1) st.pairs[st.cnt + idx - w0] = make_int2(ci, qi);
-                                ++idx;
+                            const bool mq = two && q != dg;
+                            if (idx >= w0 && idx < w1) {
+                                st.pairs[st.cnt + idx - w0] =
+                                    make_int2((int32_t)((uint32_t)W.qid[q] | (mq ? kStageMirror : 0u)), ci);
+                                wm += mq ? 1 : 0;
                             }
+                            ++idx;
                         }
                     }
                 }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) wm += __shfl_xor_sync(0xffffffffu, wm, o);
                 st.cnt += w1 - w0;
+                if (lane == 0) W.smir += wm;
                 w0 = w1;
-                if (st.cnt == st.cap) stage_flush(st, P, lane);
+                if (st.cnt == st.cap) f32s_flush(W, st, P, lane);
             }
         }
     }
@@ -444,7 +540,7 @@ __device__ __forceinline__ void f32s_chunk(F32sWarp<DP, RUNS>& W, WarpStage& st,
                 qi = W.qid[q];
             }
         }
-        stage_emit_pairs(st, P, lane, no, qi, ci);
+        f32s_emit(W, st, P, lane, no, qi, ci);
     }
 }
 
@@ -480,6 +576,7 @@ __global__ void __launch_bounds__(kF32sWarps * 32, f32s_min_blocks<DP>()) k_join
     if (lane == 0) {
         W.pruned = 0;
         W.rechecked = 0;
+        W.smir = 0;
     }
 
     long long next = 0;
@@ -495,6 +592,9 @@ __global__ void __launch_bounds__(kF32sWarps * 32, f32s_min_blocks<DP>()) k_join
         const int nr = I.r1 - I.r0;
         if (!SJ_BOUND(P, I.q0 >= 0 && Q >= 1 && Q <= kQMax && I.q1 <= P.n_points && nr >= 0 && nr <= RUNS, 13))
             continue;
+        // (batched: the stage holds one instance's entries; flushed here, in
+        // its own format, before item_route would flush it)
+        if (P.batch && st.cnt > 0 && P.batch->inst_gid[P.batch->item_inst[it]] != st.gid) f32s_flush(W, st, P, lane);
         const ItemRoute R = item_route(st, P, it, lane);
         // the item's queries (duplicated coordinates), their bounding box
         // (lane holds dim lane % DP, as 32 is a multiple of DP) and runs
@@ -570,7 +670,7 @@ __global__ void __launch_bounds__(kF32sWarps * 32, f32s_min_blocks<DP>()) k_join
         }
         __syncwarp();
     }
-    stage_flush(st, P, lane);
+    f32s_flush(W, st, P, lane);
     if (lane == 0 && W.rechecked) atomicAdd(&P.counters[2], W.rechecked);
     if (lane == 0 && W.pruned) atomicAdd(&P.counters[6], W.pruned);
 }
