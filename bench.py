@@ -151,7 +151,7 @@ METRICS = {
                "low-prec filter",
 }
 DEFAULT_VARIANTS = {
-    "uniform4d": ["filter_f32", "tuned", "fp64_fma", "fp64_dmma"],
+    "uniform4d": ["filter_f32", "tuned", "fp64_fma", "fp64_dmma", "filter_fp16x2", "filter_bf16x2", "filter_bf16x3"],
     "uniform2d": ["filter_f32", "fp64_fma", "fp64_dmma", "filter_bf16x2"],
     "mixture16d": ["filter_fp16x2", "tuned", "filter_bf16x2", "filter_bf16x3", "filter_f32", "fp64_fma",
                    "fp64_fma_sc"],
@@ -369,6 +369,8 @@ def run_native(args):
     if rank == 0:
         line = make_line(args, w, results, variants, world, kern_ms, e2e_s, head)
         line["e2e"].update(link)
+        line["e2e"]["ms_min"] = round(min(t_e2e) * 1e3, 3)
+        line["e2e"]["ms_max"] = round(max(t_e2e) * 1e3, 3)
         line["e2e"]["d2h_floor_ms"] = round(head["count"] * 8 / (link["d2h_gbs"] * 1e9) * 1e3, 3)
         line["e2e"]["path"] = ("sj_build_index on pinned host points, sj_self_join_to_host into pinned host memory "
                                "(rounds of work items, copies overlapping the next round)" if world == 1 else

@@ -626,6 +626,53 @@ __global__ void k_pack(const double* __restrict__ x, const int32_t* __restrict__
     pack_one<T>(x + (int64_t)src_i * pp.d, src_i, p, pp, o);
 }
 
+// k_pack for d == dp in {2, 4, 8} with the input dim order and no
+// short-circuit bounds: the same arithmetic as pack_one in the same order
+// (so the same bits), the rows moved with 16-byte loads and stores.
+template <typename T, int DP>
+__device__ __forceinline__ void store_row(T* dst, const T (&v)[DP]) {
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int h = 0; h < DP / 2; ++h) reinterpret_cast<double2*>(dst)[h] = make_double2(v[2 * h], v[2 * h + 1]);
+    } else if constexpr (DP == 2) {
+        *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int h = 0; h < DP / 4; ++h)
+            reinterpret_cast<float4*>(dst)[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+    }
+}
+
+template <typename T, int DP>
+__global__ void k_pack_dp(const double* __restrict__ x, const int32_t* __restrict__ perm, int64_t n,
+                          const PackParams pp, PackOut<T> o) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t src_i = perm[p];
+    double xv[DP];
+#pragma unroll
+    for (int h = 0; h < DP / 2; ++h) {
+        const double2 v = reinterpret_cast<const double2*>(x + (int64_t)src_i * DP)[h];
+        xv[2 * h] = v.x;
+        xv[2 * h + 1] = v.y;
+    }
+    store_row<double, DP>(o.xs + p * DP, xv);
+    T yv[DP];
+    T nrm = T(0);
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+        yv[k] = T((xv[k] - pp.lo[k]) * pp.scale);
+        nrm = fma_pack(yv[k], yv[k], nrm);
+    }
+    store_row<T, DP>(o.y + p * DP, yv);
+    o.h[p] = -nrm * T(0.5);
+    const T to = pack_thr_out(pp, nrm);
+    const T ti = pp.has_in ? pack_thr_in(pp, nrm) : T(INFINITY);
+    o.thr_out[p] = to;
+    o.thr_in[p] = ti;
+    if (o.aux) o.aux[p] = make_float4((float)to, (float)ti, __int_as_float(src_i), 0.f);
+}
+
 // The counting sort's scatter: one thread per input point takes its sorted
 // position, off64[key] >> 32 plus its rank among the key's points (in the
 // order warps reach the key).  (Fusing the packing into this scatter was
@@ -1126,7 +1173,18 @@ static int pack_points(Index* ix, const double* pts, const PackParams& hp) {
         ix->sc_w = o.sc_w;
         ix->sc_b = hp.sc_b;
     }
-    k_pack<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, ix->perm, n, hp, o);
+    bool identity = true;
+    for (int k = 0; k < ix->d; ++k) identity = identity && hp.order[k] == k;
+    const bool rows16 = ix->d == ix->dp && identity && !o.sc_w && (reinterpret_cast<uintptr_t>(pts) & 15u) == 0;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (rows16 && ix->dp == 2)
+        k_pack_dp<T, 2><<<blocks, 256, 0, s>>>(pts, ix->perm, n, hp, o);
+    else if (rows16 && ix->dp == 4)
+        k_pack_dp<T, 4><<<blocks, 256, 0, s>>>(pts, ix->perm, n, hp, o);
+    else if (rows16 && ix->dp == 8)
+        k_pack_dp<T, 8><<<blocks, 256, 0, s>>>(pts, ix->perm, n, hp, o);
+    else
+        k_pack<T><<<blocks, 256, 0, s>>>(pts, ix->perm, n, hp, o);
     note_launch();
     SJ_CK(cudaGetLastError());
     return SJ_OK;
