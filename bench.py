@@ -474,21 +474,30 @@ def roofline(kname, w, r, kern_ms):
         flops = 2.0 * kp * r["n_evaluated"]
         # (fp16 and bf16 have the same dense tensor rate: the bf16 peak serves both)
         fp_peak, unit_bound = float(peaks.get("bf16_tflops", 1900.0)), "tensor"
+        fp_source = ("MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 burst, measured on this pool)"
+                     if "bf16_tflops" in peaks else "fallback 1900 TFLOP/s bf16")
     else:
         flops = 2.0 * w.d * r["n_evaluated"]
         fp_peak = {"fp64_fma": FP64_DFMA_TFLOPS, "fp64_dmma": FP64_DMMA_TFLOPS}.get(kname, FP32_FMA_PEAK_TFLOPS)
+        fp_source = ("profiles/fp64_peaks_gb300.txt (this repository's FP64 micro-benchmark)"
+                     if kname in ("fp64_fma", "fp64_dmma", "fp64_fma_sc") else
+                     "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (formula)")
         unit_bound = "alu"
     tfl = flops / (kern_ms * 1e-3) / 1e12
     bytes_alg = w.n * (elt * (dp + 3) + 4) + 8 * r["count"]
     gbs = bytes_alg / (kern_ms * 1e-3) / 1e9
     frac_alu, frac_hbm = tfl / fp_peak, gbs / hbm_peak
+    hbm_source = ("MEASURED_PEAKS.json hbm_gbs (copy bandwidth, measured on this pool)" if "hbm_gbs" in peaks
+                  else "fallback 6800 GB/s")
+    # flop convention: d fused multiply-adds (2 d flop) per evaluated pair
     common = {"traffic": read_traffic(kname, w.name), "kernel": KERNEL_NAMES.get(kname, kname),
               "kernel_ms": round(kern_ms, 4), "flop_per_launch": flops, "bytes_per_launch": bytes_alg}
     if frac_alu >= frac_hbm:
         return {"bound": unit_bound, "achieved": round(tfl, 3), "peak": round(fp_peak, 3), "unit": "TFLOP/s",
-                "frac": round(frac_alu, 4), "hbm_frac": round(frac_hbm, 4), **common}
+                "frac": round(frac_alu, 4), "peak_source": fp_source, "hbm_frac": round(frac_hbm, 4), **common}
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(frac_hbm, 4), "alu_frac": round(frac_alu, 4), **common}
+            "frac": round(frac_hbm, 4), "peak_source": hbm_source, "alu_frac": round(frac_alu, 4),
+            "alu_peak_source": fp_source, **common}
 
 
 def make_line(args, w, results, variants, world, kern_ms, e2e_s, head):
@@ -507,7 +516,8 @@ def make_line(args, w, results, variants, world, kern_ms, e2e_s, head):
                   "result_pairs_per_s": r["count"] / (r["ms_per_step"] * 1e-3), "result_pairs": r["count"],
                   "evaluated_pairs": r["n_evaluated"], "rechecked_pairs": r["n_rechecked"], "reruns": r["reruns"],
                   "tile_kernel_ms": round(r["tile_ms"], 4), "kernel": r.get("kernel", k),
-                  "tile_roofline": {key: rk[key] for key in ("bound", "achieved", "peak", "unit", "frac")}}
+                  "tile_roofline": {key: rk[key] for key in ("bound", "achieved", "peak", "unit", "frac",
+                                                             "peak_source")}}
     e2e_val = cand / e2e_s
     line = {
         "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -834,13 +844,17 @@ def batch_rooflines(r):
             kp = ((6 if g["kernel"] == "filter_bf16x3" else 3) * dp + 3 + 15) // 16 * 16
             flops, peak, kern = 2.0 * kp * g["evaluated"], bf16, "k_join_tc<" + g["kernel"][7:] + ">"
             bound = "tensor"
+            source = ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16 under the power cap, measured on "
+                      "this pool)" if "bf16_tflops_sustained" in peaks else "fallback 1700 TFLOP/s bf16")
         else:
             flops = g["flops_2d"]
             peak = FP64_DFMA_TFLOPS if g["kernel"] == "fp64_fma" else FP32_FMA_PEAK_TFLOPS
             kern, bound = KERNEL_NAMES.get(g["kernel"], g["kernel"]), "alu"
+            source = ("profiles/fp64_peaks_gb300.txt (this repository's FP64 micro-benchmark)"
+                      if g["kernel"] == "fp64_fma" else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (formula)")
         tfl = flops / sec / 1e12
         out[f"d{dp}"] = {"bound": bound, "achieved": round(tfl, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                         "frac": round(tfl / peak, 4), "traffic": None, "kernel": kern,
+                         "frac": round(tfl / peak, 4), "peak_source": source, "traffic": None, "kernel": kern,
                          "kernel_ms": round(g["ms"], 3), "instances": g["instances"],
                          "evaluated_pairs": g["evaluated"]}
     return out
