@@ -77,3 +77,28 @@ def test_real_oracle_passes():
 def test_mutant_is_caught(tmp_path, name):
     lib = _build_mutant(tmp_path, name)
     assert not _pins_pass(lib), f"planted mistake {name} was not caught"
+
+
+def test_row_offset_mutant_is_caught(tmp_path):
+    """A mistake in the row function alone (the query row taken at q instead of
+    q d) is caught by the lattice row pin, which the real oracle passes."""
+    src = open(SRC).read()
+    old = "const double* a = x + q * (int64_t)d;"
+    assert src.count(old) == 1
+    c = tmp_path / "row_offset.c"
+    c.write_text(src.replace(old, "const double* a = x + q;"))
+    so = tmp_path / "row_offset.so"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so), str(c), "-lm"],
+                   check=True)
+    lib = oracle._configure(ctypes.CDLL(str(so)))
+
+    def row(x, q):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.empty(x.shape[0], dtype=np.float64)
+        lib.sjo_sqdist_row(x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), x.shape[0], x.shape[1], int(q),
+                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    from tests.test_oracle_pins import lattice_row_ok
+    assert lattice_row_ok(oracle.sqdist_row)
+    assert not lattice_row_ok(row), "planted mistake in the row function was not caught"

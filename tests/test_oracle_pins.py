@@ -185,6 +185,30 @@ def test_borderline_classifier(orc):
         assert orc.is_borderline(x, 0, 1, eps) == want, r
 
 
+def _lattice_rows():
+    g = np.random.Generator(np.random.PCG64(77))
+    k = g.integers(-50, 50, size=(300, 5))
+    return k, k / 32.0
+
+
+def lattice_row_ok(sqdist_row) -> bool:
+    """Squared distances of one point to all points on a dyadic lattice: every
+    binary64 operation is exact there, so each value must equal exact integer
+    arithmetic, (sum of squared integer differences) / 2^10."""
+    k, x = _lattice_rows()
+    for q in (0, 17, 299):
+        want = ((k - k[q]) ** 2).sum(1) / 1024.0
+        if not np.array_equal(sqdist_row(x, q), want):
+            return False
+    return True
+
+
+def test_sqdist_row_exact_on_lattice(orc):
+    """The rows the GPU certification and kNN tests compare with (Eq. 1 squared,
+    the decision rule's operation order) against exact integer arithmetic."""
+    assert lattice_row_ok(orc.sqdist_row)
+
+
 def test_rows_match_join(orc):
     """Per-query rows equal the corresponding slice of the full result."""
     w = workloads.uniform2d(n=3000, seed=4)
