@@ -47,11 +47,10 @@
 
 namespace sj {
 
-// Candidate slots per lane of the chunks (register budget: 2 for d = 8) and
-// entries in a warp's stage (after the prune a chunk stages about 90 entries
-// on the uniform 4-D workload, the stage several chunks' worth; a smaller
-// stage sends more chunks down the windowed path).  Compile-time tuning
-// constants.
+// Candidate slots per lane of the main chunks (register budget: 2 for d = 8)
+// and pairs in a warp's stage (a main chunk emits about 32 TC x the mean
+// queries per item x 13% x 2 pairs on the uniform workloads; the stage holds
+// a typical chunk's output).  Compile-time tuning constants.
 #ifndef SJ_F32S_TC_SMALL
 #define SJ_F32S_TC_SMALL 2
 #endif
